@@ -1,0 +1,186 @@
+/*
+ * pmmm.h -- C ABI of the GB300 particle mesh multipole method library (libpmmm.so).
+ *
+ * The library computes, for N point charges (or masses) in a rectangular box
+ * split into a uniform mesh of cells, the potential and force on every
+ * particle with the particle mesh multipole method (PMMM) of K. Nitadori,
+ * arXiv:1409.5981.  The problem statement follows Sec. 2.1 of the paper:
+ * N particles in K uniform cells; multipole moments of (p+1)^2 real numbers per
+ * cell (App. A.7); the cell convolution L_i = sum_j G_{i-j} M_j of Eq. pmmm done
+ * with FFTs (Sec. 2.1), zero-padded to twice the mesh per axis for open
+ * boundaries (App. C); the nearest (2c+1)^3 cells masked out of G and summed
+ * directly as a pure 1/r near field (Sec. 2.1, Sec. 2.2); periodic boundaries
+ * through the Ewald-split Green function of App. B with the corrections of
+ * App. B.3.
+ *
+ * Conventions shared by every call:
+ *   - Status: every function returning int returns PMMM_OK (0) or a negative
+ *     PMMM_ERR_* code; no call aborts or prints.  pmmm_strerror() names a code.
+ *   - Memory: pointers passed to pmmm_compute are DEVICE pointers of the
+ *     current CUDA device, owned by the caller, and must stay valid until the
+ *     work queued on the plan's stream has finished.  The plan owns its own
+ *     workspace (allocated in pmmm_plan_create / pmmm_plan_reserve).
+ *   - Element types: double for PMMM_FP64, float for the FP32 precisions.
+ *   - Layout: positions and forces are array-of-structs, n x 3 (x, y, z);
+ *     charges and potentials n.  Results are in the caller's particle order.
+ *   - Streams: work is queued on the stream given at plan creation (NULL = the
+ *     legacy default stream); calls return without waiting except where noted.
+ *   - Physics: phi_i = sign * sum_{j != i} q_j / |r_i - r_j| (sign = +1 Coulomb,
+ *     sign = -1 gravity with G = 1); force_i = -q_i grad phi_i.  Periodic
+ *     results are those of the Ewald sum with tin-foil boundary conditions.
+ */
+#ifndef PMMM_H
+#define PMMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PMMM_ABI_VERSION 1
+
+/* Boundary condition (abstract of the paper: open and periodic). */
+typedef enum { PMMM_OPEN = 0, PMMM_PERIODIC = 1 } pmmm_boundary;
+
+/* Arithmetic of the hot path.  FP64: everything in double.  FP32: binning,
+ * Green-function set-up and global reductions in double, P2M / FFT / M2L /
+ * L2P / near field in float.  FP32_SPLITBF16_M2L is reserved for the batched
+ * tensor-core M2L and currently behaves as FP32. */
+typedef enum { PMMM_FP64 = 0, PMMM_FP32 = 1, PMMM_FP32_SPLITBF16_M2L = 2 } pmmm_precision;
+
+enum {
+  PMMM_OK = 0,
+  PMMM_ERR_INVALID_ARG = -1,     /* NULL pointer, bad size, bad config field */
+  PMMM_ERR_UNSUPPORTED = -2,     /* valid but not implemented (mesh not a power of two, p too high, ...) */
+  PMMM_ERR_OUT_OF_BOX = -3,      /* open boundary: a particle outside [lo, lo + len) */
+  PMMM_ERR_NONFINITE_INPUT = -4, /* a position is NaN or infinite */
+  PMMM_ERR_CUDA = -5,            /* a CUDA runtime call or kernel launch failed */
+  PMMM_ERR_TIMEOUT = -6,         /* a bounded device-side wait gave up */
+  PMMM_ERR_OOM = -7              /* device allocation failed */
+};
+
+/* Problem configuration.  Initialise with pmmm_config_init() and set fields. */
+typedef struct pmmm_config {
+  double box_lo[3];    /* lower corner of the box */
+  double box_len[3];   /* box side lengths b_x, b_y, b_z (> 0) */
+  int32_t mesh[3];     /* cells per axis; powers of two, 1..256 (open) or 4..512 (periodic, >= 2c+1) */
+  int32_t p;           /* expansion order 0..12 (gradients need p >= 1; at p = 0 only the near field has a gradient) */
+  int32_t cutoff;      /* c: minimum cell separation of the far field; 1 -> 27 near cells, 2 -> 125 */
+  int32_t boundary;    /* pmmm_boundary */
+  int32_t precision;   /* pmmm_precision */
+  int32_t reserved0;
+  double sign;         /* +1 Coulomb, -1 gravity */
+  double ewald_alpha;  /* periodic splitting parameter; 0 -> 1.5 / min(box_len) (App. B.1 example) */
+  int32_t ewald_nmax;  /* periodic lattice sums over |n|_2 <= nmax (both sums); 0 -> 5 */
+  int32_t reserved[7];
+} pmmm_config;
+
+typedef struct pmmm_plan pmmm_plan;
+
+/* ABI version of the loaded library (PMMM_ABI_VERSION). */
+int pmmm_abi_version(void);
+
+/* Fills *cfg with defaults: unit box at the origin, mesh 8^3, p = 4, c = 1,
+ * open boundary, FP64, sign +1, alpha and nmax automatic. */
+void pmmm_config_init(pmmm_config* cfg);
+
+/* Validates cfg, allocates the plan's workspace on the current device and
+ * precomputes the Fourier spectra of the (2p+1)^2 Green-function components
+ * (Sec. 2.1: "performed and saved at the beginning"; App. B for periodic).
+ * Synchronises the stream before returning.  cuda_stream: a cudaStream_t or NULL.
+ * On error *out is set to NULL and nothing is leaked. */
+int pmmm_plan_create(const pmmm_config* cfg, void* cuda_stream, pmmm_plan** out);
+
+/* Releases the plan and its device memory (synchronises its stream first).  NULL is accepted. */
+int pmmm_plan_destroy(pmmm_plan* plan);
+
+/* Pre-allocates particle workspace for up to n_max particles, so that later
+ * pmmm_compute calls with n <= n_max allocate nothing. */
+int pmmm_plan_reserve(pmmm_plan* plan, int64_t n_max);
+
+/* One full force evaluation (all steps of the hot path on the plan's stream):
+ * binning and stable counting sort by cell (Sec. 2.1), P2M (Eq. P2M), forward
+ * FFTs of the (p+1)^2 channels, per-wavevector M2L (Eq. realmatrix), inverse
+ * FFTs, periodic corrections (App. B.3), L2P with the order-one gradient
+ * (Eqs. L2P, L2L, phigrad) and the (2c+1)^3-cell near field.
+ *   n       number of particles (>= 0; n <= 2^31 - 1)
+ *   pos     device, n x 3 positions (double for FP64, float otherwise)
+ *   q       device, n charges / masses
+ *   phi     device, n potentials (output; may be NULL)
+ *   force   device, n x 3 forces (output; may be NULL)
+ *   energy  HOST pointer or NULL; if given, receives U = 1/2 sum q_i phi_i
+ *           (FP64 reduction) and the call synchronises the stream and also
+ *           reports input errors (out-of-box, non-finite) detected on device.
+ * Without `energy` the call is asynchronous: input errors detected on the device
+ * are reported by the next pmmm_plan_status().  Invalid positions never cause an
+ * out-of-bounds access: they are clamped into a cell and flagged. */
+int pmmm_compute(pmmm_plan* plan, int64_t n, const void* pos, const void* q, void* phi, void* force, double* energy);
+
+/* Same as pmmm_compute with HOST arrays (pinned memory recommended): copies
+ * the inputs to plan-owned device buffers, computes, and copies phi / force
+ * back; synchronises the stream and returns the device-side status.  */
+int pmmm_compute_host(pmmm_plan* plan, int64_t n, const void* pos, const void* q, void* phi, void* force,
+                      double* energy);
+
+/* Synchronises the plan's stream and returns (and clears) the first error
+ * recorded on the device by earlier pmmm_compute calls. */
+int pmmm_plan_status(pmmm_plan* plan);
+
+/* Copies an internal result of the last pmmm_compute to host memory, for
+ * tests and diagnostics (synchronises).  bytes must equal the size stated:
+ *   PMMM_EXPORT_PERM        int32[n]     original index of each sorted slot
+ *   PMMM_EXPORT_SORTED_CELL int32[n]     cell id (ix + nx (iy + ny iz)) of each sorted slot
+ *   PMMM_EXPORT_CELL_START  int32[K+1]   first sorted slot of each cell; [K] = n
+ *   PMMM_EXPORT_MULTIPOLE   double[C*K]  M in the real storage of App. A.7, channel-major
+ *                                        ([c][cell]), physical units (C = (p+1)^2)
+ *   PMMM_EXPORT_LOCAL       double[C*K]  L after the cell convolution, before the
+ *                                        periodic corrections, same layout and units
+ *   PMMM_EXPORT_CORR        double[8]    total charge Q, sum_cells M_1^0, Re and Im of
+ *                                        sum_cells M_1^1, sum q |r_rel|^2, alpha, V, unused
+ *   PMMM_EXPORT_FAR         double[4*n]  per sorted slot: far-field phi and grad phi
+ *                                        (Coulomb sign, corrections included)
+ */
+enum {
+  PMMM_EXPORT_PERM = 1,
+  PMMM_EXPORT_SORTED_CELL = 2,
+  PMMM_EXPORT_CELL_START = 3,
+  PMMM_EXPORT_MULTIPOLE = 4,
+  PMMM_EXPORT_LOCAL = 5,
+  PMMM_EXPORT_CORR = 6,
+  PMMM_EXPORT_FAR = 7
+};
+int pmmm_plan_export(pmmm_plan* plan, int what, void* host_dst, size_t bytes);
+
+/* Integer facts about a plan: PMMM_INFO_K (cells), PMMM_INFO_C ((p+1)^2),
+ * PMMM_INFO_CG ((2p+1)^2), PMMM_INFO_KH (stored wavevectors per channel),
+ * PMMM_INFO_N (particles of the last compute), PMMM_INFO_WORKSPACE_BYTES,
+ * PMMM_INFO_LAUNCHES (kernels launched by the last compute). */
+enum {
+  PMMM_INFO_K = 1,
+  PMMM_INFO_C = 2,
+  PMMM_INFO_CG = 3,
+  PMMM_INFO_KH = 4,
+  PMMM_INFO_N = 5,
+  PMMM_INFO_WORKSPACE_BYTES = 6,
+  PMMM_INFO_LAUNCHES = 7
+};
+int pmmm_plan_info(pmmm_plan* plan, int what, int64_t* value);
+
+/* Per-stage timing with CUDA events on the plan's stream (off by default).
+ * pmmm_plan_stage_times synchronises and writes up to max_stages values in
+ * milliseconds for the last compute, in the order of pmmm_stage_name(i);
+ * returns the number of stages written. */
+int pmmm_plan_set_timing(pmmm_plan* plan, int enable);
+int pmmm_plan_stage_times(pmmm_plan* plan, float* ms, int max_stages);
+const char* pmmm_stage_name(int i);
+
+/* Human-readable name of a status code (static string). */
+const char* pmmm_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMMM_H */

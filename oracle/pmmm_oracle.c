@@ -674,39 +674,59 @@ int orc_pmmm(const orc_cfg *cfg, int64_t n, const double *pos, const double *q, 
     }
     if (M_out) memcpy(M_out, M, sizeof(cplx) * K * np);
 
-    /* Green function for every distinct displacement */
+    /* Green function for every distinct displacement, precomputed when that
+     * table fits in 1 GiB, else evaluated for each cell pair. */
     int gx = cfg->periodic ? nx : 2 * nx - 1, gy = cfg->periodic ? ny : 2 * ny - 1, gz = cfg->periodic ? nz : 2 * nz - 1;
     int64_t NG = (int64_t)gx * gy * gz;
-    cplx *Gall = (cplx *)malloc(sizeof(cplx) * NG * ng);
+    int table = (double)NG * ng * sizeof(cplx) <= (double)(1 << 30);
+    cplx *Gall = table ? (cplx *)malloc(sizeof(cplx) * NG * ng) : NULL;
+    if (table) {
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t t = 0; t < NG; ++t) {
-        int a = (int)(t % gx), b = (int)((t / gx) % gy), e = (int)(t / ((int64_t)gx * gy));
-        if (cfg->periodic) {
-            int d[3] = {a, b, e};
-            orc_green_periodic(p, c, cfg->mesh, cfg->len, cfg->alpha, cfg->nmax, d, (double *)(Gall + t * ng));
-        } else {
-            int d[3] = {a - (nx - 1), b - (ny - 1), e - (nz - 1)};
-            orc_green_open(p, c, h, d, (double *)(Gall + t * ng));
+        for (int64_t t = 0; t < NG; ++t) {
+            int a = (int)(t % gx), b = (int)((t / gx) % gy), e = (int)(t / ((int64_t)gx * gy));
+            if (cfg->periodic) {
+                int d[3] = {a, b, e};
+                orc_green_periodic(p, c, cfg->mesh, cfg->len, cfg->alpha, cfg->nmax, d, (double *)(Gall + t * ng));
+            } else {
+                int d[3] = {a - (nx - 1), b - (ny - 1), e - (nz - 1)};
+                orc_green_open(p, c, h, d, (double *)(Gall + t * ng));
+            }
         }
     }
 
     int64_t nT = ntc < 0 ? K : ntc;
     cplx *L = (cplx *)calloc((size_t)nT * np, sizeof(cplx));
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t t = 0; t < nT; ++t) {
-        int64_t ci = ntc < 0 ? t : tcells[t];
-        int ix = (int)(ci % nx), iy = (int)((ci / nx) % ny), iz = (int)(ci / ((int64_t)nx * ny));
-        for (int64_t cj = 0; cj < K; ++cj) {
-            int jx = (int)(cj % nx), jy = (int)((cj / nx) % ny), jz = (int)(cj / ((int64_t)nx * ny));
-            int64_t g;
-            if (cfg->periodic) {
-                int dx = ((ix - jx) % nx + nx) % nx, dy = ((iy - jy) % ny + ny) % ny, dz = ((iz - jz) % nz + nz) % nz;
-                g = dx + (int64_t)gx * (dy + (int64_t)gy * dz);
-            } else {
-                g = (ix - jx + nx - 1) + (int64_t)gx * ((iy - jy + ny - 1) + (int64_t)gy * (iz - jz + nz - 1));
+#pragma omp parallel
+    {
+        cplx *Gp = (cplx *)malloc(sizeof(cplx) * ng);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t t = 0; t < nT; ++t) {
+            int64_t ci = ntc < 0 ? t : tcells[t];
+            int ix = (int)(ci % nx), iy = (int)((ci / nx) % ny), iz = (int)(ci / ((int64_t)nx * ny));
+            for (int64_t cj = 0; cj < K; ++cj) {
+                int jx = (int)(cj % nx), jy = (int)((cj / nx) % ny), jz = (int)(cj / ((int64_t)nx * ny));
+                const cplx *G;
+                if (cfg->periodic) {
+                    int d[3] = {((ix - jx) % nx + nx) % nx, ((iy - jy) % ny + ny) % ny, ((iz - jz) % nz + nz) % nz};
+                    if (table) {
+                        G = Gall + (d[0] + (int64_t)gx * (d[1] + (int64_t)gy * d[2])) * ng;
+                    } else {
+                        orc_green_periodic(p, c, cfg->mesh, cfg->len, cfg->alpha, cfg->nmax, d, (double *)Gp);
+                        G = Gp;
+                    }
+                } else {
+                    int d[3] = {ix - jx, iy - jy, iz - jz};
+                    if (table) {
+                        G = Gall + ((d[0] + nx - 1) + (int64_t)gx * ((d[1] + ny - 1) + (int64_t)gy * (d[2] + nz - 1))) * ng;
+                    } else {
+                        orc_green_open(p, c, h, d, (double *)Gp);
+                        G = Gp;
+                    }
+                }
+                m2l_green(p, M + cj * np, G, L + t * np);
             }
-            m2l_green(p, M + cj * np, Gall + g * ng, L + t * np);
         }
+        free(Gp);
     }
     free(Gall);
     if (L_out)

@@ -1,0 +1,266 @@
+"""Python binding of libpmmm.so, the GB300 particle mesh multipole method library.
+
+Argument marshalling only: every step of a force evaluation runs in the CUDA
+kernels of ``csrc/`` behind the C ABI of ``include/pmmm.h``.  PyTorch supplies
+device memory and the stream.  There is no CPU fallback: if the compiled
+library is missing, loading fails with an error naming the build step.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpmmm.so")
+
+OK = 0
+ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OUT_OF_BOX, ERR_NONFINITE_INPUT = -1, -2, -3, -4
+ERR_CUDA, ERR_TIMEOUT, ERR_OOM = -5, -6, -7
+OPEN, PERIODIC = 0, 1
+FP64, FP32, FP32_SPLITBF16_M2L = 0, 1, 2
+EXPORT_PERM, EXPORT_SORTED_CELL, EXPORT_CELL_START = 1, 2, 3
+EXPORT_MULTIPOLE, EXPORT_LOCAL, EXPORT_CORR, EXPORT_FAR = 4, 5, 6, 7
+INFO_K, INFO_C, INFO_CG, INFO_KH, INFO_N, INFO_WORKSPACE_BYTES, INFO_LAUNCHES = 1, 2, 3, 4, 5, 6, 7
+
+
+class PmmmError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = _lib().pmmm_strerror(status).decode() if _LIB is not None else str(status)
+        super().__init__(f"{what}: {msg} ({status})" if what else f"{msg} ({status})")
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [
+        ("box_lo", ctypes.c_double * 3),
+        ("box_len", ctypes.c_double * 3),
+        ("mesh", ctypes.c_int32 * 3),
+        ("p", ctypes.c_int32),
+        ("cutoff", ctypes.c_int32),
+        ("boundary", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("sign", ctypes.c_double),
+        ("ewald_alpha", ctypes.c_double),
+        ("ewald_nmax", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
+    ]
+
+
+_LIB = None
+
+# Every function the C ABI declares, with its ctypes signature.
+_SIGS = {
+    "pmmm_abi_version": (ctypes.c_int, []),
+    "pmmm_config_init": (None, [ctypes.POINTER(_Config)]),
+    "pmmm_plan_create": (ctypes.c_int, [ctypes.POINTER(_Config), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "pmmm_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pmmm_plan_reserve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "pmmm_compute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "pmmm_compute_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "pmmm_plan_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "pmmm_plan_export": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
+    "pmmm_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+    "pmmm_plan_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "pmmm_plan_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+    "pmmm_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "pmmm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def _lib():
+    """Loads libpmmm.so; raises if it has not been built (no fallback)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; "
+                               f"g.build()\"` (nvcc, sm_103a)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def build(force: bool = False) -> str:
+    """Compiles libpmmm.so in-tree (see buildlib.py)."""
+    from . import buildlib
+    return buildlib.build(force=force)
+
+
+def stage_names():
+    out, i = [], 0
+    while True:
+        s = _lib().pmmm_stage_name(i)
+        if s is None:
+            return out
+        out.append(s.decode())
+        i += 1
+
+
+@dataclass
+class Config:
+    """Mirror of pmmm_config (include/pmmm.h)."""
+    box_lo: tuple = (0.0, 0.0, 0.0)
+    box_len: tuple = (1.0, 1.0, 1.0)
+    mesh: tuple = (8, 8, 8)
+    p: int = 4
+    cutoff: int = 1
+    boundary: int = OPEN
+    precision: int = FP64
+    sign: float = 1.0
+    ewald_alpha: float = 0.0
+    ewald_nmax: int = 0
+
+    def to_c(self) -> _Config:
+        c = _Config()
+        _lib().pmmm_config_init(ctypes.byref(c))
+        for a in range(3):
+            c.box_lo[a] = float(self.box_lo[a])
+            c.box_len[a] = float(self.box_len[a])
+            c.mesh[a] = int(self.mesh[a])
+        c.p, c.cutoff, c.boundary, c.precision = int(self.p), int(self.cutoff), int(self.boundary), int(self.precision)
+        c.sign, c.ewald_alpha, c.ewald_nmax = float(self.sign), float(self.ewald_alpha), int(self.ewald_nmax)
+        return c
+
+    @property
+    def fp64(self) -> bool:
+        return self.precision == FP64
+
+
+def _check(st: int, what: str):
+    if st != OK:
+        raise PmmmError(st, what)
+
+
+class Plan:
+    """A PMMM plan: geometry, order, precision, precomputed kernel spectra and workspace.
+
+    ``compute`` takes CUDA tensors (float64 for FP64, float32 otherwise):
+    pos (n, 3), q (n,), and returns (phi (n,), force (n, 3), energy or None).
+    """
+
+    def __init__(self, cfg: Config, stream=None):
+        import torch
+        self.cfg = cfg
+        self._c = cfg.to_c()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = ctypes.c_void_p()
+        _check(_lib().pmmm_plan_create(ctypes.byref(self._c), ctypes.c_void_p(stream.cuda_stream),
+                                       ctypes.byref(handle)), "pmmm_plan_create")
+        self._h = handle
+        self.dtype = torch.float64 if cfg.fp64 else torch.float32
+        self.np_dtype = np.float64 if cfg.fp64 else np.float32
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().pmmm_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------------ compute
+    def reserve(self, n: int):
+        _check(_lib().pmmm_plan_reserve(self._h, int(n)), "pmmm_plan_reserve")
+
+    def compute(self, pos, q, phi=None, force=None, energy: bool = False, check: bool = False):
+        import torch
+        n = int(q.shape[0])
+        for t, nm in ((pos, "pos"), (q, "q")):
+            if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous()):
+                raise ValueError(f"{nm} must be a contiguous CUDA {self.dtype} tensor")
+        if pos.shape != (n, 3):
+            raise ValueError("pos must have shape (n, 3)")
+        if phi is None:
+            phi = torch.empty(n, dtype=self.dtype, device=q.device)
+        if force is None:
+            force = torch.empty((n, 3), dtype=self.dtype, device=q.device)
+        e = ctypes.c_double(0.0)
+        st = _lib().pmmm_compute(self._h, n, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(q.data_ptr()),
+                                 ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(force.data_ptr()),
+                                 ctypes.byref(e) if energy else None)
+        _check(st, "pmmm_compute")
+        if check and not energy:
+            _check(_lib().pmmm_plan_status(self._h), "pmmm_compute (device status)")
+        return phi, force, (e.value if energy else None)
+
+    def compute_raw(self, n: int, pos_ptr: int, q_ptr: int, phi_ptr: int, force_ptr: int) -> int:
+        """Queue one evaluation on raw device pointers; returns the status."""
+        return _lib().pmmm_compute(self._h, int(n), ctypes.c_void_p(pos_ptr), ctypes.c_void_p(q_ptr),
+                                   ctypes.c_void_p(phi_ptr), ctypes.c_void_p(force_ptr), None)
+
+    def compute_host(self, pos, q, phi=None, force=None, energy: bool = False):
+        """Host arrays in and out (numpy or pinned CPU tensors); synchronous."""
+        def ptr(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        n = int(q.shape[0])
+        if phi is None:
+            phi = np.empty(n, dtype=self.np_dtype)
+        if force is None:
+            force = np.empty((n, 3), dtype=self.np_dtype)
+        e = ctypes.c_double(0.0)
+        st = _lib().pmmm_compute_host(self._h, n, ctypes.c_void_p(ptr(pos)), ctypes.c_void_p(ptr(q)),
+                                      ctypes.c_void_p(ptr(phi)), ctypes.c_void_p(ptr(force)),
+                                      ctypes.byref(e) if energy else None)
+        _check(st, "pmmm_compute_host")
+        return phi, force, (e.value if energy else None)
+
+    def status(self) -> int:
+        return int(_lib().pmmm_plan_status(self._h))
+
+    # ------------------------------------------------------------------ diagnostics
+    def info(self, what: int) -> int:
+        v = ctypes.c_int64(0)
+        _check(_lib().pmmm_plan_info(self._h, int(what), ctypes.byref(v)), "pmmm_plan_info")
+        return int(v.value)
+
+    def export(self, what: int) -> np.ndarray:
+        n, K, C = self.info(INFO_N), self.info(INFO_K), self.info(INFO_C)
+        shapes = {
+            EXPORT_PERM: ((n,), np.int32),
+            EXPORT_SORTED_CELL: ((n,), np.int32),
+            EXPORT_CELL_START: ((K + 1,), np.int32),
+            EXPORT_MULTIPOLE: ((C, K), np.float64),
+            EXPORT_LOCAL: ((C, K), np.float64),
+            EXPORT_CORR: ((8,), np.float64),
+            EXPORT_FAR: ((n, 4), np.float64),
+        }
+        shape, dt = shapes[what]
+        out = np.zeros(shape, dtype=dt)
+        _check(_lib().pmmm_plan_export(self._h, int(what), ctypes.c_void_p(out.ctypes.data), out.nbytes),
+               "pmmm_plan_export")
+        return out
+
+    def set_timing(self, on: bool = True):
+        _check(_lib().pmmm_plan_set_timing(self._h, int(bool(on))), "pmmm_plan_set_timing")
+
+    def stage_times(self) -> dict:
+        names = stage_names()
+        buf = (ctypes.c_float * len(names))()
+        k = _lib().pmmm_plan_stage_times(self._h, buf, len(names))
+        if k < 0:
+            raise PmmmError(k, "pmmm_plan_stage_times")
+        return {names[i]: float(buf[i]) for i in range(k)}

@@ -1,0 +1,280 @@
+// Batched 3-D real FFTs of the (p+1)^2 moment channels (Sec. 2.1) on
+// power-of-two meshes, with the zero padding of open boundaries (App. C) kept
+// implicit: rows, columns and planes known to be zero are neither read nor
+// transformed, and only the physical octant of the inverse is written.
+//
+//   forward:  x: real rows -> half spectra (two real rows per complex FFT)
+//             y: columns of length Ly over z < nz planes (rows y >= ny are zero)
+//             z: columns of length Lz (planes z >= nz are zero)
+//   inverse:  z (only z < nz written), y (only y < ny), x: half -> real rows,
+//             only x < nx written.
+// Spectra are stored [C][Lz][Ly][hx], hx = Lx/2 + 1.  Every 1-D transform is a
+// shared-memory Stockham FFT (fft.cuh).
+#include "internal.cuh"
+
+namespace pmmm {
+
+namespace {
+
+constexpr int FFT_THREADS = 256;
+
+// Runs every Stockham stage of `ntrans` transforms held in shared memory.
+// ROWS: transform tr occupies A[tr * L .. tr * L + L) (element stride 1) and the
+// butterfly index varies fastest across threads.  Otherwise (columns) element t
+// of transform tr sits at A[t * ntrans + tr] and the transform index varies
+// fastest, so that neighbouring threads touch neighbouring words.
+template <typename T, bool ROWS>
+__device__ __forceinline__ void run_stages(cpx<T>*& A, cpx<T>*& B, const FftPlan1D& pl, int ntrans,
+                                           const cpx<T>* tw, int sgn) {
+  int Ns = 1;
+  const int L = pl.L;
+  for (int st = 0; st < pl.nst; ++st) {
+    const int R = pl.rad[st];
+    const int nb = L / R;
+    const int tasks = nb * ntrans;
+    for (int t = threadIdx.x; t < tasks; t += blockDim.x) {
+      if (ROWS) {
+        const int tr = t / nb, j = t - tr * nb;
+        stockham_bf_any<T>(R, A + tr * L, B + tr * L, L, Ns, j, 1, tw, sgn);
+      } else {
+        const int tr = t % ntrans, j = t / ntrans;
+        stockham_bf_any<T>(R, A + tr, B + tr, L, Ns, j, ntrans, tw, sgn);
+      }
+    }
+    __syncthreads();
+    cpx<T>* tmp = A;
+    A = B;
+    B = tmp;
+    Ns *= R;
+  }
+}
+
+// Forward x pass: rows r = (c, z, y), z < nz, y < ny, real length nx inside Lx.
+// Block handles `ppb` pairs of rows; pair (a, b) is packed as a + i b.
+template <typename T>
+__global__ void __launch_bounds__(FFT_THREADS) r2c_rows_kernel(const T* __restrict__ in, cpx<T>* __restrict__ out,
+                                                               Dims d, int C, FftPlan1D pl,
+                                                               const cpx<T>* __restrict__ tw, int ppb) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* B = A + (size_t)ppb * d.Lx;
+  const int64_t nrows = (int64_t)C * d.nz * d.ny;
+  const int64_t pair0 = (int64_t)blockIdx.x * ppb;
+  const int Lx = d.Lx;
+  for (int e = threadIdx.x; e < ppb * Lx; e += blockDim.x) {
+    const int pr = e / Lx, x = e - pr * Lx;
+    const int64_t ra = 2 * (pair0 + pr), rb = ra + 1;
+    T a = T(0), b = T(0);
+    if (x < d.nx) {
+      if (ra < nrows) a = in[ra * d.nx + x];
+      if (rb < nrows) b = in[rb * d.nx + x];
+    }
+    A[e] = mk(a, b);
+  }
+  __syncthreads();
+  run_stages<T, true>(A, B, pl, ppb, tw, -1);
+  const int hx = d.hx;
+  for (int e = threadIdx.x; e < ppb * hx; e += blockDim.x) {
+    const int pr = e / hx, k = e - pr * hx;
+    const int64_t ra = 2 * (pair0 + pr), rb = ra + 1;
+    const cpx<T> Z = A[pr * Lx + k];
+    const cpx<T> Zm = conjg(A[pr * Lx + ((Lx - k) & (Lx - 1))]);
+    // X = (Z + conj Z_{-k}) / 2 ;  Y = (Z - conj Z_{-k}) / (2i)
+    const cpx<T> X = mk((Z.x + Zm.x) * T(0.5), (Z.y + Zm.y) * T(0.5));
+    const cpx<T> Dd = mk(Z.x - Zm.x, Z.y - Zm.y);
+    const cpx<T> Y = mk(Dd.y * T(0.5), -Dd.x * T(0.5));
+    if (ra < nrows) {
+      const int64_t c = ra / ((int64_t)d.nz * d.ny), rem = ra - c * d.nz * d.ny;
+      const int z = (int)(rem / d.ny), y = (int)(rem - (int64_t)z * d.ny);
+      out[c * d.Kh + ((int64_t)z * d.Ly + y) * hx + k] = X;
+    }
+    if (rb < nrows) {
+      const int64_t c = rb / ((int64_t)d.nz * d.ny), rem = rb - c * d.nz * d.ny;
+      const int z = (int)(rem / d.ny), y = (int)(rem - (int64_t)z * d.ny);
+      out[c * d.Kh + ((int64_t)z * d.Ly + y) * hx + k] = Y;
+    }
+  }
+}
+
+// Inverse x pass: half spectra of rows (c, z < nz, y < ny) -> real rows, x < nx written.
+template <typename T>
+__global__ void __launch_bounds__(FFT_THREADS) c2r_rows_kernel(const cpx<T>* __restrict__ in, T* __restrict__ out,
+                                                               Dims d, int C, FftPlan1D pl,
+                                                               const cpx<T>* __restrict__ tw, int ppb) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* B = A + (size_t)ppb * d.Lx;
+  const int64_t nrows = (int64_t)C * d.nz * d.ny;
+  const int64_t pair0 = (int64_t)blockIdx.x * ppb;
+  const int Lx = d.Lx, hx = d.hx, half = Lx / 2;
+  for (int e = threadIdx.x; e < ppb * Lx; e += blockDim.x) {
+    const int pr = e / Lx, k = e - pr * Lx;
+    const int64_t r2[2] = {2 * (pair0 + pr), 2 * (pair0 + pr) + 1};
+    cpx<T> v[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      v[q] = mk(T(0), T(0));
+      if (r2[q] < nrows) {
+        const int64_t c = r2[q] / ((int64_t)d.nz * d.ny), rem = r2[q] - c * d.nz * d.ny;
+        const int z = (int)(rem / d.ny), y = (int)(rem - (int64_t)z * d.ny);
+        const cpx<T>* row = in + c * d.Kh + ((int64_t)z * d.Ly + y) * hx;
+        if (k <= half) {
+          v[q] = row[k];
+          if (k == 0 || k == half) v[q].y = T(0);
+        } else {
+          v[q] = conjg(row[Lx - k]);
+        }
+      }
+    }
+    // Z = X + i Y
+    A[e] = mk(v[0].x - v[1].y, v[0].y + v[1].x);
+  }
+  __syncthreads();
+  run_stages<T, true>(A, B, pl, ppb, tw, +1);
+  for (int e = threadIdx.x; e < ppb * d.nx; e += blockDim.x) {
+    const int pr = e / d.nx, x = e - pr * d.nx;
+    const int64_t ra = 2 * (pair0 + pr), rb = ra + 1;
+    const cpx<T> z = A[pr * Lx + x];
+    if (ra < nrows) out[ra * d.nx + x] = z.x;
+    if (rb < nrows) out[rb * d.nx + x] = z.y;
+  }
+}
+
+// Column FFTs along a strided axis: element (row, col) of batch b at
+// base(b) + row * col_stride + col, col < inner.  Tile of TW columns per block;
+// rows >= nin read as zero, only rows < nout written back (in place).
+template <typename T>
+__global__ void __launch_bounds__(FFT_THREADS) cols_kernel(cpx<T>* __restrict__ data, int64_t col_stride, int inner,
+                                                           int64_t bstride1, int nb1, int64_t bstride2, int TW,
+                                                           int nin, int nout, int sgn, FftPlan1D pl,
+                                                           const cpx<T>* __restrict__ tw) {
+  extern __shared__ unsigned char smem_raw[];
+  const int L = pl.L;
+  cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* B = A + (size_t)L * TW;
+  const int col0 = blockIdx.y * TW;
+  const int b1 = (int)(blockIdx.x % (unsigned)nb1), b2 = (int)(blockIdx.x / (unsigned)nb1);
+  cpx<T>* base = data + (int64_t)b2 * bstride2 + (int64_t)b1 * bstride1 + col0;
+  const int w = min(TW, inner - col0);
+  for (int e = threadIdx.x; e < L * TW; e += blockDim.x) {
+    const int row = e / TW, col = e - row * TW;
+    A[e] = (row < nin && col < w) ? base[row * col_stride + col] : mk(T(0), T(0));
+  }
+  __syncthreads();
+  run_stages<T, false>(A, B, pl, TW, tw, sgn);
+  for (int e = threadIdx.x; e < L * TW; e += blockDim.x) {
+    const int row = e / TW, col = e - row * TW;
+    if (row < nout && col < w) base[row * col_stride + col] = A[e];
+  }
+}
+
+template <typename T>
+__global__ void twiddle_kernel(int L, cpx<T>* tw) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L) return;
+  double s, c;
+  sincospi(-2.0 * (double)t / (double)L, &s, &c);
+  tw[t] = mk((T)c, (T)s);
+}
+
+int pick_ppb(int L) {
+  int ppb = 2048 / L;
+  return ppb < 1 ? 1 : ppb;
+}
+
+int pick_tw(int inner, int L, size_t elem) {
+  // whole rows of up to 40 columns (e.g. the 17 or 33 points of a half spectrum), else 16
+  int TW = inner <= 40 ? inner : 16;
+  while (TW > 1 && 2 * (size_t)L * TW * elem > 96 * 1024) TW /= 2;
+  return TW;
+}
+
+template <typename T>
+cudaError_t cols(cpx<T>* data, int64_t col_stride, int inner, int64_t bs1, int nb1, int64_t bs2, int nb2, int nin,
+                 int nout, int sgn, int L, const cpx<T>* tw, cudaStream_t s) {
+  const FftPlan1D pl = make_fft_plan(L);
+  const int TW = pick_tw(inner, L, sizeof(cpx<T>));
+  const size_t smem = 2 * (size_t)L * TW * sizeof(cpx<T>);
+  // batches on x (up to 2^31 - 1), column tiles on y (inner / TW <= 65535 for L <= 512)
+  dim3 grid((unsigned)(nb1 * nb2), (unsigned)((inner + TW - 1) / TW));
+  if (smem > 48 * 1024) cudaFuncSetAttribute(cols_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cols_kernel<T><<<grid, FFT_THREADS, smem, s>>>(data, col_stride, inner, bs1, nb1, bs2, TW, nin, nout, sgn, pl, tw);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t forward(const T* in, cpx<T>* spec, const Dims& d, int C, const FftTw& tw, cudaStream_t s, int* nl) {
+  // x pass
+  {
+    const FftPlan1D pl = make_fft_plan(d.Lx);
+    const int ppb = pick_ppb(d.Lx);
+    const int64_t nrows = (int64_t)C * d.nz * d.ny;
+    const int64_t npairs = (nrows + 1) / 2;
+    const size_t smem = 2 * (size_t)ppb * d.Lx * sizeof(cpx<T>);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(r2c_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    r2c_rows_kernel<T><<<(int)((npairs + ppb - 1) / ppb), FFT_THREADS, smem, s>>>(in, spec, d, C, pl,
+                                                                                 (const cpx<T>*)tw.x, ppb);
+    ++*nl;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // y pass over (c, z < nz): rows y >= ny are zero
+  cudaError_t e = cols<T>(spec, d.hx, d.hx, (int64_t)d.Ly * d.hx, d.nz, d.Kh, C, d.ny, d.Ly, -1, d.Ly,
+                          (const cpx<T>*)tw.y, s);
+  ++*nl;
+  if (e != cudaSuccess) return e;
+  // z pass over c: planes z >= nz are zero
+  e = cols<T>(spec, (int64_t)d.Ly * d.hx, (int)((int64_t)d.Ly * d.hx), 0, 1, d.Kh, C, d.nz, d.Lz, -1, d.Lz,
+              (const cpx<T>*)tw.z, s);
+  ++*nl;
+  return e;
+}
+
+template <typename T>
+cudaError_t inverse(cpx<T>* spec, T* out, const Dims& d, int C, const FftTw& tw, cudaStream_t s, int* nl) {
+  // z pass: only planes z < nz are needed afterwards
+  cudaError_t e = cols<T>(spec, (int64_t)d.Ly * d.hx, (int)((int64_t)d.Ly * d.hx), 0, 1, d.Kh, C, d.Lz, d.nz, +1,
+                          d.Lz, (const cpx<T>*)tw.z, s);
+  ++*nl;
+  if (e != cudaSuccess) return e;
+  // y pass over (c, z < nz): only rows y < ny needed
+  e = cols<T>(spec, d.hx, d.hx, (int64_t)d.Ly * d.hx, d.nz, d.Kh, C, d.Ly, d.ny, +1, d.Ly, (const cpx<T>*)tw.y, s);
+  ++*nl;
+  if (e != cudaSuccess) return e;
+  const FftPlan1D pl = make_fft_plan(d.Lx);
+  const int ppb = pick_ppb(d.Lx);
+  const int64_t nrows = (int64_t)C * d.nz * d.ny;
+  const int64_t npairs = (nrows + 1) / 2;
+  const size_t smem = 2 * (size_t)ppb * d.Lx * sizeof(cpx<T>);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(c2r_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  c2r_rows_kernel<T><<<(int)((npairs + ppb - 1) / ppb), FFT_THREADS, smem, s>>>(spec, out, d, C, pl,
+                                                                               (const cpx<T>*)tw.x, ppb);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fft_forward(bool fp64, const void* in, void* spec, const Dims& d, int C, const FftTw& tw,
+                               cudaStream_t s, int* nl) {
+  return fp64 ? forward<double>((const double*)in, (cpx<double>*)spec, d, C, tw, s, nl)
+              : forward<float>((const float*)in, (cpx<float>*)spec, d, C, tw, s, nl);
+}
+
+cudaError_t launch_fft_inverse(bool fp64, void* spec, void* out, const Dims& d, int C, const FftTw& tw,
+                               cudaStream_t s, int* nl) {
+  return fp64 ? inverse<double>((cpx<double>*)spec, (double*)out, d, C, tw, s, nl)
+              : inverse<float>((cpx<float>*)spec, (float*)out, d, C, tw, s, nl);
+}
+
+cudaError_t launch_twiddles(bool fp64, int L, void* tw, cudaStream_t s) {
+  if (fp64)
+    twiddle_kernel<double><<<(L + 255) / 256, 256, 0, s>>>(L, (cpx<double>*)tw);
+  else
+    twiddle_kernel<float><<<(L + 255) / 256, 256, 0, s>>>(L, (cpx<float>*)tw);
+  return cudaGetLastError();
+}
+
+}  // namespace pmmm

@@ -1,0 +1,132 @@
+// Internal declarations of the PMMM GPU library: plan state, geometry and the
+// launchers of every kernel.  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "pmmm.h"
+
+namespace pmmm {
+
+// Mesh and transform geometry.  Physical cells nx*ny*nz; transforms of
+// Lx*Ly*Lz points (L = n periodic, L = 2n open, App. C); r2c half spectrum
+// along x with hx = Lx/2 + 1 points.
+struct Dims {
+  int nx, ny, nz;
+  int Lx, Ly, Lz;
+  int hx;
+  int64_t K;   // nx*ny*nz
+  int64_t Kt;  // Lx*Ly*Lz
+  int64_t Kh;  // Lz*Ly*hx
+};
+
+// Physical constants of one plan, in the units the kernels use.  Lengths on
+// the device are in units of hs (one scalar cell size); cs[a] = h_a / hs.
+struct Geo {
+  double lo[3], len[3], inv[3];  // binning: inv = n / len
+  double h[3];                   // cell sizes
+  double hs;                     // length unit of the device arithmetic
+  double cs[3];                  // h / hs
+  double V;                      // box volume
+  double alpha;                  // Ewald splitting parameter (physical)
+  double sign;
+  int n[3];
+  int periodic;
+  int c;
+};
+
+enum ErrBits { ERRBIT_OUT_OF_BOX = 1, ERRBIT_NONFINITE = 2, ERRBIT_TIMEOUT = 4 };
+
+// Device error flag helpers
+__device__ __forceinline__ void set_err(int* err, int bit) { atomicOr(err, bit); }
+
+// ---------------------------------------------------------------- sort.cu
+struct SortWork {
+  uint32_t *keys0, *keys1, *vals0, *vals1;
+  uint32_t* hist;    // [256 * ntiles_max]
+  uint32_t* chunks;  // [scan chunk sums]
+  int64_t cap;
+};
+int sort_tiles(int64_t n);
+size_t sort_hist_entries(int64_t n);
+size_t sort_chunk_entries(int64_t n);
+// Bins the particles (FP64 formula) and sorts them stably by cell.
+// Result: sorted keys in *keys_out, original indices in *vals_out.
+cudaError_t launch_bin(const void* pos, bool pos_fp64, int64_t n, const Geo& g, uint32_t* keys, int* err,
+                       cudaStream_t s, int* nlaunch);
+cudaError_t launch_radix_sort(SortWork& w, int64_t n, int key_bits, uint32_t** keys_out, uint32_t** vals_out,
+                              cudaStream_t s, int* nlaunch);
+cudaError_t launch_cell_bounds(const uint32_t* keys, int64_t n, int64_t K, int* cell_start, cudaStream_t s,
+                               int* nlaunch);
+// Sorted particle records (u_x, u_y, u_z, q): position relative to the cell
+// centre in units of hs, and the charge.
+cudaError_t launch_gather(const void* pos, const void* q, bool fp64, const uint32_t* keys, const uint32_t* vals,
+                          int64_t n, const Geo& g, void* part, cudaStream_t s, int* nlaunch);
+
+// ---------------------------------------------------------------- p2m_l2p.cu
+cudaError_t launch_p2m(int p, bool fp64, const void* part, const int* cell_start, int64_t K, void* M,
+                       double* cellq, double* celld, cudaStream_t s, int* nlaunch);
+struct CorrParams {
+  double hs, alpha, V;
+  int periodic;
+};
+cudaError_t launch_l2p(int p, bool fp64, const void* part, const uint32_t* keys, int64_t n, const void* L,
+                       int64_t K, const double* corr, const double* cellq, CorrParams cp, void* far,
+                       cudaStream_t s, int* nlaunch);
+
+// ---------------------------------------------------------------- fft.cu
+struct FftTw {
+  void* x;  // twiddles exp(-2 pi i t / L) for t < L, per axis
+  void* y;
+  void* z;
+};
+// Forward: real channels [C][nz][ny][nx] -> half spectra [C][Lz][Ly][hx].
+cudaError_t launch_fft_forward(bool fp64, const void* in, void* spec, const Dims& d, int C, const FftTw& tw,
+                               cudaStream_t s, int* nlaunch);
+// Inverse (unnormalised): half spectra -> real channels [C][nz][ny][nx] (physical part).
+cudaError_t launch_fft_inverse(bool fp64, void* spec, void* out, const Dims& d, int C, const FftTw& tw,
+                               cudaStream_t s, int* nlaunch);
+cudaError_t launch_twiddles(bool fp64, int L, void* tw, cudaStream_t s);
+
+// ---------------------------------------------------------------- m2l.cu
+cudaError_t launch_m2l(int p, bool fp64, const void* Mt, const void* Gt, void* Lt, int64_t Kh, cudaStream_t s,
+                       int* nlaunch);
+
+// ---------------------------------------------------------------- green.cu
+// Builds the real-space Green components G[s][Kt] (FP64, units of hs), s < (2p+1)^2.
+cudaError_t launch_green_open(double* G, const Dims& d, int p, int c, const double cs[3], cudaStream_t st);
+cudaError_t launch_green_periodic(double* G, const Dims& d, int p, int c, const double cs[3], double alpha_s,
+                                  int nmax, cudaStream_t st);
+// spectrum (FP64, [CG][Kh]) scaled by 1/Kt -> T
+cudaError_t launch_green_finish(const void* specd, void* out, bool fp64, int64_t count, double scale,
+                                cudaStream_t st);
+
+// ---------------------------------------------------------------- pp.cu
+struct PPParams {
+  int n[3];
+  int c;
+  int periodic;
+  double cs[3];
+  double hs;
+  double sign;
+};
+// Near field over the (2c+1)^3 cells plus the far field from `far`, written in
+// the caller's order to phi / force, with per-cell energy and force partials.
+cudaError_t launch_pp(bool fp64, const void* part, const uint32_t* vals, const int* cell_start, int64_t K,
+                      const void* far, PPParams pp, void* phi, void* force, double* epart, cudaStream_t s,
+                      int* nlaunch);
+
+// ---------------------------------------------------------------- reduce.cu
+// Sums per-cell FP64 quantities and builds the periodic correction terms:
+// corr[0] = c0 (potential constant), corr[1..3] = c1 (linear term), corr[4] = qfac,
+// corr[8..12] = raw sums (Q, sum q u_x, sum q u_y, sum q u_z, sum q |u|^2) in hs units.
+cudaError_t launch_corrections(const double* cellq, const double* celld, int64_t K, double hs, double V,
+                               double* partial, double* corr, cudaStream_t s, int* nlaunch);
+// energy[0] = sum of epart[cell*4 + 0], energy[1..3] = net force
+cudaError_t launch_energy(const double* epart, int64_t K, double* partial, double* energy, cudaStream_t s,
+                          int* nlaunch);
+cudaError_t launch_to_physical(bool fp64, const void* X, double* out, int p, int64_t K, double hs, int power_shift,
+                               cudaStream_t s);
+
+}  // namespace pmmm

@@ -1,0 +1,158 @@
+// P2M (Eq. P2M) and L2P with the order-one gradient (Eqs. L2P, L2L, phigrad).
+//
+// Device units: positions relative to the cell centre in units of hs, so the
+// moments computed here are M'_l = M_l / hs^l and the locals read are
+// L'_l = hs^(l+1) L_l; the physical potential is phi = phi' / hs and the
+// gradient grad' / hs^2.
+#include "harmonics.cuh"
+#include "internal.cuh"
+#include "translations.cuh"
+
+namespace pmmm {
+
+namespace {
+
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = double4; };
+
+// One warp per cell: each lane accumulates q R(r_M - r_i) = q R(-u) of its
+// particles into (p+1)^2 registers, then a butterfly reduction over the warp.
+// Also the FP64 per-cell sums used by the periodic corrections:
+// cellq = sum q, celld = (sum q u_x, sum q u_y, sum q u_z, sum q |u|^2).
+template <int P, typename T>
+__global__ void __launch_bounds__(256) p2m_kernel(const T* __restrict__ part, const int* __restrict__ cs, int64_t K,
+                                                  T* __restrict__ M, double* __restrict__ cellq,
+                                                  double* __restrict__ celld) {
+  constexpr int C = (P + 1) * (P + 1);
+  const int lane = threadIdx.x & 31;
+  const int64_t cell = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (cell >= K) return;
+  const int beg = cs[cell], end = cs[cell + 1];
+  T acc[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) acc[c] = T(0);
+  double sq = 0, sx = 0, sy = 0, sz = 0, sr = 0;
+  for (int i = beg + lane; i < end; i += 32) {
+    const typename V4<T>::type r = reinterpret_cast<const typename V4<T>::type*>(part)[i];
+    T R[C];
+    regular_real<P, T>(-r.x, -r.y, -r.z, R);
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] += r.w * R[c];
+    const double q = (double)r.w, ux = (double)r.x, uy = (double)r.y, uz = (double)r.z;
+    sq += q;
+    sx += q * ux;
+    sy += q * uy;
+    sz += q * uz;
+    sr += q * (ux * ux + uy * uy + uz * uz);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+  }
+#pragma unroll
+  for (int c = 0; c < C; ++c)
+    if ((c & 31) == lane) M[(int64_t)c * K + cell] = acc[c];
+  if (lane == 0) {
+    cellq[cell] = sq;
+    celld[cell] = sx;
+    celld[K + cell] = sy;
+    celld[2 * K + cell] = sz;
+    celld[3 * K + cell] = sr;
+  }
+}
+
+// One thread per sorted particle.  Far-field potential and gradient in
+// physical units, with the periodic corrections of App. B.3:
+//   phi  += c0 + c1 . r_rel + qfac (|r_rel|^2 - 3/(2 alpha^2)) - 2 alpha/sqrt(pi) Q_cell
+//   grad += c1 + 2 qfac r_rel
+// (c0 = 2pi/(3V) sum q|r_rel|^2, c1 = -4pi/(3V) sum q r_rel, qfac = 2pi/(3V) Q).
+template <int P, typename T>
+__global__ void __launch_bounds__(128) l2p_kernel(const T* __restrict__ part, const uint32_t* __restrict__ keys,
+                                                  int64_t n, const T* __restrict__ L, int64_t K,
+                                                  const double* __restrict__ corr, const double* __restrict__ cellq,
+                                                  CorrParams cp, T* __restrict__ far) {
+  constexpr int C = (P + 1) * (P + 1);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const typename V4<T>::type r = reinterpret_cast<const typename V4<T>::type*>(part)[i];
+  const int64_t cell = keys[i];
+  T R[C];
+  regular_real<P, T>(r.x, r.y, r.z, R);
+  T f, gx, gy, gz;
+  l2p_real<P, T>([&](int c) { return __ldg(L + (int64_t)c * K + cell); }, R, f, gx, gy, gz);
+  const double ih = 1.0 / cp.hs;
+  double phi = (double)f * ih;
+  double g[3] = {(double)gx * ih * ih, (double)gy * ih * ih, (double)gz * ih * ih};
+  if (cp.periodic) {
+    const double rel[3] = {(double)r.x * cp.hs, (double)r.y * cp.hs, (double)r.z * cp.hs};
+    const double rr = rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2];
+    phi += corr[0] + corr[1] * rel[0] + corr[2] * rel[1] + corr[3] * rel[2] +
+           corr[4] * (rr - 1.5 / (cp.alpha * cp.alpha)) - 2.0 * cp.alpha * 0.56418958354775628695 * cellq[cell];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[a] += corr[1 + a] + 2.0 * corr[4] * rel[a];
+  }
+  typename V4<T>::type o;
+  o.x = (T)phi;
+  o.y = (T)g[0];
+  o.z = (T)g[1];
+  o.w = (T)g[2];
+  reinterpret_cast<typename V4<T>::type*>(far)[i] = o;
+}
+
+template <int P, typename T>
+cudaError_t p2m_run(const void* part, const int* cs, int64_t K, void* M, double* cq, double* cd, cudaStream_t s) {
+  const int blocks = (int)((K + 7) / 8);
+  p2m_kernel<P, T><<<blocks, 256, 0, s>>>((const T*)part, cs, K, (T*)M, cq, cd);
+  return cudaGetLastError();
+}
+
+template <int P, typename T>
+cudaError_t l2p_run(const void* part, const uint32_t* keys, int64_t n, const void* L, int64_t K, const double* corr,
+                    const double* cq, CorrParams cp, void* far, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  l2p_kernel<P, T><<<(int)((n + 127) / 128), 128, 0, s>>>((const T*)part, keys, n, (const T*)L, K, corr, cq, cp,
+                                                          (T*)far);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t p2m_dispatch(int p, bool fp64, const void* part, const int* cs, int64_t K, void* M, double* cq,
+                         double* cd, cudaStream_t s) {
+  if (p == P)
+    return fp64 ? p2m_run<P, double>(part, cs, K, M, cq, cd, s) : p2m_run<P, float>(part, cs, K, M, cq, cd, s);
+  if constexpr (P < PMMM_PMAX) return p2m_dispatch<P + 1>(p, fp64, part, cs, K, M, cq, cd, s);
+  return cudaErrorInvalidValue;
+}
+
+template <int P>
+cudaError_t l2p_dispatch(int p, bool fp64, const void* part, const uint32_t* keys, int64_t n, const void* L,
+                         int64_t K, const double* corr, const double* cq, CorrParams cp, void* far, cudaStream_t s) {
+  if (p == P)
+    return fp64 ? l2p_run<P, double>(part, keys, n, L, K, corr, cq, cp, far, s)
+                : l2p_run<P, float>(part, keys, n, L, K, corr, cq, cp, far, s);
+  if constexpr (P < PMMM_PMAX) return l2p_dispatch<P + 1>(p, fp64, part, keys, n, L, K, corr, cq, cp, far, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_p2m(int p, bool fp64, const void* part, const int* cell_start, int64_t K, void* M, double* cellq,
+                       double* celld, cudaStream_t s, int* nl) {
+  ++*nl;
+  return p2m_dispatch<0>(p, fp64, part, cell_start, K, M, cellq, celld, s);
+}
+
+cudaError_t launch_l2p(int p, bool fp64, const void* part, const uint32_t* keys, int64_t n, const void* L, int64_t K,
+                       const double* corr, const double* cellq, CorrParams cp, void* far, cudaStream_t s, int* nl) {
+  if (n > 0) ++*nl;
+  return l2p_dispatch<0>(p, fp64, part, keys, n, L, K, corr, cellq, cp, far, s);
+}
+
+}  // namespace pmmm

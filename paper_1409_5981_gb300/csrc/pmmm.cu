@@ -1,0 +1,589 @@
+// C ABI of the PMMM GPU library (include/pmmm.h): plan life cycle, the full
+// force evaluation and diagnostics.  Every step of the evaluation is a kernel
+// of this library queued on the plan's stream; there is no host fallback.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace pmmm;
+
+namespace {
+
+enum Stage { ST_SORT = 0, ST_P2M, ST_FFT_FWD, ST_M2L, ST_FFT_INV, ST_L2P, ST_PP, ST_REDUCE, ST_COUNT };
+const char* kStageNames[ST_COUNT] = {"bin_sort", "p2m", "fft_forward", "m2l", "fft_inverse", "l2p", "near_field",
+                                     "reduce"};
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int map_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return PMMM_OK;
+  if (e == cudaErrorMemoryAllocation) return PMMM_ERR_OOM;
+  return PMMM_ERR_CUDA;
+}
+
+}  // namespace
+
+struct pmmm_plan {
+  pmmm_config cfg;
+  cudaStream_t stream = nullptr;
+  int p = 0, C = 0, CG = 0;
+  bool fp64 = true;
+  Dims d{};
+  Geo g{};
+  int nmax = 5;
+  size_t tsize = 8;  // sizeof(T)
+  // mesh workspace
+  void *M = nullptr, *L = nullptr, *specM = nullptr, *specL = nullptr, *G = nullptr;
+  void *twx = nullptr, *twy = nullptr, *twz = nullptr;
+  double* cellsum = nullptr;  // [5][K]: sum q, sum q u_x, sum q u_y, sum q u_z, sum q |u|^2
+  int* cs = nullptr;          // [K+1]
+  double* corr = nullptr;     // [16]
+  double* partial = nullptr;  // [256 * 8]
+  double* epart = nullptr;    // [K][4]
+  double* energy = nullptr;   // [4]
+  int* err = nullptr;
+  // particle workspace
+  int64_t cap = 0;
+  SortWork sw{};
+  void *part = nullptr, *far = nullptr;
+  // staging for pmmm_compute_host
+  int64_t hcap = 0;
+  void *hpos = nullptr, *hq = nullptr, *hphi = nullptr, *hforce = nullptr;
+  // last evaluation
+  int64_t n_last = 0;
+  uint32_t *keys_sorted = nullptr, *vals_sorted = nullptr;
+  int launches = 0;
+  size_t ws_bytes = 0;
+  bool timing = false, timed = false;
+  cudaEvent_t ev[ST_COUNT + 1] = {};
+};
+
+namespace {
+
+cudaError_t dalloc(pmmm_plan* pl, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e == cudaSuccess) pl->ws_bytes += bytes;
+  return e;
+}
+
+void dfree(void*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_particles(pmmm_plan* pl) {
+  void* v;
+  v = pl->sw.keys0; dfree(v);
+  v = pl->sw.keys1; dfree(v);
+  v = pl->sw.vals0; dfree(v);
+  v = pl->sw.vals1; dfree(v);
+  v = pl->sw.hist; dfree(v);
+  v = pl->sw.chunks; dfree(v);
+  pl->sw = SortWork{};
+  dfree(pl->part);
+  dfree(pl->far);
+  pl->cap = 0;
+}
+
+void free_all(pmmm_plan* pl) {
+  if (!pl) return;
+  free_particles(pl);
+  dfree(pl->M); dfree(pl->L); dfree(pl->specM); dfree(pl->specL); dfree(pl->G);
+  dfree(pl->twx); dfree(pl->twy); dfree(pl->twz);
+  void* v;
+  v = pl->cellsum; dfree(v); pl->cellsum = nullptr;
+  v = pl->cs; dfree(v); pl->cs = nullptr;
+  v = pl->corr; dfree(v); pl->corr = nullptr;
+  v = pl->partial; dfree(v); pl->partial = nullptr;
+  v = pl->epart; dfree(v); pl->epart = nullptr;
+  v = pl->energy; dfree(v); pl->energy = nullptr;
+  v = pl->err; dfree(v); pl->err = nullptr;
+  dfree(pl->hpos); dfree(pl->hq); dfree(pl->hphi); dfree(pl->hforce);
+  for (int i = 0; i <= ST_COUNT; ++i)
+    if (pl->ev[i]) cudaEventDestroy(pl->ev[i]);
+}
+
+int validate(const pmmm_config* c) {
+  if (!c) return PMMM_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a) {
+    if (!(c->box_len[a] > 0.0) || !isfinite(c->box_len[a]) || !isfinite(c->box_lo[a])) return PMMM_ERR_INVALID_ARG;
+    if (c->mesh[a] < 1) return PMMM_ERR_INVALID_ARG;
+  }
+  if (c->boundary != PMMM_OPEN && c->boundary != PMMM_PERIODIC) return PMMM_ERR_INVALID_ARG;
+  if (c->precision < PMMM_FP64 || c->precision > PMMM_FP32_SPLITBF16_M2L) return PMMM_ERR_INVALID_ARG;
+  if (c->p < 0 || c->cutoff < 1) return PMMM_ERR_INVALID_ARG;
+  if (!(c->sign == 1.0 || c->sign == -1.0)) return PMMM_ERR_INVALID_ARG;
+  if (c->ewald_alpha < 0.0 || !isfinite(c->ewald_alpha) || c->ewald_nmax < 0) return PMMM_ERR_INVALID_ARG;
+  if (c->p > PMMM_PMAX || c->cutoff > 2) return PMMM_ERR_UNSUPPORTED;
+  for (int a = 0; a < 3; ++a) {
+    if (!pow2(c->mesh[a])) return PMMM_ERR_UNSUPPORTED;
+    if (c->boundary == PMMM_PERIODIC) {
+      if (c->mesh[a] < 2 * c->cutoff + 1 || c->mesh[a] > 512) return PMMM_ERR_UNSUPPORTED;
+    } else if (c->mesh[a] > 256) {
+      return PMMM_ERR_UNSUPPORTED;
+    }
+  }
+  const int64_t K = (int64_t)c->mesh[0] * c->mesh[1] * c->mesh[2];
+  if (K > (int64_t)1 << 28) return PMMM_ERR_UNSUPPORTED;
+  return PMMM_OK;
+}
+
+int ensure_particles(pmmm_plan* pl, int64_t n) {
+  if (n <= pl->cap) return PMMM_OK;
+  cudaStreamSynchronize(pl->stream);
+  free_particles(pl);
+  const int64_t cap = n < 1024 ? 1024 : n;
+  cudaError_t e = cudaSuccess;
+  void* v;
+#define ALLOC(field, type, count)                       \
+  e = dalloc(pl, &v, sizeof(type) * (size_t)(count));   \
+  if (e != cudaSuccess) {                               \
+    free_particles(pl);                                 \
+    return map_cuda(e);                                 \
+  }                                                     \
+  field = (type*)v;
+  ALLOC(pl->sw.keys0, uint32_t, cap);
+  ALLOC(pl->sw.keys1, uint32_t, cap);
+  ALLOC(pl->sw.vals0, uint32_t, cap);
+  ALLOC(pl->sw.vals1, uint32_t, cap);
+  ALLOC(pl->sw.hist, uint32_t, sort_hist_entries(cap));
+  ALLOC(pl->sw.chunks, uint32_t, sort_chunk_entries(cap));
+#undef ALLOC
+  e = dalloc(pl, &pl->part, 4 * pl->tsize * (size_t)cap);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->far, 4 * pl->tsize * (size_t)cap);
+  if (e != cudaSuccess) {
+    free_particles(pl);
+    return map_cuda(e);
+  }
+  pl->sw.cap = cap;
+  pl->cap = cap;
+  return PMMM_OK;
+}
+
+int build_green(pmmm_plan* pl) {
+  const Dims& d = pl->d;
+  // full-grid geometry for the FFT of the kernel components
+  Dims gd = d;
+  gd.nx = d.Lx;
+  gd.ny = d.Ly;
+  gd.nz = d.Lz;
+  gd.K = d.Kt;
+  void *Gd = nullptr, *Sd = nullptr, *t64[3] = {nullptr, nullptr, nullptr};
+  cudaError_t e = cudaMalloc(&Gd, sizeof(double) * (size_t)pl->CG * d.Kt);
+  if (e == cudaSuccess) e = cudaMalloc(&Sd, sizeof(double) * 2 * (size_t)pl->CG * d.Kh);
+  const int Ls[3] = {d.Lx, d.Ly, d.Lz};
+  for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+    e = cudaMalloc(&t64[a], sizeof(double) * 2 * Ls[a]);
+    if (e == cudaSuccess) e = launch_twiddles(true, Ls[a], t64[a], pl->stream);
+  }
+  if (e == cudaSuccess) {
+    if (pl->g.periodic)
+      e = launch_green_periodic((double*)Gd, d, pl->p, pl->g.c, pl->g.cs, pl->g.alpha * pl->g.hs, pl->nmax,
+                                pl->stream);
+    else
+      e = launch_green_open((double*)Gd, d, pl->p, pl->g.c, pl->g.cs, pl->stream);
+  }
+  int nl = 0;
+  if (e == cudaSuccess) {
+    FftTw tw{t64[0], t64[1], t64[2]};
+    e = launch_fft_forward(true, Gd, Sd, gd, pl->CG, tw, pl->stream, &nl);
+  }
+  if (e == cudaSuccess)
+    e = launch_green_finish(Sd, pl->G, pl->fp64, (int64_t)pl->CG * d.Kh, 1.0 / (double)d.Kt, pl->stream);
+  cudaError_t e2 = cudaStreamSynchronize(pl->stream);
+  if (e == cudaSuccess) e = e2;
+  if (Gd) cudaFree(Gd);
+  if (Sd) cudaFree(Sd);
+  for (int a = 0; a < 3; ++a)
+    if (t64[a]) cudaFree(t64[a]);
+  return map_cuda(e);
+}
+
+int read_device_status(pmmm_plan* pl) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, pl->err, sizeof(int), cudaMemcpyDeviceToHost, pl->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
+  if (e != cudaSuccess) return map_cuda(e);
+  if (h) cudaMemsetAsync(pl->err, 0, sizeof(int), pl->stream);
+  if (h & ERRBIT_TIMEOUT) return PMMM_ERR_TIMEOUT;
+  if (h & ERRBIT_NONFINITE) return PMMM_ERR_NONFINITE_INPUT;
+  if (h & ERRBIT_OUT_OF_BOX) return PMMM_ERR_OUT_OF_BOX;
+  return PMMM_OK;
+}
+
+void mark(pmmm_plan* pl, int st) {
+  if (pl->timing) cudaEventRecord(pl->ev[st], pl->stream);
+}
+
+int run(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, void* force) {
+  int rc = ensure_particles(pl, n);
+  if (rc != PMMM_OK) return rc;
+  cudaStream_t s = pl->stream;
+  int nl = 0;
+  cudaError_t e = cudaSuccess;
+  const bool fp64 = pl->fp64;
+  const int64_t K = pl->d.K;
+#define CK(x)                    \
+  do {                           \
+    e = (x);                     \
+    if (e != cudaSuccess) goto done; \
+  } while (0)
+  mark(pl, ST_SORT);
+  {
+    int key_bits = 0;
+    while (((int64_t)1 << key_bits) < K) ++key_bits;
+    CK(launch_bin(pos, fp64, n, pl->g, pl->sw.keys0, pl->err, s, &nl));
+    CK(launch_radix_sort(pl->sw, n, key_bits, &pl->keys_sorted, &pl->vals_sorted, s, &nl));
+    CK(launch_cell_bounds(pl->keys_sorted, n, K, pl->cs, s, &nl));
+    CK(launch_gather(pos, q, fp64, pl->keys_sorted, pl->vals_sorted, n, pl->g, pl->part, s, &nl));
+  }
+  mark(pl, ST_P2M);
+  CK(launch_p2m(pl->p, fp64, pl->part, pl->cs, K, pl->M, pl->cellsum, pl->cellsum + K, s, &nl));
+  mark(pl, ST_FFT_FWD);
+  {
+    FftTw tw{pl->twx, pl->twy, pl->twz};
+    CK(launch_fft_forward(fp64, pl->M, pl->specM, pl->d, pl->C, tw, s, &nl));
+    mark(pl, ST_M2L);
+    CK(launch_m2l(pl->p, fp64, pl->specM, pl->G, pl->specL, pl->d.Kh, s, &nl));
+    mark(pl, ST_FFT_INV);
+    CK(launch_fft_inverse(fp64, pl->specL, pl->L, pl->d, pl->C, tw, s, &nl));
+  }
+  mark(pl, ST_L2P);
+  if (pl->g.periodic)
+    CK(launch_corrections(pl->cellsum, pl->cellsum + K, K, pl->g.hs, pl->g.V, pl->partial, pl->corr, s, &nl));
+  {
+    CorrParams cp{pl->g.hs, pl->g.alpha, pl->g.V, pl->g.periodic};
+    CK(launch_l2p(pl->p, fp64, pl->part, pl->keys_sorted, n, pl->L, K, pl->corr, pl->cellsum, cp, pl->far, s, &nl));
+  }
+  mark(pl, ST_PP);
+  {
+    PPParams pp;
+    for (int a = 0; a < 3; ++a) {
+      pp.n[a] = pl->g.n[a];
+      pp.cs[a] = pl->g.cs[a];
+    }
+    pp.c = pl->g.c;
+    pp.periodic = pl->g.periodic;
+    pp.hs = pl->g.hs;
+    pp.sign = pl->g.sign;
+    CK(launch_pp(fp64, pl->part, pl->vals_sorted, pl->cs, K, pl->far, pp, phi, force, pl->epart, s, &nl));
+  }
+  mark(pl, ST_REDUCE);
+  CK(launch_energy(pl->epart, K, pl->partial + 256 * 5, pl->energy, s, &nl));
+  mark(pl, ST_COUNT);
+#undef CK
+done:
+  pl->launches = nl;
+  pl->n_last = n;
+  pl->timed = pl->timing && e == cudaSuccess;
+  return map_cuda(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pmmm_abi_version(void) { return PMMM_ABI_VERSION; }
+
+void pmmm_config_init(pmmm_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  for (int a = 0; a < 3; ++a) {
+    c->box_lo[a] = 0.0;
+    c->box_len[a] = 1.0;
+    c->mesh[a] = 8;
+  }
+  c->p = 4;
+  c->cutoff = 1;
+  c->boundary = PMMM_OPEN;
+  c->precision = PMMM_FP64;
+  c->sign = 1.0;
+  c->ewald_alpha = 0.0;
+  c->ewald_nmax = 0;
+}
+
+const char* pmmm_strerror(int s) {
+  switch (s) {
+    case PMMM_OK: return "ok";
+    case PMMM_ERR_INVALID_ARG: return "invalid argument";
+    case PMMM_ERR_UNSUPPORTED: return "unsupported configuration";
+    case PMMM_ERR_OUT_OF_BOX: return "particle outside the open-boundary box";
+    case PMMM_ERR_NONFINITE_INPUT: return "non-finite particle coordinate";
+    case PMMM_ERR_CUDA: return "CUDA error";
+    case PMMM_ERR_TIMEOUT: return "device-side wait timed out";
+    case PMMM_ERR_OOM: return "device out of memory";
+    default: return "unknown status";
+  }
+}
+
+const char* pmmm_stage_name(int i) { return (i >= 0 && i < ST_COUNT) ? kStageNames[i] : nullptr; }
+
+int pmmm_plan_create(const pmmm_config* cfg, void* stream, pmmm_plan** out) {
+  if (!out) return PMMM_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc != PMMM_OK) return rc;
+  pmmm_plan* pl = new (std::nothrow) pmmm_plan();
+  if (!pl) return PMMM_ERR_OOM;
+  pl->cfg = *cfg;
+  pl->stream = (cudaStream_t)stream;
+  pl->p = cfg->p;
+  pl->C = (cfg->p + 1) * (cfg->p + 1);
+  pl->CG = (2 * cfg->p + 1) * (2 * cfg->p + 1);
+  pl->fp64 = cfg->precision == PMMM_FP64;
+  pl->tsize = pl->fp64 ? sizeof(double) : sizeof(float);
+  const bool per = cfg->boundary == PMMM_PERIODIC;
+  Dims& d = pl->d;
+  d.nx = cfg->mesh[0];
+  d.ny = cfg->mesh[1];
+  d.nz = cfg->mesh[2];
+  d.Lx = per ? d.nx : 2 * d.nx;
+  d.Ly = per ? d.ny : 2 * d.ny;
+  d.Lz = per ? d.nz : 2 * d.nz;
+  d.hx = d.Lx / 2 + 1;
+  d.K = (int64_t)d.nx * d.ny * d.nz;
+  d.Kt = (int64_t)d.Lx * d.Ly * d.Lz;
+  d.Kh = (int64_t)d.Lz * d.Ly * d.hx;
+  Geo& g = pl->g;
+  double hmin = 1e300;
+  for (int a = 0; a < 3; ++a) {
+    g.lo[a] = cfg->box_lo[a];
+    g.len[a] = cfg->box_len[a];
+    g.n[a] = cfg->mesh[a];
+    g.inv[a] = (double)cfg->mesh[a] / cfg->box_len[a];
+    g.h[a] = cfg->box_len[a] / cfg->mesh[a];
+    hmin = fmin(hmin, g.h[a]);
+  }
+  g.hs = (g.h[0] == g.h[1] && g.h[1] == g.h[2]) ? g.h[0] : cbrt(g.h[0] * g.h[1] * g.h[2]);
+  for (int a = 0; a < 3; ++a) g.cs[a] = g.h[a] / g.hs;
+  g.V = cfg->box_len[0] * cfg->box_len[1] * cfg->box_len[2];
+  g.alpha = cfg->ewald_alpha > 0.0 ? cfg->ewald_alpha
+                                   : 1.5 / fmin(cfg->box_len[0], fmin(cfg->box_len[1], cfg->box_len[2]));
+  g.sign = cfg->sign;
+  g.periodic = per ? 1 : 0;
+  g.c = cfg->cutoff;
+  pl->nmax = cfg->ewald_nmax > 0 ? cfg->ewald_nmax : 5;
+
+  cudaError_t e = cudaSuccess;
+  const size_t T = pl->tsize;
+  void* v;
+  e = dalloc(pl, &pl->M, T * pl->C * (size_t)d.K);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->L, T * pl->C * (size_t)d.K);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->specM, 2 * T * pl->C * (size_t)d.Kh);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->specL, 2 * T * pl->C * (size_t)d.Kh);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->G, 2 * T * pl->CG * (size_t)d.Kh);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->twx, 2 * T * d.Lx);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->twy, 2 * T * d.Ly);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->twz, 2 * T * d.Lz);
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 5 * (size_t)d.K); pl->cellsum = (double*)v; }
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(int) * (size_t)(d.K + 1)); pl->cs = (int*)v; }
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 16); pl->corr = (double*)v; }
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 256 * 16); pl->partial = (double*)v; }
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 4 * (size_t)d.K); pl->epart = (double*)v; }
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 4); pl->energy = (double*)v; }
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(int)); pl->err = (int*)v; }
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->err, 0, sizeof(int), pl->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->corr, 0, sizeof(double) * 16, pl->stream);
+  if (e == cudaSuccess) e = launch_twiddles(pl->fp64, d.Lx, pl->twx, pl->stream);
+  if (e == cudaSuccess) e = launch_twiddles(pl->fp64, d.Ly, pl->twy, pl->stream);
+  if (e == cudaSuccess) e = launch_twiddles(pl->fp64, d.Lz, pl->twz, pl->stream);
+  for (int i = 0; i <= ST_COUNT && e == cudaSuccess; ++i) e = cudaEventCreate(&pl->ev[i]);
+  if (e != cudaSuccess) {
+    rc = map_cuda(e);
+    free_all(pl);
+    delete pl;
+    return rc;
+  }
+  rc = build_green(pl);
+  if (rc != PMMM_OK) {
+    free_all(pl);
+    delete pl;
+    return rc;
+  }
+  *out = pl;
+  return PMMM_OK;
+}
+
+int pmmm_plan_destroy(pmmm_plan* pl) {
+  if (!pl) return PMMM_OK;
+  cudaStreamSynchronize(pl->stream);
+  free_all(pl);
+  delete pl;
+  return PMMM_OK;
+}
+
+int pmmm_plan_reserve(pmmm_plan* pl, int64_t n) {
+  if (!pl || n < 0 || n > INT32_MAX) return PMMM_ERR_INVALID_ARG;
+  return ensure_particles(pl, n);
+}
+
+int pmmm_compute(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, void* force, double* energy) {
+  if (!pl || n < 0 || n > INT32_MAX) return PMMM_ERR_INVALID_ARG;
+  if (n > 0 && (!pos || !q)) return PMMM_ERR_INVALID_ARG;
+  int rc = run(pl, n, pos, q, phi, force);
+  if (rc != PMMM_OK) return rc;
+  if (energy) {
+    double h[4];
+    cudaError_t e = cudaMemcpyAsync(h, pl->energy, sizeof(h), cudaMemcpyDeviceToHost, pl->stream);
+    if (e != cudaSuccess) return map_cuda(e);
+    rc = read_device_status(pl);
+    *energy = h[0];
+    return rc;
+  }
+  return PMMM_OK;
+}
+
+int pmmm_compute_host(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, void* force,
+                      double* energy) {
+  if (!pl || n < 0 || n > INT32_MAX) return PMMM_ERR_INVALID_ARG;
+  if (n > 0 && (!pos || !q)) return PMMM_ERR_INVALID_ARG;
+  const size_t T = pl->tsize;
+  if (n > pl->hcap) {
+    cudaStreamSynchronize(pl->stream);
+    dfree(pl->hpos); dfree(pl->hq); dfree(pl->hphi); dfree(pl->hforce);
+    pl->hcap = 0;
+    cudaError_t e = dalloc(pl, &pl->hpos, 3 * T * (size_t)n);
+    if (e == cudaSuccess) e = dalloc(pl, &pl->hq, T * (size_t)n);
+    if (e == cudaSuccess) e = dalloc(pl, &pl->hphi, T * (size_t)n);
+    if (e == cudaSuccess) e = dalloc(pl, &pl->hforce, 3 * T * (size_t)n);
+    if (e != cudaSuccess) return map_cuda(e);
+    pl->hcap = n;
+  }
+  cudaStream_t s = pl->stream;
+  cudaError_t e = cudaSuccess;
+  if (n > 0) {
+    e = cudaMemcpyAsync(pl->hpos, pos, 3 * T * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pl->hq, q, T * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return map_cuda(e);
+  }
+  int rc = run(pl, n, pl->hpos, pl->hq, phi ? pl->hphi : nullptr, force ? pl->hforce : nullptr);
+  if (rc != PMMM_OK) return rc;
+  double h[4] = {0, 0, 0, 0};
+  if (phi && n > 0) e = cudaMemcpyAsync(phi, pl->hphi, T * (size_t)n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && force && n > 0)
+    e = cudaMemcpyAsync(force, pl->hforce, 3 * T * (size_t)n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && energy) e = cudaMemcpyAsync(h, pl->energy, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return map_cuda(e);
+  rc = read_device_status(pl);
+  if (energy) *energy = h[0];
+  return rc;
+}
+
+int pmmm_plan_status(pmmm_plan* pl) {
+  if (!pl) return PMMM_ERR_INVALID_ARG;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return map_cuda(e);
+  return read_device_status(pl);
+}
+
+int pmmm_plan_export(pmmm_plan* pl, int what, void* dst, size_t bytes) {
+  if (!pl || !dst) return PMMM_ERR_INVALID_ARG;
+  const int64_t n = pl->n_last, K = pl->d.K;
+  cudaStream_t s = pl->stream;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return map_cuda(e);
+  switch (what) {
+    case PMMM_EXPORT_PERM:
+    case PMMM_EXPORT_SORTED_CELL: {
+      if (bytes != sizeof(int32_t) * (size_t)n) return PMMM_ERR_INVALID_ARG;
+      if (n == 0) return PMMM_OK;
+      const void* src = what == PMMM_EXPORT_PERM ? (const void*)pl->vals_sorted : (const void*)pl->keys_sorted;
+      e = cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+      break;
+    }
+    case PMMM_EXPORT_CELL_START:
+      if (bytes != sizeof(int32_t) * (size_t)(K + 1)) return PMMM_ERR_INVALID_ARG;
+      e = cudaMemcpy(dst, pl->cs, bytes, cudaMemcpyDeviceToHost);
+      break;
+    case PMMM_EXPORT_MULTIPOLE:
+    case PMMM_EXPORT_LOCAL: {
+      if (bytes != sizeof(double) * (size_t)pl->C * K) return PMMM_ERR_INVALID_ARG;
+      void* tmp = nullptr;
+      e = cudaMalloc(&tmp, bytes);
+      if (e != cudaSuccess) return map_cuda(e);
+      e = launch_to_physical(pl->fp64, what == PMMM_EXPORT_MULTIPOLE ? pl->M : pl->L, (double*)tmp, pl->p, K,
+                             pl->g.hs, what == PMMM_EXPORT_MULTIPOLE ? 0 : 1, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e == cudaSuccess) e = cudaMemcpy(dst, tmp, bytes, cudaMemcpyDeviceToHost);
+      cudaFree(tmp);
+      break;
+    }
+    case PMMM_EXPORT_CORR: {
+      if (bytes != sizeof(double) * 8) return PMMM_ERR_INVALID_ARG;
+      double c[16] = {0};
+      e = cudaMemcpy(c, pl->corr, sizeof(c), cudaMemcpyDeviceToHost);
+      double* o = (double*)dst;
+      const double hs = pl->g.hs;
+      o[0] = c[8];                    // Q
+      o[1] = -c[11] * hs;             // sum M_1^0 = -sum q z_rel
+      o[2] = 0.5 * c[9] * hs;         // Re sum M_1^1 = sum q x_rel / 2
+      o[3] = 0.5 * c[10] * hs;        // Im sum M_1^1 = sum q y_rel / 2
+      o[4] = c[12] * hs * hs;         // sum q |r_rel|^2
+      o[5] = pl->g.alpha;
+      o[6] = pl->g.V;
+      o[7] = 0.0;
+      break;
+    }
+    case PMMM_EXPORT_FAR: {
+      if (bytes != sizeof(double) * 4 * (size_t)n) return PMMM_ERR_INVALID_ARG;
+      if (n == 0) return PMMM_OK;
+      if (pl->fp64) {
+        e = cudaMemcpy(dst, pl->far, bytes, cudaMemcpyDeviceToHost);
+      } else {
+        std::vector<float> t((size_t)4 * n);
+        e = cudaMemcpy(t.data(), pl->far, sizeof(float) * 4 * (size_t)n, cudaMemcpyDeviceToHost);
+        for (size_t i = 0; i < t.size(); ++i) ((double*)dst)[i] = t[i];
+      }
+      break;
+    }
+    default:
+      return PMMM_ERR_INVALID_ARG;
+  }
+  return map_cuda(e);
+}
+
+int pmmm_plan_info(pmmm_plan* pl, int what, int64_t* value) {
+  if (!pl || !value) return PMMM_ERR_INVALID_ARG;
+  switch (what) {
+    case PMMM_INFO_K: *value = pl->d.K; break;
+    case PMMM_INFO_C: *value = pl->C; break;
+    case PMMM_INFO_CG: *value = pl->CG; break;
+    case PMMM_INFO_KH: *value = pl->d.Kh; break;
+    case PMMM_INFO_N: *value = pl->n_last; break;
+    case PMMM_INFO_WORKSPACE_BYTES: *value = (int64_t)pl->ws_bytes; break;
+    case PMMM_INFO_LAUNCHES: *value = pl->launches; break;
+    default: return PMMM_ERR_INVALID_ARG;
+  }
+  return PMMM_OK;
+}
+
+int pmmm_plan_set_timing(pmmm_plan* pl, int enable) {
+  if (!pl) return PMMM_ERR_INVALID_ARG;
+  pl->timing = enable != 0;
+  pl->timed = false;
+  return PMMM_OK;
+}
+
+int pmmm_plan_stage_times(pmmm_plan* pl, float* ms, int max_stages) {
+  if (!pl || (!ms && max_stages > 0)) return PMMM_ERR_INVALID_ARG;
+  if (!pl->timed) return 0;
+  cudaError_t e = cudaEventSynchronize(pl->ev[ST_COUNT]);
+  if (e != cudaSuccess) return map_cuda(e);
+  int k = 0;
+  for (int i = 0; i < ST_COUNT && k < max_stages; ++i, ++k) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, pl->ev[i], pl->ev[i + 1]);
+    ms[k] = t;
+  }
+  return k;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// FP64 global reductions: the periodic correction terms of App. B.3 and the
+// energy / net force.  Both are two-level tree reductions with a fixed
+// assignment of cells to threads, so the results do not depend on scheduling.
+#include "internal.cuh"
+
+namespace pmmm {
+
+namespace {
+
+constexpr int RD_THREADS = 256;
+constexpr int RD_BLOCKS = 256;
+constexpr double kPi = 3.14159265358979323846;
+
+// Sums NQ per-cell quantities, quantity q of cell i at src[q * qstride + i * istride].
+template <int NQ>
+__global__ void __launch_bounds__(RD_THREADS) reduce_partial_kernel(const double* __restrict__ src, int64_t K,
+                                                                    int64_t qstride, int64_t istride,
+                                                                    double* __restrict__ partial) {
+  __shared__ double sh[NQ][RD_THREADS];
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  const int64_t per = (K + gridDim.x - 1) / gridDim.x;
+  const int64_t beg = (int64_t)blockIdx.x * per, end = min(K, beg + per);
+  for (int64_t i = beg + threadIdx.x; i < end; i += RD_THREADS)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] += src[q * qstride + i * istride];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int w = RD_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < NQ) partial[blockIdx.x * NQ + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+template <int NQ>
+__device__ void reduce_final(const double* __restrict__ partial, int nb, double* out) {
+  __shared__ double sh[NQ][RD_THREADS];
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += RD_THREADS)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] += partial[b * NQ + q];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int w = RD_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < NQ) out[threadIdx.x] = sh[threadIdx.x][0];
+  __syncthreads();
+}
+
+// corr[0] = 2pi/(3V) sum q |r_rel|^2           (potential constant, App. B.3)
+// corr[1..3] = -4pi/(3V) sum q r_rel           (dipole term of Eq. phicorr)
+// corr[4] = 2pi/(3V) Q                         (charged-system factor)
+// corr[8..12] = Q, sum q u (3), sum q |u|^2 in units of hs
+__global__ void __launch_bounds__(RD_THREADS) corrections_kernel(const double* __restrict__ partial, int nb, double hs,
+                                                                 double V, double* __restrict__ corr) {
+  __shared__ double tot[5];
+  reduce_final<5>(partial, nb, tot);
+  if (threadIdx.x == 0) {
+    const double f = 2.0 * kPi / (3.0 * V);
+    const double Q = tot[0];
+    corr[0] = f * tot[4] * hs * hs;
+    corr[1] = -2.0 * f * tot[1] * hs;
+    corr[2] = -2.0 * f * tot[2] * hs;
+    corr[3] = -2.0 * f * tot[3] * hs;
+    corr[4] = f * Q;
+    for (int q = 0; q < 5; ++q) corr[8 + q] = tot[q];
+  }
+}
+
+__global__ void __launch_bounds__(RD_THREADS) energy_final_kernel(const double* __restrict__ partial, int nb,
+                                                                  double* __restrict__ energy) {
+  __shared__ double tot[4];
+  reduce_final<4>(partial, nb, tot);
+  if (threadIdx.x < 4) energy[threadIdx.x] = tot[threadIdx.x];
+}
+
+// channel c = sidx(l, m) of X (device units) times hs^(sh * l + off) -> FP64 out
+template <typename T>
+__global__ void to_physical_kernel(const T* __restrict__ X, double* __restrict__ out, int p, int64_t K, double hs,
+                                   int mode) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int C = (p + 1) * (p + 1);
+  if (i >= (int64_t)C * K) return;
+  const int c = (int)(i / K);
+  int l = 0;
+  while ((l + 1) * (l + 1) <= c) ++l;
+  // mode 0: multipoles M = M' hs^l ; mode 1: locals L = L' / hs^(l+1)
+  const double f = mode == 0 ? pow(hs, (double)l) : pow(hs, -(double)(l + 1));
+  out[i] = (double)X[i] * f;
+}
+
+}  // namespace
+
+cudaError_t launch_corrections(const double* cellq, const double* celld, int64_t K, double hs, double V,
+                               double* partial, double* corr, cudaStream_t s, int* nl) {
+  // quantity 0 = cellq, quantities 1..4 = celld[0..3]; celld follows cellq in memory
+  (void)celld;
+  reduce_partial_kernel<5><<<RD_BLOCKS, RD_THREADS, 0, s>>>(cellq, K, K, 1, partial);
+  corrections_kernel<<<1, RD_THREADS, 0, s>>>(partial, RD_BLOCKS, hs, V, corr);
+  *nl += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const double* epart, int64_t K, double* partial, double* energy, cudaStream_t s, int* nl) {
+  reduce_partial_kernel<4><<<RD_BLOCKS, RD_THREADS, 0, s>>>(epart, K, 1, 4, partial);
+  energy_final_kernel<<<1, RD_THREADS, 0, s>>>(partial, RD_BLOCKS, energy);
+  *nl += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_physical(bool fp64, const void* X, double* out, int p, int64_t K, double hs, int mode,
+                               cudaStream_t s) {
+  const int64_t n = (int64_t)(p + 1) * (p + 1) * K;
+  const unsigned b = (unsigned)((n + 255) / 256);
+  if (fp64)
+    to_physical_kernel<double><<<b, 256, 0, s>>>((const double*)X, out, p, K, hs, mode);
+  else
+    to_physical_kernel<float><<<b, 256, 0, s>>>((const float*)X, out, p, K, hs, mode);
+  return cudaGetLastError();
+}
+
+}  // namespace pmmm

@@ -1,0 +1,332 @@
+// Binning and stable counting sort of the particles by cell (Sec. 2.1: "for
+// each cell, the set of particles inside is known ... in an O(N) procedure").
+//
+// Cell index, in FP64 with every operation rounded (no contraction):
+//   t = x - lo;  periodic: t = t - len * floor(t / len), and t -= len if t >= len
+//   open: flag OUT_OF_BOX unless 0 <= t < len
+//   i = floor(t * (n / len)) clamped to [0, n-1];  id = ix + nx (iy + ny iz)
+// The sort is an LSD radix sort on the id (digits of <= 8 bits), stable in
+// every pass, so the particles of a cell keep their input order.
+#include "internal.cuh"
+
+namespace pmmm {
+
+namespace {
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 2048 keys per tile
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_CH = SCAN_THREADS * 4;  // entries per scan chunk
+
+__device__ __forceinline__ int bin_axis(double x, double lo, double len, double inv, int n, int periodic, int* err,
+                                        double* tout) {
+  if (!isfinite(x)) {
+    set_err(err, ERRBIT_NONFINITE);
+    *tout = 0.0;
+    return 0;
+  }
+  double t = __dsub_rn(x, lo);
+  if (periodic) {
+    const double qd = __ddiv_rn(t, len);
+    const double fl = floor(qd);
+    t = __dsub_rn(t, __dmul_rn(len, fl));
+    if (t >= len) t = __dsub_rn(t, len);
+  } else if (!(t >= 0.0 && t < len)) {
+    set_err(err, ERRBIT_OUT_OF_BOX);
+  }
+  *tout = t;
+  const double f = floor(__dmul_rn(t, inv));
+  if (!(f >= 0.0)) return 0;
+  if (f > (double)(n - 1)) return n - 1;
+  return (int)f;
+}
+
+template <typename TIN>
+__global__ void bin_kernel(const TIN* __restrict__ pos, int64_t n, Geo g, uint32_t* __restrict__ keys,
+                           int* __restrict__ err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int ix[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double t;
+    ix[a] = bin_axis((double)pos[3 * i + a], g.lo[a], g.len[a], g.inv[a], g.n[a], g.periodic, err, &t);
+  }
+  keys[i] = (uint32_t)(ix[0] + g.n[0] * (ix[1] + g.n[1] * ix[2]));
+}
+
+__global__ void radix_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift, int nbits,
+                                  uint32_t* __restrict__ hist, int ntiles) {
+  __shared__ uint32_t cnt[256];
+  const int radix = 1 << nbits;
+  for (int t = threadIdx.x; t < radix; t += RS_THREADS) cnt[t] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    const int64_t i = base + k * RS_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & (radix - 1)], 1u);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < radix; t += RS_THREADS) hist[(int64_t)t * ntiles + blockIdx.x] = cnt[t];
+}
+
+// Block-wide exclusive scan of SCAN_CH entries in place; writes the chunk total.
+__global__ void scan_chunks_kernel(uint32_t* __restrict__ data, int64_t total, uint32_t* __restrict__ sums) {
+  __shared__ uint32_t wsum[SCAN_THREADS / 32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_CH + (int64_t)threadIdx.x * 4;
+  uint32_t v[4];
+  uint32_t local = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = (base + k < total) ? data[base + k] : 0u;
+    local += v[k];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = (lane < SCAN_THREADS / 32) ? wsum[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < SCAN_THREADS / 32) wsum[lane] = wi - w;  // exclusive warp offsets
+    if (lane == 31) sums[blockIdx.x] = wi;
+  }
+  __syncthreads();
+  uint32_t run = wsum[warp] + incl - local;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (base + k < total) data[base + k] = run;
+    run += v[k];
+  }
+}
+
+// Exclusive scan of the chunk totals (one block, sequential over groups of 1024).
+__global__ void scan_top_kernel(uint32_t* __restrict__ sums, int nchunks) {
+  __shared__ uint32_t wsum[SCAN_THREADS / 32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = 0; base < nchunks; base += SCAN_THREADS) {
+    const int i = base + threadIdx.x;
+    const uint32_t v = (i < nchunks) ? sums[i] : 0u;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = wsum[lane];
+      uint32_t wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+      }
+      wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    const uint32_t c0 = carry;
+    if (i < nchunks) sums[i] = c0 + wsum[warp] + incl - v;
+    __syncthreads();
+    if (threadIdx.x == SCAN_THREADS - 1) carry = c0 + wsum[warp] + incl;
+    __syncthreads();
+  }
+}
+
+// Stable scatter of one radix pass.  Warp w of a tile owns keys
+// [w*256, (w+1)*256) of the tile, visited in 8 rounds of 32 in index order, so
+// that ranks among equal digits follow the input order.
+__global__ void radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                     uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
+                                     int nbits, const uint32_t* __restrict__ hist, const uint32_t* __restrict__ chunks,
+                                     int ntiles) {
+  __shared__ uint32_t whist[RS_WARPS][256];
+  __shared__ uint32_t gbase[256];
+  const int radix = 1 << nbits;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < RS_WARPS * 256; t += RS_THREADS) (&whist[0][0])[t] = 0;
+  __syncthreads();
+  const uint32_t lt = (1u << lane) - 1u;
+  const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (32 * RS_ITEMS);
+  uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
+  int dig[RS_ITEMS];
+#pragma unroll
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    const int64_t i = wbase + r * 32 + lane;
+    const bool valid = i < n;
+    const uint32_t k = valid ? kin[i] : 0u;
+    const int d = valid ? (int)((k >> shift) & (uint32_t)(radix - 1)) : 0x10000;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t prev = valid ? whist[warp][d] : 0u;
+    __syncwarp();
+    const int leader = __ffs(peers) - 1;
+    if (valid && lane == leader) whist[warp][d] = prev + __popc(peers);
+    __syncwarp();
+    rank[r] = prev + __popc(peers & lt);
+    key[r] = k;
+    val[r] = valid ? (vin ? vin[i] : (uint32_t)i) : 0u;
+    dig[r] = d;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < radix; t += RS_THREADS) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) {
+      const uint32_t c = whist[w][t];
+      whist[w][t] = run;
+      run += c;
+    }
+    const int64_t idx = (int64_t)t * ntiles + blockIdx.x;
+    gbase[t] = hist[idx] + chunks[idx / SCAN_CH];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    const int d = dig[r];
+    if (d < radix) {
+      const uint32_t dst = gbase[d] + whist[warp][d] + rank[r];
+      kout[dst] = key[r];
+      vout[dst] = val[r];
+    }
+  }
+}
+
+__global__ void cell_bounds_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t K, int* __restrict__ cs) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > n) return;
+  const int64_t kprev = (s == 0) ? -1 : (int64_t)keys[s - 1];
+  const int64_t k = (s == n) ? K : (int64_t)keys[s];
+  for (int64_t c = kprev + 1; c <= k; ++c) cs[c] = (int)s;
+}
+
+template <typename TIN, typename T>
+__global__ void gather_kernel(const TIN* __restrict__ pos, const TIN* __restrict__ q,
+                              const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n, Geo g,
+                              T* __restrict__ part) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint32_t i = vals[s];
+  const uint32_t cell = keys[s];
+  int ic[3];
+  ic[0] = (int)(cell % (uint32_t)g.n[0]);
+  ic[1] = (int)((cell / (uint32_t)g.n[0]) % (uint32_t)g.n[1]);
+  ic[2] = (int)(cell / ((uint32_t)g.n[0] * (uint32_t)g.n[1]));
+  int dummy = 0;
+  T u[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double t;
+    (void)bin_axis((double)pos[3 * (int64_t)i + a], g.lo[a], g.len[a], g.inv[a], g.n[a], g.periodic, &dummy, &t);
+    if (!isfinite(t)) t = 0.0;
+    const double rel = t - (ic[a] + 0.5) * g.h[a];
+    u[a] = (T)(rel / g.hs);
+  }
+  T* o = part + 4 * s;
+  o[0] = u[0];
+  o[1] = u[1];
+  o[2] = u[2];
+  o[3] = (T)q[i];
+}
+
+inline int grid1(int64_t n, int b) { return (int)((n + b - 1) / b); }
+}  // namespace
+
+int sort_tiles(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
+size_t sort_hist_entries(int64_t n) { return (size_t)256 * (size_t)(sort_tiles(n) > 0 ? sort_tiles(n) : 1); }
+size_t sort_chunk_entries(int64_t n) { return (sort_hist_entries(n) + SCAN_CH - 1) / SCAN_CH + 1; }
+
+cudaError_t launch_bin(const void* pos, bool pos_fp64, int64_t n, const Geo& g, uint32_t* keys, int* err,
+                       cudaStream_t s, int* nl) {
+  if (n <= 0) return cudaSuccess;
+  if (pos_fp64)
+    bin_kernel<double><<<grid1(n, 256), 256, 0, s>>>((const double*)pos, n, g, keys, err);
+  else
+    bin_kernel<float><<<grid1(n, 256), 256, 0, s>>>((const float*)pos, n, g, keys, err);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_radix_sort(SortWork& w, int64_t n, int key_bits, uint32_t** keys_out, uint32_t** vals_out,
+                              cudaStream_t s, int* nl) {
+  uint32_t *ki = w.keys0, *ko = w.keys1, *vi = nullptr, *vo = w.vals1;
+  if (n <= 0) {
+    *keys_out = w.keys0;
+    *vals_out = w.vals0;
+    return cudaSuccess;
+  }
+  const int ntiles = sort_tiles(n);
+  const int64_t total = (int64_t)256 * ntiles;
+  const int nchunks = (int)((total + SCAN_CH - 1) / SCAN_CH);
+  int passes = (key_bits + 7) / 8;
+  if (passes == 0) {
+    // a single cell: the identity permutation is the stable order
+    passes = 1;
+    key_bits = 1;
+  }
+  const int per = (key_bits + passes - 1) / passes;
+  int shift = 0;
+  for (int ps = 0; ps < passes; ++ps) {
+    const int nb = (shift + per <= key_bits) ? per : key_bits - shift;
+    radix_hist_kernel<<<ntiles, RS_THREADS, 0, s>>>(ki, n, shift, nb, w.hist, ntiles);
+    scan_chunks_kernel<<<nchunks, SCAN_THREADS, 0, s>>>(w.hist, (int64_t)(1 << nb) * ntiles, w.chunks);
+    scan_top_kernel<<<1, SCAN_THREADS, 0, s>>>(w.chunks, nchunks);
+    radix_scatter_kernel<<<ntiles, RS_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, nb, w.hist, w.chunks, ntiles);
+    *nl += 4;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    shift += nb;
+    // ping-pong: keys0 <-> keys1; the first pass reads implicit indices and
+    // writes vals1, later passes alternate vals1 <-> vals0
+    uint32_t* t = ki;
+    ki = ko;
+    ko = t;
+    if (vi == nullptr) {
+      vi = vo;
+      vo = w.vals0;
+    } else {
+      uint32_t* tv = vi;
+      vi = vo;
+      vo = tv;
+    }
+  }
+  *keys_out = ki;
+  *vals_out = vi;
+  return cudaSuccess;
+}
+
+cudaError_t launch_cell_bounds(const uint32_t* keys, int64_t n, int64_t K, int* cs, cudaStream_t s, int* nl) {
+  cell_bounds_kernel<<<grid1(n + 1, 256), 256, 0, s>>>(keys, n, K, cs);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const void* pos, const void* q, bool fp64, const uint32_t* keys, const uint32_t* vals,
+                          int64_t n, const Geo& g, void* part, cudaStream_t s, int* nl) {
+  if (n <= 0) return cudaSuccess;
+  if (fp64)
+    gather_kernel<double, double><<<grid1(n, 256), 256, 0, s>>>((const double*)pos, (const double*)q, keys, vals, n,
+                                                                 g, (double*)part);
+  else
+    gather_kernel<float, float><<<grid1(n, 256), 256, 0, s>>>((const float*)pos, (const float*)q, keys, vals, n, g,
+                                                               (float*)part);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+}  // namespace pmmm

@@ -1,0 +1,175 @@
+// Per-element translations of the PMMM path, for registers:
+//   * M2L of one wavevector in the real-matrix form of App. A.8 (Eq. realmatrix),
+//     applied to Fourier spectra of the real storage channels (Sec. 2.1: the
+//     convolution theorem turns the cell sum of Eq. pmmm into one M2L per k);
+//   * L2P (Eq. L2P) and the gradient from the order-one L2L (Eq. L2L, Eq. phigrad).
+#pragma once
+#include "common.cuh"
+
+namespace pmmm {
+
+// Spectrum of the real field Re S_j^kap (re = true) or Im S_j^kap, for any sign of
+// kap, from the spectra of the stored components sre[a] = X[sidx(j, a)] and
+// sim[a] = X[sidx(j, -a)] (a >= 0), using S_j^{-a} = (-1)^a conj(S_j^a) (App. A.1).
+template <typename T, int KAP>
+PMMM_HD cpx<T> s_re(const cpx<T>* sre, const cpx<T>* sim) {
+  (void)sim;
+  if (KAP >= 0) return sre[KAP];
+  return ((-KAP) & 1) ? mk(-sre[-KAP].x, -sre[-KAP].y) : sre[-KAP];
+}
+template <typename T, int KAP>
+PMMM_HD cpx<T> s_im(const cpx<T>* sre, const cpx<T>* sim) {
+  (void)sre;
+  if (KAP == 0) return mk(T(0), T(0));
+  if (KAP > 0) return sim[KAP];
+  return ((-KAP) & 1) ? sim[-KAP] : mk(-sim[-KAP].x, -sim[-KAP].y);
+}
+
+// Compile-time loops (the orders m, mu are template constants so that every
+// register array index and sign is fixed at compile time).
+template <int P, typename T, int M, int MU>
+struct M2LTerm {
+  PMMM_HD static void apply(int l, int lam, const cpx<T>* sre, const cpx<T>* sim, const cpx<T>* mre,
+                            const cpx<T>* mim, cpx<T>* Lre, cpx<T>* Lim) {
+    if (M <= l && MU <= lam) {
+      // G^{m,mu} = S_{l+lam}^{-(m+mu)}:  A = Re, B = Im  (Eq. realmatrix)
+      const cpx<T> A = s_re<T, -(M + MU)>(sre, sim);
+      const cpx<T> B = s_im<T, -(M + MU)>(sre, sim);
+      if (MU == 0) {
+        cmac(Lre[M], A, mre[0]);
+        cmac(Lim[M], B, mre[0]);
+      } else {
+        // (-1)^mu G^{m,-mu} = (-1)^mu S_{l+lam}^{-(m-mu)}:  C = Re, D = Im
+        cpx<T> C = s_re<T, MU - M>(sre, sim);
+        cpx<T> D = s_im<T, MU - M>(sre, sim);
+        if (MU & 1) {
+          C = mk(-C.x, -C.y);
+          D = mk(-D.x, -D.y);
+        }
+        // Re L += (A + C) Re M - (B - D) Im M ;  Im L += (B + D) Re M + (A - C) Im M
+        cmac(Lre[M], A + C, mre[MU]);
+        cmac(Lre[M], D - B, mim[MU]);
+        cmac(Lim[M], B + D, mre[MU]);
+        cmac(Lim[M], A - C, mim[MU]);
+      }
+    }
+    M2LTerm<P, T, M, MU + 1>::apply(l, lam, sre, sim, mre, mim, Lre, Lim);
+  }
+};
+template <int P, typename T, int M>
+struct M2LTerm<P, T, M, P + 1> {
+  PMMM_HD static void apply(int l, int lam, const cpx<T>*, const cpx<T>*, const cpx<T>*, const cpx<T>*, cpx<T>*,
+                            cpx<T>*) {
+    (void)l; (void)lam;
+  }
+};
+template <int P, typename T, int M>
+struct M2LRow {
+  PMMM_HD static void apply(int l, int lam, const cpx<T>* sre, const cpx<T>* sim, const cpx<T>* mre,
+                            const cpx<T>* mim, cpx<T>* Lre, cpx<T>* Lim) {
+    M2LTerm<P, T, M, 0>::apply(l, lam, sre, sim, mre, mim, Lre, Lim);
+    M2LRow<P, T, M + 1>::apply(l, lam, sre, sim, mre, mim, Lre, Lim);
+  }
+};
+template <int P, typename T>
+struct M2LRow<P, T, P + 1> {
+  PMMM_HD static void apply(int, int, const cpx<T>*, const cpx<T>*, const cpx<T>*, const cpx<T>*, cpx<T>*,
+                            cpx<T>*) {}
+};
+
+// One output order l of the M2L at one wavevector.
+//   Mk(c)  -> spectrum of real channel c of M at this k      (c < (p+1)^2)
+//   Gk(s)  -> spectrum of real component s of the kernel      (s < (2p+1)^2)
+//   St(c, v) stores the spectrum of real channel c of L.
+// The kernel component s = sidx(j, kap) is the real storage of S_j (App. A.7).
+template <int P, typename T, class LM, class LG, class ST>
+PMMM_HD void m2l_order(int l, int p, LM&& Mk, LG&& Gk, ST&& St) {
+  cpx<T> Lre[P + 1], Lim[P + 1];
+#pragma unroll
+  for (int m = 0; m <= P; ++m) {
+    Lre[m] = mk(T(0), T(0));
+    Lim[m] = mk(T(0), T(0));
+  }
+  for (int lam = 0; lam <= p; ++lam) {
+    const int j = l + lam;
+    cpx<T> mre[P + 1], mim[P + 1];
+#pragma unroll
+    for (int mu = 0; mu <= P; ++mu) {
+      mre[mu] = mk(T(0), T(0));
+      mim[mu] = mk(T(0), T(0));
+      if (mu <= lam) {
+        mre[mu] = Mk(sidx(lam, mu));
+        if (mu > 0) mim[mu] = Mk(sidx(lam, -mu));
+      }
+    }
+    cpx<T> sre[2 * P + 1], sim[2 * P + 1];
+#pragma unroll
+    for (int a = 0; a <= 2 * P; ++a) {
+      sre[a] = mk(T(0), T(0));
+      sim[a] = mk(T(0), T(0));
+      if (a <= j) {
+        sre[a] = Gk(sidx(j, a));
+        if (a > 0) sim[a] = Gk(sidx(j, -a));
+      }
+    }
+    M2LRow<P, T, 0>::apply(l, lam, sre, sim, mre, mim, Lre, Lim);
+  }
+#pragma unroll
+  for (int m = 0; m <= P; ++m) {
+    if (m <= l) {
+      St(sidx(l, m), Lre[m]);
+      if (m > 0) St(sidx(l, -m), Lim[m]);
+    }
+  }
+}
+
+// L2P of Eq. L2P and the gradient through the order-one L2L of Eq. L2L
+// (Eq. phigrad: dPhi/dx = -Re L'_1^1, dPhi/dy = Im L'_1^1, dPhi/dz = L'_1^0).
+//   L(c) -> real channel c of the local expansion; R: real storage of R(r - r_L).
+template <int P, typename T, class LL>
+PMMM_HD void l2p_real(LL&& Lc, const T* R, T& phi, T& gx, T& gy, T& gz) {
+  T f = T(0), l10 = T(0), l11r = T(0), l11i = T(0);
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    // Phi = sum_l [L_l^0 R_l^0 + 2 sum_{m>0} Re(L_l^m R_l^m)]
+    const T L0 = Lc(sidx(l, 0));
+    f += L0 * R[sidx(l, 0)];
+#pragma unroll
+    for (int m = 1; m <= l; ++m) {
+      const T lr = Lc(sidx(l, m)), li = Lc(sidx(l, -m));
+      f += T(2) * (lr * R[sidx(l, m)] - li * R[sidx(l, -m)]);
+    }
+    if (l >= 1) {
+      // L'_1^0 = sum_l [L_l^0 R_{l-1}^0 + 2 sum_{mu=1}^{l-1} Re(L_l^mu R_{l-1}^mu)]
+      l10 += L0 * R[sidx(l - 1, 0)];
+#pragma unroll
+      for (int m = 1; m <= l - 1; ++m) {
+        const T lr = Lc(sidx(l, m)), li = Lc(sidx(l, -m));
+        l10 += T(2) * (lr * R[sidx(l - 1, m)] - li * R[sidx(l - 1, -m)]);
+      }
+      // L'_1^1 = sum_l [ sum_{mu=1}^{l} L_l^mu R_{l-1}^{mu-1}
+      //                  - sum_{nu=0}^{l-2} conj(L_l^nu R_{l-1}^{nu+1}) ]
+#pragma unroll
+      for (int m = 1; m <= l; ++m) {
+        const T lr = Lc(sidx(l, m)), li = Lc(sidx(l, -m));
+        const T rr = R[sidx(l - 1, m - 1)], ri = (m - 1 > 0) ? R[sidx(l - 1, -(m - 1))] : T(0);
+        l11r += lr * rr - li * ri;
+        l11i += lr * ri + li * rr;
+      }
+#pragma unroll
+      for (int nu = 0; nu <= l - 2; ++nu) {
+        const T lr = Lc(sidx(l, nu)), li = (nu > 0) ? Lc(sidx(l, -nu)) : T(0);
+        const T rr = R[sidx(l - 1, nu + 1)], ri = R[sidx(l - 1, -(nu + 1))];
+        // -conj(a b) = -(Re(ab)) + i Im(ab)
+        l11r -= lr * rr - li * ri;
+        l11i += lr * ri + li * rr;
+      }
+    }
+  }
+  phi = f;
+  gx = -l11r;
+  gy = l11i;
+  gz = l10;
+}
+
+}  // namespace pmmm

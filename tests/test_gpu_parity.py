@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, step by
+step (binning, P2M, cell convolution, corrections) and end to end.
+
+Tolerances:
+  * integer work (cell ids, permutation, cell_start): bit-exact;
+  * FP64 path: relative RMS force and potential error <= 1e-10 against the oracle
+    PMMM at the same (mesh, p, c) (the bound asked for is 1e-6; FFT rounding
+    gives ~1e-13);
+  * FP32 path: the per-p tolerance FP32_TOL below, derived from float rounding
+    (u = 6e-8) amplified by the FFT depth, the (p+1)^4 M2L sums and the
+    cancellation between near and far fields; the measured values are logged.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+# relative RMS force error bound of the FP32 path against the FP64 oracle, per p
+FP32_TOL = {p: 3e-6 * (1 + 0.25 * p) for p in range(0, 13)}
+
+
+@pytest.fixture(scope="module")
+def pk():
+    import torch
+    import paper_1409_5981_gb300 as pk
+    pk.build()
+    torch.cuda.set_device(0)
+    return pk
+
+
+def _t(a, dtype):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _rel(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
+
+
+def _run(pk, cfg, pos, q):
+    import torch
+    dt = torch.float64 if cfg.precision == pk.FP64 else torch.float32
+    plan = pk.Plan(cfg)
+    phi, force, energy = plan.compute(_t(pos, dt), _t(q, dt), energy=True)
+    torch.cuda.synchronize()
+    return plan, phi.cpu().numpy().astype(np.float64), force.cpu().numpy().astype(np.float64), energy
+
+
+def _oracle(cfg, pk, pos, q, target_cells=None, want_ml=False):
+    alpha = cfg.ewald_alpha if cfg.ewald_alpha > 0 else None
+    return oracle.pmmm(pos, q, cfg.box_lo, cfg.box_len, cfg.mesh, cfg.p, cfg.cutoff, cfg.boundary == pk.PERIODIC,
+                       alpha=alpha, nmax=cfg.ewald_nmax or 5, target_cells=target_cells, want_ml=want_ml)
+
+
+# ----------------------------------------------------------------------------- binning
+@pytest.mark.parametrize("boundary", [0, 1])
+@pytest.mark.parametrize("fp64", [True, False])
+def test_binning_bit_exact(pk, boundary, fp64):
+    n = 5003  # several sort tiles and a ragged tail
+    g = synth.rng(201)
+    mesh = (8, 4, 16)
+    lo, ln = (-0.5, 0.25, 1.0), (1.0, 0.5, 2.0)
+    pos = lo + g.random((n, 3)) * ln
+    # particles exactly on cell faces and (periodic) outside the box
+    h = np.array(ln) / np.array(mesh)
+    pos[:200] = lo + np.floor(g.random((200, 3)) * mesh) * h
+    if boundary == pk.PERIODIC:
+        pos[200:400] += np.round(g.standard_normal((200, 3))) * ln
+    if not fp64:
+        pos = pos.astype(np.float32).astype(np.float64)
+    q = g.standard_normal(n)
+    cfg = pk.Config(box_lo=lo, box_len=ln, mesh=mesh, p=2, boundary=boundary,
+                    precision=pk.FP64 if fp64 else pk.FP32)
+    plan, *_ = _run(pk, cfg, pos, q)
+    st, cell, perm, cs, _ = oracle.bin_particles(pos, lo, ln, mesh, boundary == pk.PERIODIC)
+    assert st == 0
+    assert np.array_equal(plan.export(pk.EXPORT_PERM), perm.astype(np.int32))
+    assert np.array_equal(plan.export(pk.EXPORT_SORTED_CELL), cell[perm].astype(np.int32))
+    assert np.array_equal(plan.export(pk.EXPORT_CELL_START), cs.astype(np.int32))
+    plan.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 2047, 2048, 2049, 70001])
+def test_sort_sizes(pk, n):
+    g = synth.rng(202 + n)
+    pos = g.random((n, 3))
+    q = np.ones(n)
+    cfg = pk.Config(mesh=(32, 32, 32), p=1, boundary=pk.PERIODIC, precision=pk.FP32)
+    pos = pos.astype(np.float32).astype(np.float64)
+    plan, *_ = _run(pk, cfg, pos, q)
+    st, cell, perm, cs, _ = oracle.bin_particles(pos, (0, 0, 0), (1, 1, 1), (32, 32, 32), True)
+    assert np.array_equal(plan.export(pk.EXPORT_PERM), perm.astype(np.int32))
+    assert np.array_equal(plan.export(pk.EXPORT_CELL_START), cs.astype(np.int32))
+    plan.close()
+
+
+# ----------------------------------------------------------------------------- stages
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_multipoles_and_locals_fp64(pk, boundary):
+    pos, q = synth.uniform_pm1(3000, synth.seed(1, 3))
+    cfg = pk.Config(mesh=(8, 8, 8), p=4, boundary=boundary, precision=pk.FP64)
+    plan, *_ = _run(pk, cfg, pos, q)
+    ref = _oracle(cfg, pk, pos, q, want_ml=True)
+    M = plan.export(pk.EXPORT_MULTIPOLE)
+    Mr = oracle.to_real_storage(ref["M"]).T
+    assert np.abs(M - Mr).max() < 1e-13 * np.abs(Mr).max()
+    Lg = plan.export(pk.EXPORT_LOCAL)
+    Lr = oracle.to_real_storage(ref["L"]).T
+    for l in range(cfg.p + 1):
+        sl = slice(l * l, (l + 1) ** 2)
+        assert np.abs(Lg[sl] - Lr[sl]).max() < 1e-11 * np.abs(Lr[sl]).max(), l
+    if boundary == pk.PERIODIC:
+        corr = plan.export(pk.EXPORT_CORR)
+        assert np.allclose(corr[:5], ref["corr"][:5], rtol=1e-12, atol=1e-12)
+    plan.close()
+
+
+# ----------------------------------------------------------------------------- full evaluation
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_full_fp64_config1(pk, boundary):
+    """4096 point charges +-1 in the unit cube, mesh 8^3 (16^3 padded when open), p = 4, c = 1."""
+    pos, q = synth.uniform_pm1(4096, synth.seed(1, boundary))
+    cfg = pk.Config(mesh=(8, 8, 8), p=4, boundary=boundary, precision=pk.FP64)
+    plan, phi, force, energy = _run(pk, cfg, pos, q)
+    ref = _oracle(cfg, pk, pos, q)
+    rf = -(q[:, None] * ref["grad"])
+    e_f, e_p = _rel(force, rf), _rel(phi, ref["phi"])
+    print(f"fp64 boundary={boundary}: force {e_f:.2e} phi {e_p:.2e}")
+    assert e_f < FP64_TOL and e_p < FP64_TOL
+    u = 0.5 * float((q * ref["phi"]).sum())
+    assert abs(energy - u) < 1e-10 * abs(u)
+    plan.close()
+
+
+@pytest.mark.parametrize("p", [0, 1, 3, 5, 7])
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_full_fp32_per_p(pk, p, boundary):
+    pos, q = synth.uniform_pm1(6000, synth.seed(2, 10 + p))
+    pos = pos.astype(np.float32).astype(np.float64)
+    cfg = pk.Config(mesh=(8, 8, 8), p=p, boundary=boundary, precision=pk.FP32)
+    plan, phi, force, energy = _run(pk, cfg, pos, q)
+    ref = _oracle(cfg, pk, pos, q)
+    rf = -(q[:, None] * ref["grad"])
+    e_f, e_p = _rel(force, rf), _rel(phi, ref["phi"])
+    print(f"fp32 p={p} boundary={boundary}: force {e_f:.2e} phi {e_p:.2e}")
+    assert e_f < FP32_TOL[p] and e_p < FP32_TOL[p]
+    plan.close()
+
+
+def test_cutoff2_and_anisotropic_box(pk):
+    g = synth.rng(203)
+    n = 3000
+    lo, ln = (0.0, -1.0, 0.5), (1.0, 2.0, 0.5)
+    pos = lo + g.random((n, 3)) * ln
+    q = g.standard_normal(n)
+    for boundary in (0, 1):
+        cfg = pk.Config(box_lo=lo, box_len=ln, mesh=(8, 16, 8), p=3, cutoff=2, boundary=boundary,
+                        precision=pk.FP64)
+        plan, phi, force, _ = _run(pk, cfg, pos, q)
+        ref = _oracle(cfg, pk, pos, q)
+        rf = -(q[:, None] * ref["grad"])
+        assert _rel(force, rf) < FP64_TOL and _rel(phi, ref["phi"]) < FP64_TOL
+        plan.close()
+
+
+def test_gravity_sign_and_clustered_cell(pk):
+    """sign = -1 (gravity) and one crowded cell (more particles than a near-field tile)."""
+    g = synth.rng(204)
+    n = 4000
+    pos = g.random((n, 3))
+    pos[:2500] = 0.3 + 0.05 * g.random((2500, 3))
+    m = np.full(n, 1.0 / n)
+    cfg = pk.Config(mesh=(8, 8, 8), p=4, boundary=pk.OPEN, precision=pk.FP64, sign=-1.0)
+    plan, phi, force, _ = _run(pk, cfg, pos, m)
+    ref = _oracle(cfg, pk, pos, m)
+    assert _rel(phi, -ref["phi"]) < FP64_TOL
+    assert _rel(force, m[:, None] * ref["grad"]) < FP64_TOL
+    plan.close()
+
+
+def test_empty_and_single(pk):
+    import torch
+    cfg = pk.Config(mesh=(4, 4, 4), p=2, boundary=pk.PERIODIC, precision=pk.FP64)
+    plan = pk.Plan(cfg)
+    phi, force, e = plan.compute(torch.zeros((0, 3), dtype=torch.float64, device="cuda"),
+                                 torch.zeros(0, dtype=torch.float64, device="cuda"), energy=True)
+    assert e == 0.0 and phi.numel() == 0
+    pos, q = np.array([[0.3, 0.6, 0.1]]), np.array([1.0])
+    phi, force, e = plan.compute(_t(pos, torch.float64), _t(q, torch.float64), energy=True)
+    ref = _oracle(cfg, pk, pos, q)
+    assert abs(phi.item() - ref["phi"][0]) < 1e-12
+    assert np.abs(force.cpu().numpy()).max() < 1e-12
+    plan.close()
+
+
+def test_input_errors(pk):
+    import torch
+    cfg = pk.Config(mesh=(4, 4, 4), p=2, boundary=pk.OPEN, precision=pk.FP64)
+    plan = pk.Plan(cfg)
+    pos = np.array([[0.3, 0.6, 0.1], [1.2, 0.5, 0.5]])
+    q = np.ones(2)
+    with pytest.raises(pk.PmmmError) as ei:
+        plan.compute(_t(pos, torch.float64), _t(q, torch.float64), energy=True)
+    assert ei.value.status == pk.ERR_OUT_OF_BOX
+    pos[1, 0] = np.nan
+    plan.compute(_t(pos, torch.float64), _t(q, torch.float64))
+    assert plan.status() == pk.ERR_NONFINITE_INPUT
+    assert plan.status() == pk.OK  # cleared
+    plan.close()
+
+
+def test_host_api_and_determinism(pk):
+    pos, q = synth.uniform_pm1(20000, synth.seed(2, 99))
+    pos32, q32 = pos.astype(np.float32), q.astype(np.float32)
+    cfg = pk.Config(mesh=(16, 16, 16), p=5, boundary=pk.PERIODIC, precision=pk.FP32)
+    plan = pk.Plan(cfg)
+    a = plan.compute_host(pos32, q32, energy=True)
+    b = plan.compute_host(pos32, q32, energy=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
+    import torch
+    phi, force, e = plan.compute(_t(pos32, torch.float32), _t(q32, torch.float32), energy=True)
+    assert np.array_equal(phi.cpu().numpy(), a[0]) and np.array_equal(force.cpu().numpy(), a[1])
+    plan.close()
+
+
+# ----------------------------------------------------------------------------- full-size workloads
+def test_config2_periodic_sampled(pk):
+    """N = 2^20 uniform +-1, periodic, mesh 32^3, p = 7, FP32, 27-cell near field, in the
+    launch configuration the benchmark times; the oracle checks a seeded sample of cells."""
+    n = 1 << 20
+    pos, q = synth.uniform_pm1(n, synth.seed(2, 0))
+    pos = pos.astype(np.float32).astype(np.float64)
+    cfg = pk.Config(mesh=(32, 32, 32), p=7, boundary=pk.PERIODIC, precision=pk.FP32)
+    plan, phi, force, energy = _run(pk, cfg, pos, q)
+    cells = synth.rng(205).choice(32 ** 3, size=6, replace=False)
+    ref = _oracle(cfg, pk, pos, q, target_cells=cells)
+    sel = ~np.isnan(ref["phi"])
+    rf = -(q[sel, None] * ref["grad"][sel])
+    e_f, e_p = _rel(force[sel], rf), _rel(phi[sel], ref["phi"][sel])
+    print(f"config2 sampled {sel.sum()} particles: force {e_f:.2e} phi {e_p:.2e}")
+    assert e_f < FP32_TOL[7] and e_p < FP32_TOL[7]
+    # neutral periodic system: the net force is small (truncation only)
+    F = force
+    assert np.abs(F.sum(0)).max() < 1e-2 * np.sqrt((F ** 2).sum())
+    plan.close()
+
+
+def test_config2b_plummer_open_sampled(pk):
+    """N = 2^20 Plummer sphere (a = 0.1, cut at 10a), equal masses, open box [-1,1]^3,
+    mesh 64^3 -> 128^3 padded, p = 5, gravity; sampled cells against the oracle."""
+    n = 1 << 20
+    pos, m = synth.plummer(n, synth.seed(2, 1))
+    pos = pos.astype(np.float32).astype(np.float64)
+    cfg = pk.Config(box_lo=(-1, -1, -1), box_len=(2, 2, 2), mesh=(64, 64, 64), p=5, boundary=pk.OPEN,
+                    precision=pk.FP32, sign=-1.0)
+    plan, phi, force, _ = _run(pk, cfg, pos, m)
+    cs = plan.export(pk.EXPORT_CELL_START)
+    counts = np.diff(cs)
+    busy = np.argsort(counts)[-2:]          # the two most crowded cells
+    some = synth.rng(206).choice(np.nonzero(counts)[0], size=3, replace=False)
+    cells = np.concatenate([busy, some])
+    ref = _oracle(cfg, pk, pos, m, target_cells=cells)
+    sel = ~np.isnan(ref["phi"])
+    e_f = _rel(force[sel], m[sel, None] * ref["grad"][sel])
+    e_p = _rel(phi[sel], -ref["phi"][sel])
+    print(f"plummer sampled {sel.sum()} particles: force {e_f:.2e} phi {e_p:.2e}")
+    assert e_f < FP32_TOL[5] and e_p < FP32_TOL[5]
+    plan.close()
