@@ -1,0 +1,453 @@
+#!/usr/bin/env python
+"""Benchmark of one full PMMM force evaluation on GB300.
+
+Metric: particles per second of a full force evaluation (binning, P2M, FFTs,
+M2L, inverse FFTs, corrections, L2P, near field, energy), whole job over all
+ranks, at the relative RMS force error the configuration reaches (stated in
+the JSON line), plus the mesh-stage HBM fraction.
+
+Default workload: N = 2^20 point charges +-1 (neutral) uniform in the unit cube,
+periodic, mesh 32^3, p = 7, FP32, 27-cell near field.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--no-cpu-baseline]
+
+With N > 1 it runs under torchrun, one independent replica per GPU (the method
+needs no exchange between independent systems): the timed region is bracketed
+by a barrier and synchronisation, and the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    # name: (n, boundary, mesh, p, precision, box_lo, box_len, generator, sign)
+    "periodic_uniform_n1048576_mesh32_p7_fp32": (1 << 20, "periodic", 32, 7, "fp32", (0, 0, 0), (1, 1, 1),
+                                                  "uniform_pm1", 1.0),
+    "open_plummer_n1048576_mesh64_p5_fp32": (1 << 20, "open", 64, 5, "fp32", (-1, -1, -1), (2, 2, 2), "plummer",
+                                             -1.0),
+    "periodic_uniform_n16777216_mesh64_p7_fp32": (1 << 24, "periodic", 64, 7, "fp32", (0, 0, 0), (1, 1, 1),
+                                                   "uniform_pm1", 1.0),
+    "open_uniform_n4096_mesh8_p4_fp64": (4096, "open", 8, 4, "fp64", (0, 0, 0), (1, 1, 1), "uniform_pm1", 1.0),
+}
+DEFAULT_WORKLOAD = "periodic_uniform_n1048576_mesh32_p7_fp32"
+METRIC = "particles/s per full force eval at fixed RMS force error; mesh-stage HBM % peak"
+UNIT = "particles/s"
+# Flops counted per near-field pair interaction: 3 sub, 5 for r^2, 1 rsqrt, 1 mul (q/r),
+# 1 add (phi), 2 mul (q/r^3), 6 for the three gradient FMAs, 1 select: 20.
+PP_FLOPS_PER_PAIR = 20
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _inputs(name: str, rank: int):
+    n, boundary, mesh, p, prec, lo, ln, gen, sign = WORKLOADS[name]
+    s = synth.seed(2, 100 * rank)
+    if gen == "uniform_pm1":
+        pos, q = synth.uniform_pm1(n, s, lo, ln)
+    else:
+        pos, q = synth.plummer(n, s)
+    return pos, q
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+def _src_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str, workload: str, sha: str):
+    """DRAM bytes per launch from profiles/traffic.txt when recorded for this exact source."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == workload \
+                    and parts[2] == sha:
+                return float(parts[3])
+    return None
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.samples = []
+        self.proc = None
+        self.gpu_id = gpu_id
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.t is not None:
+            self.t.join(timeout=5)
+
+    def summary(self, t0: float, t1: float):
+        rows = [s for (ts, s) in self.samples if t0 - 0.06 <= ts <= t1 + 0.06 and len(s) >= 6]
+        if not rows and self.samples:
+            mid = 0.5 * (t0 + t1)
+            rows = [min(self.samples, key=lambda x: abs(x[0] - mid))[1]]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2 + k].lower().startswith("active")})
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _gpu_id(torch, dev):
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        bus = getattr(pr, "pci_bus_id", None)
+        dom = getattr(pr, "pci_domain_id", 0)
+        devid = getattr(pr, "pci_device_id", 0)
+        if bus is not None:
+            return f"{dom:08x}:{bus:02x}:{devid:02x}.0"
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        return vis.split(",")[dev].strip()
+    return str(dev)
+
+
+def _pairs(cs: np.ndarray, mesh: int, periodic: bool, c: int = 1) -> int:
+    """Near-field pair count: sum over cells of n_cell * (sum of n over the (2c+1)^3 cells) - N."""
+    cnt = np.diff(cs.astype(np.int64)).reshape(mesh, mesh, mesh)  # [z][y][x]
+    tot = np.zeros_like(cnt)
+    for dz in range(-c, c + 1):
+        for dy in range(-c, c + 1):
+            for dx in range(-c, c + 1):
+                if periodic:
+                    tot += np.roll(cnt, shift=(dz, dy, dx), axis=(0, 1, 2))
+                else:
+                    sh = np.zeros_like(cnt)
+                    zs = slice(max(dz, 0), mesh + min(dz, 0)), slice(max(-dz, 0), mesh + min(-dz, 0))
+                    ys = slice(max(dy, 0), mesh + min(dy, 0)), slice(max(-dy, 0), mesh + min(-dy, 0))
+                    xs = slice(max(dx, 0), mesh + min(dx, 0)), slice(max(-dx, 0), mesh + min(-dx, 0))
+                    sh[zs[0], ys[0], xs[0]] = cnt[zs[1], ys[1], xs[1]]
+                    tot += sh
+    return int((cnt * tot).sum() - cnt.sum())
+
+
+def _cpu_baseline(name: str, pos, q, g, budget_s: float = 20.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the
+    workload: its Green-function table g (set-up, untimed like the GPU plan), then one
+    evaluation restricted to a seeded sample of target cells, timed."""
+    import oracle
+    n, boundary, mesh, p, prec, lo, ln, gen, sign = WORKLOADS[name]
+    per = boundary == "periodic"
+    ncell = 8
+    t_one = None
+    rng = synth.rng(4242)
+    while True:
+        cells = rng.choice(mesh ** 3, size=ncell, replace=False)
+        t0 = time.perf_counter()
+        r = oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, 1, per, target_cells=cells, green=g)
+        dt = time.perf_counter() - t0
+        done = int((~np.isnan(r["phi"])).sum())
+        if dt >= 0.5 * budget_s or ncell >= mesh ** 3:
+            break
+        t_one = dt
+        ncell = min(mesh ** 3, int(ncell * max(2.0, 0.8 * budget_s / max(dt, 1e-3))))
+    return {"value": done / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"FP64 oracle (cell-pair convolution of Eq. pmmm), one evaluation of the same {n}-particle "
+                      f"workload restricted to {ncell} seeded target cells ({done} particles) after its Green-function "
+                      f"table; {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the oracle on the host cores, same config and metric."""
+    if rank != 0:
+        return 0
+    import oracle
+    name = args.workload
+    n, boundary, mesh, p, prec, lo, ln, gen, sign = WORKLOADS[name]
+    per = boundary == "periodic"
+    pos, q = _inputs(name, 0)
+    g = oracle.green_table(lo, ln, (mesh,) * 3, p, 1, per)
+    rng = synth.rng(777)
+    # size one step to ~3 s so that warmup + steps end within a few minutes
+    ncell = 8
+    while True:
+        cells = rng.choice(mesh ** 3, size=ncell, replace=False)
+        t0 = time.perf_counter()
+        oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, 1, per, target_cells=cells, green=g)
+        dt = time.perf_counter() - t0
+        if dt > 1.5 or ncell >= mesh ** 3:
+            break
+        ncell = min(mesh ** 3, ncell * 2)
+    times, done = [], []
+    for it in range(args.warmup + args.steps):
+        cells = rng.choice(mesh ** 3, size=ncell, replace=False)
+        t0 = time.perf_counter()
+        r = oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, 1, per, target_cells=cells, green=g)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+            done.append(int((~np.isnan(r["phi"])).sum()))
+    value = sum(done) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(name, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"each step: one oracle evaluation restricted to {ncell} random target cells "
+                                       f"of the {n}-particle workload (Green table precomputed once)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(name, world):
+    n, boundary, mesh, p, prec, lo, ln, gen, sign = WORKLOADS[name]
+    return {"workload": name, "n_particles": n, "boundary": boundary, "mesh": [mesh] * 3,
+            "fft_grid": [mesh if boundary == "periodic" else 2 * mesh] * 3, "p": p, "cutoff_cells": 27,
+            "distribution": gen, "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)"}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1409_5981_gb300 as pk
+
+    name = args.workload
+    n, boundary, mesh, p, prec, lo, ln, gen, sign = WORKLOADS[name]
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    pk._lib()  # fails loudly when the library is missing
+    fp64 = prec == "fp64"
+    dt = torch.float64 if fp64 else torch.float32
+    cfg = pk.Config(box_lo=lo, box_len=ln, mesh=(mesh,) * 3, p=p, cutoff=1,
+                    boundary=pk.PERIODIC if boundary == "periodic" else pk.OPEN,
+                    precision=pk.FP64 if fp64 else pk.FP32, sign=sign)
+    stream = torch.cuda.current_stream()
+    t_plan = time.perf_counter()
+    plan = pk.Plan(cfg, stream)
+    t_plan = time.perf_counter() - t_plan
+    pos_np, q_np = _inputs(name, rank)
+    npdt = np.float64 if fp64 else np.float32
+    pos = torch.tensor(pos_np.astype(npdt), device=dev)
+    q = torch.tensor(q_np.astype(npdt), device=dev)
+    phi = torch.empty(n, dtype=dt, device=dev)
+    force = torch.empty((n, 3), dtype=dt, device=dev)
+    plan.reserve(n)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        st = plan.compute_raw(n, pos.data_ptr(), q.data_ptr(), phi.data_ptr(), force.data_ptr())
+        if st != 0:
+            raise pk.PmmmError(st, "pmmm_compute")
+
+    # accuracy of this workload: sampled cells against the oracle (rank 0, outside timing)
+    sampler = ClockSampler(_gpu_id(torch, local_rank))
+    sampler.start()
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    st = plan.status()
+    if st != 0:
+        raise pk.PmmmError(st, "warm-up")
+    plan.set_timing(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_acc = {}
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0w = time.time()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+        if k == 0 or k == args.steps - 1 or k % 8 == 0:
+            for kk, v in plan.stage_times().items():
+                stage_acc.setdefault(kk, []).append(v)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t1w = time.time()
+    sampler.stop()
+    plan.set_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    st = plan.status()
+    if st != 0:
+        raise pk.PmmmError(st, "timed region")
+    launches = plan.info(pk.INFO_LAUNCHES)
+    clocks = sampler.summary(t0w, t1w)
+
+    # end-to-end through the host-buffer ABI call (pinned memory)
+    pos_h = torch.tensor(pos_np.astype(npdt)).pin_memory()
+    q_h = torch.tensor(q_np.astype(npdt)).pin_memory()
+    phi_h = torch.empty(n, dtype=dt).pin_memory()
+    force_h = torch.empty((n, 3), dtype=dt).pin_memory()
+    plan.compute_host(pos_h, q_h, phi_h, force_h)
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        plan.compute_host(pos_h, q_h, phi_h, force_h)
+        e2e_ms.append(1e3 * (time.perf_counter() - t))
+    esz = 8 if fp64 else 4
+
+    # near-field pair count and mesh byte model
+    cs = plan.export(pk.EXPORT_CELL_START)
+    pairs = _pairs(cs, mesh, boundary == "periodic")
+    C, CG, Kh, K = plan.info(pk.INFO_C), plan.info(pk.INFO_CG), plan.info(pk.INFO_KH), plan.info(pk.INFO_K)
+    pp_ms = statistics.median(stage_acc.get("near_field", [float("nan")]))
+    mesh_ms = sum(statistics.median(stage_acc.get(s, [0.0])) for s in ("fft_forward", "m2l", "fft_inverse"))
+    mesh_bytes = esz * (2 * C * K + 4 * 2 * C * Kh + 2 * CG * Kh)
+    hbm, sm_max, peak_kind = _peaks()
+    sm_clock = clocks.get("sm_max_mhz") or sm_max
+    alu_peak = 2.0 * FP32_LANES_PER_SM * NUM_SMS * sm_max * 1e6 / 1e12
+    pp_tf = PP_FLOPS_PER_PAIR * pairs / (pp_ms * 1e-3) / 1e12
+    sha = _src_sha(["paper_1409_5981_gb300/csrc/pp.cu"])
+
+    # reduce over ranks: max time
+    tmax = total_ms
+    e2e_tot = sum(e2e_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms, e2e_tot], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        tmax, e2e_tot = float(tt[0]), float(tt[1])
+    value = world * n * args.steps / (tmax * 1e-3)
+    e2e_value = world * n * args.steps / (e2e_tot * 1e-3)
+    if rank != 0:
+        return 0
+
+    # error of this configuration against the oracle on sampled cells (outside timing)
+    err = None
+    green = None
+    pos64, q64 = pos_np.astype(npdt).astype(np.float64), q_np.astype(npdt).astype(np.float64)
+    if not (args.no_accuracy and (args.no_cpu_baseline or world > 1)):
+        import oracle
+        green = oracle.green_table(lo, ln, (mesh,) * 3, p, 1, boundary == "periodic")
+    if not args.no_accuracy:
+        import oracle
+        cells = synth.rng(99).choice(mesh ** 3, size=4, replace=False)
+        r = oracle.pmmm(pos64, q64, lo, ln, (mesh,) * 3, p, 1, boundary == "periodic", target_cells=cells,
+                        green=green)
+        sel = ~np.isnan(r["phi"])
+        plan.compute_raw(n, pos.data_ptr(), q.data_ptr(), phi.data_ptr(), force.data_ptr())
+        f = force.cpu().numpy().astype(np.float64)[sel]
+        rf = -sign * q64[sel, None] * r["grad"][sel]
+        err = float(np.sqrt(((f - rf) ** 2).sum() / (rf ** 2).sum()))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
+        "config": _config(name, world),
+        "rel_rms_force_err_vs_fp64_oracle_pmmm": err,
+        "stage_ms": {k: statistics.median(v) for k, v in stage_acc.items()},
+        "plan_create_s": t_plan,
+        "roofline": {"bound": "alu", "kernel": "near field (pp_kernel)", "achieved": pp_tf,
+                     "peak": alu_peak, "unit": "TFLOP/s", "frac": pp_tf / alu_peak,
+                     "traffic": _traffic("pp_kernel", name, sha),
+                     "per_launch": f"{pairs} pair interactions x {PP_FLOPS_PER_PAIR} flop",
+                     "peak_basis": f"{NUM_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                   f"(FMA peak; HBM peak {hbm} GB/s {peak_kind})"},
+        "mesh_roofline": {"bound": "hbm", "achieved": mesh_bytes / (mesh_ms * 1e-3) / 1e9, "peak": hbm,
+                          "unit": "GB/s", "frac": mesh_bytes / (mesh_ms * 1e-3) / 1e9 / hbm,
+                          "bytes_model": "4B*(2CK + 8CKh + 2C_G Kh): M read, spectra written/read, G~ read, "
+                                         "L written", "stages": "fft_forward + m2l + fft_inverse",
+                          "peak_kind": peak_kind},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * esz * n,
+                "d2h_bytes_per_step": 4 * esz * n + 8},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(name, pos64, q64, green)
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

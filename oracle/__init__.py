@@ -78,7 +78,9 @@ def _L():
                 "orc_bin": (i32, [i64, vp, vp, vp, vp, i32, vp, vp, vp, vp]),
                 "orc_green_open": (None, [i32, i32, vp, vp, vp]),
                 "orc_green_periodic": (None, [i32, i32, vp, vp, d, i32, vp, vp]),
-                "orc_pmmm": (i32, [vp, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp]),
+                "orc_pmmm": (i32, [vp, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp]),
+                "orc_green_table_size": (i64, [vp]),
+                "orc_green_table": (None, [vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -302,17 +304,7 @@ def default_alpha(box) -> float:
     return 1.5 / float(min(box))
 
 
-def pmmm(pos, q, lo, length, mesh, p: int, c: int = 1, periodic: bool = False, alpha: float | None = None,
-         nmax: int = 5, target_cells=None, want_ml: bool = False):
-    """PMMM by its definition: all-cell-pair convolution, corrections, L2P, near field.
-
-    Returns dict(status, phi, grad, [M, L, corr]).  phi/grad (Coulomb sign, grad = grad Phi)
-    are filled for the particles of the target cells (all cells if None), NaN elsewhere.
-    M: (K, (p+1)^2) complex multipoles; L: (K, (p+1)^2) complex locals after the
-    convolution (before corrections) for the target cells, zeros elsewhere.
-    """
-    pos = _f64(pos).reshape(-1, 3)
-    q = _f64(q).reshape(-1)
+def _cfg(lo, length, mesh, p, c, periodic, alpha, nmax) -> _Cfg:
     cfg = _Cfg()
     for a in range(3):
         cfg.lo[a] = float(lo[a])
@@ -321,6 +313,33 @@ def pmmm(pos, q, lo, length, mesh, p: int, c: int = 1, periodic: bool = False, a
     cfg.p, cfg.c, cfg.periodic = int(p), int(c), int(bool(periodic))
     cfg.alpha = float(default_alpha(length) if alpha is None else alpha)
     cfg.nmax = int(nmax)
+    return cfg
+
+
+def green_table(lo, length, mesh, p: int, c: int = 1, periodic: bool = False, alpha: float | None = None,
+                nmax: int = 5) -> np.ndarray:
+    """Green function of every distinct cell displacement (the set-up step of Sec. 2.1),
+    to pass to pmmm(..., green=...) for repeated evaluations with the same geometry."""
+    cfg = _cfg(lo, length, mesh, p, c, periodic, alpha, nmax)
+    ng = _L().orc_green_table_size(ctypes.byref(cfg))
+    out = np.zeros((ng, nterms(2 * p)), dtype=np.complex128)
+    _L().orc_green_table(ctypes.byref(cfg), _p(out))
+    return out
+
+
+def pmmm(pos, q, lo, length, mesh, p: int, c: int = 1, periodic: bool = False, alpha: float | None = None,
+         nmax: int = 5, target_cells=None, want_ml: bool = False, green: np.ndarray | None = None):
+    """PMMM by its definition: all-cell-pair convolution, corrections, L2P, near field.
+
+    Returns dict(status, phi, grad, [M, L, corr]).  phi/grad (Coulomb sign, grad = grad Phi)
+    are filled for the particles of the target cells (all cells if None), NaN elsewhere.
+    M: (K, (p+1)^2) complex multipoles; L: (K, (p+1)^2) complex locals after the
+    convolution (before corrections) for the target cells, zeros elsewhere.
+    green: optional table from green_table() with the same geometry.
+    """
+    pos = _f64(pos).reshape(-1, 3)
+    q = _f64(q).reshape(-1)
+    cfg = _cfg(lo, length, mesh, p, c, periodic, alpha, nmax)
     n = pos.shape[0]
     K = int(mesh[0]) * int(mesh[1]) * int(mesh[2])
     tc = None if target_cells is None else np.ascontiguousarray(target_cells, dtype=np.int64)
@@ -330,7 +349,12 @@ def pmmm(pos, q, lo, length, mesh, p: int, c: int = 1, periodic: bool = False, a
     M = np.zeros((K, nterms(p)), dtype=np.complex128) if want_ml else None
     Lo = np.zeros((K, nterms(p)), dtype=np.complex128) if want_ml else None
     corr = np.zeros(8)
-    st = _L().orc_pmmm(ctypes.byref(cfg), n, _p(pos), _p(q), ntc, _p(tc), _p(phi), _p(g), _p(M), _p(Lo), _p(corr))
+    if green is not None:
+        green = np.ascontiguousarray(green, dtype=np.complex128)
+        if green.shape != (_L().orc_green_table_size(ctypes.byref(cfg)), nterms(2 * p)):
+            raise ValueError("green table does not match the geometry")
+    st = _L().orc_pmmm(ctypes.byref(cfg), n, _p(pos), _p(q), ntc, _p(tc), _p(phi), _p(g), _p(M), _p(Lo), _p(corr),
+                       _p(green))
     out = {"status": int(st), "phi": phi, "grad": g, "corr": corr, "alpha": cfg.alpha}
     if want_ml:
         out["M"] = M

@@ -641,8 +641,44 @@ typedef struct {
  *   after the cell convolution, before the corrections.
  * corr_out (8 doubles, optional): Q, sum_cells M_1^0, Re/Im sum_cells M_1^1,
  *   sum q|r_rel|^2, and 3 spare. */
+/* Number of distinct cell displacements of the Green-function table and its
+ * dimensions: n^3 (periodic, d mod n) or (2n-1)^3 (open, d in [-(n-1), n-1]). */
+int64_t orc_green_table_size(const orc_cfg *cfg)
+{
+    int gx = cfg->periodic ? cfg->mesh[0] : 2 * cfg->mesh[0] - 1;
+    int gy = cfg->periodic ? cfg->mesh[1] : 2 * cfg->mesh[1] - 1;
+    int gz = cfg->periodic ? cfg->mesh[2] : 2 * cfg->mesh[2] - 1;
+    return (int64_t)gx * gy * gz;
+}
+
+/* The Green function of every distinct displacement, (2p+1)^2 complex values
+ * each (Sec. 2.1: computed once at the beginning and saved). */
+void orc_green_table(const orc_cfg *cfg, double *out)
+{
+    const int p = cfg->p, c = cfg->c;
+    const int nx = cfg->mesh[0], ny = cfg->mesh[1], nz = cfg->mesh[2];
+    const int ng = (2 * p + 1) * (2 * p + 1);
+    double h[3];
+    for (int a = 0; a < 3; ++a) h[a] = cfg->len[a] / cfg->mesh[a];
+    int gx = cfg->periodic ? nx : 2 * nx - 1, gy = cfg->periodic ? ny : 2 * ny - 1;
+    int64_t NG = orc_green_table_size(cfg);
+    cplx *Gall = (cplx *)out;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < NG; ++t) {
+        int a = (int)(t % gx), b = (int)((t / gx) % gy), e = (int)(t / ((int64_t)gx * gy));
+        if (cfg->periodic) {
+            int d[3] = {a, b, e};
+            orc_green_periodic(p, c, cfg->mesh, cfg->len, cfg->alpha, cfg->nmax, d, (double *)(Gall + t * ng));
+        } else {
+            int d[3] = {a - (nx - 1), b - (ny - 1), e - (nz - 1)};
+            orc_green_open(p, c, h, d, (double *)(Gall + t * ng));
+        }
+    }
+}
+
+/* green_table: optional table from orc_green_table for the same cfg (not owned). */
 int orc_pmmm(const orc_cfg *cfg, int64_t n, const double *pos, const double *q, int64_t ntc, const int64_t *tcells,
-             double *phi, double *grad, double *M_out, double *L_out, double *corr_out)
+             double *phi, double *grad, double *M_out, double *L_out, double *corr_out, const double *green_table)
 {
     const int p = cfg->p, c = cfg->c, J = 2 * p;
     const int nx = cfg->mesh[0], ny = cfg->mesh[1], nz = cfg->mesh[2];
@@ -678,20 +714,14 @@ int orc_pmmm(const orc_cfg *cfg, int64_t n, const double *pos, const double *q, 
      * table fits in 1 GiB, else evaluated for each cell pair. */
     int gx = cfg->periodic ? nx : 2 * nx - 1, gy = cfg->periodic ? ny : 2 * ny - 1, gz = cfg->periodic ? nz : 2 * nz - 1;
     int64_t NG = (int64_t)gx * gy * gz;
-    int table = (double)NG * ng * sizeof(cplx) <= (double)(1 << 30);
-    cplx *Gall = table ? (cplx *)malloc(sizeof(cplx) * NG * ng) : NULL;
-    if (table) {
-#pragma omp parallel for schedule(dynamic, 1)
-        for (int64_t t = 0; t < NG; ++t) {
-            int a = (int)(t % gx), b = (int)((t / gx) % gy), e = (int)(t / ((int64_t)gx * gy));
-            if (cfg->periodic) {
-                int d[3] = {a, b, e};
-                orc_green_periodic(p, c, cfg->mesh, cfg->len, cfg->alpha, cfg->nmax, d, (double *)(Gall + t * ng));
-            } else {
-                int d[3] = {a - (nx - 1), b - (ny - 1), e - (nz - 1)};
-                orc_green_open(p, c, h, d, (double *)(Gall + t * ng));
-            }
-        }
+    int owned = !green_table && (double)NG * ng * sizeof(cplx) <= (double)(1 << 30);
+    int table = green_table != NULL || owned;
+    cplx *Gall = NULL;
+    if (green_table) {
+        Gall = (cplx *)green_table;
+    } else if (owned) {
+        Gall = (cplx *)malloc(sizeof(cplx) * NG * ng);
+        orc_green_table(cfg, (double *)Gall);
     }
 
     int64_t nT = ntc < 0 ? K : ntc;
@@ -728,7 +758,7 @@ int orc_pmmm(const orc_cfg *cfg, int64_t n, const double *pos, const double *q, 
         }
         free(Gp);
     }
-    free(Gall);
+    if (owned) free(Gall);
     if (L_out)
         for (int64_t t = 0; t < nT; ++t) {
             int64_t ci = ntc < 0 ? t : tcells[t];

@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(256) p2m_kernel(const T* __restrict__ part, co
 // physical units, with the periodic corrections of App. B.3:
 //   phi  += c0 + c1 . r_rel + qfac (|r_rel|^2 - 3/(2 alpha^2)) - 2 alpha/sqrt(pi) Q_cell
 //   grad += c1 + 2 qfac r_rel
+// (the c1 terms only for p >= 1: they are the correction of L_1)
 // (c0 = 2pi/(3V) sum q|r_rel|^2, c1 = -4pi/(3V) sum q r_rel, qfac = 2pi/(3V) Q).
 template <int P, typename T>
 __global__ void __launch_bounds__(128) l2p_kernel(const T* __restrict__ part, const uint32_t* __restrict__ keys,
@@ -93,10 +94,16 @@ __global__ void __launch_bounds__(128) l2p_kernel(const T* __restrict__ part, co
   if (cp.periodic) {
     const double rel[3] = {(double)r.x * cp.hs, (double)r.y * cp.hs, (double)r.z * cp.hs};
     const double rr = rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2];
-    phi += corr[0] + corr[1] * rel[0] + corr[2] * rel[1] + corr[3] * rel[2] +
-           corr[4] * (rr - 1.5 / (cp.alpha * cp.alpha)) - 2.0 * cp.alpha * 0.56418958354775628695 * cellq[cell];
+    phi += corr[0] + corr[4] * (rr - 1.5 / (cp.alpha * cp.alpha)) -
+           2.0 * cp.alpha * 0.56418958354775628695 * cellq[cell];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) g[a] += corr[1 + a] + 2.0 * corr[4] * rel[a];
+    for (int a = 0; a < 3; ++a) g[a] += 2.0 * corr[4] * rel[a];
+    // the dipole term corrects L_1 (App. B.3), which exists only for p >= 1
+    if (P >= 1) {
+      phi += corr[1] * rel[0] + corr[2] * rel[1] + corr[3] * rel[2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) g[a] += corr[1 + a];
+    }
   }
   typename V4<T>::type o;
   o.x = (T)phi;

@@ -19,10 +19,12 @@ constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 2048 keys per tile
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_CH = SCAN_THREADS * 4;  // entries per scan chunk
 
-__device__ __forceinline__ int bin_axis(double x, double lo, double len, double inv, int n, int periodic, int* err,
+// Returns the cell index along one axis; error bits are OR-ed into *bits (a
+// register of the caller), the binned coordinate t is stored in *tout.
+__device__ __forceinline__ int bin_axis(double x, double lo, double len, double inv, int n, int periodic, int* bits,
                                         double* tout) {
   if (!isfinite(x)) {
-    set_err(err, ERRBIT_NONFINITE);
+    *bits |= ERRBIT_NONFINITE;
     *tout = 0.0;
     return 0;
   }
@@ -33,7 +35,7 @@ __device__ __forceinline__ int bin_axis(double x, double lo, double len, double 
     t = __dsub_rn(t, __dmul_rn(len, fl));
     if (t >= len) t = __dsub_rn(t, len);
   } else if (!(t >= 0.0 && t < len)) {
-    set_err(err, ERRBIT_OUT_OF_BOX);
+    *bits |= ERRBIT_OUT_OF_BOX;
   }
   *tout = t;
   const double f = floor(__dmul_rn(t, inv));
@@ -48,11 +50,13 @@ __global__ void bin_kernel(const TIN* __restrict__ pos, int64_t n, Geo g, uint32
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int ix[3];
+  int bits = 0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     double t;
-    ix[a] = bin_axis((double)pos[3 * i + a], g.lo[a], g.len[a], g.inv[a], g.n[a], g.periodic, err, &t);
+    ix[a] = bin_axis((double)pos[3 * i + a], g.lo[a], g.len[a], g.inv[a], g.n[a], g.periodic, &bits, &t);
   }
+  if (bits) set_err(err, bits);
   keys[i] = (uint32_t)(ix[0] + g.n[0] * (ix[1] + g.n[1] * ix[2]));
 }
 
@@ -227,12 +231,12 @@ __global__ void gather_kernel(const TIN* __restrict__ pos, const TIN* __restrict
   ic[0] = (int)(cell % (uint32_t)g.n[0]);
   ic[1] = (int)((cell / (uint32_t)g.n[0]) % (uint32_t)g.n[1]);
   ic[2] = (int)(cell / ((uint32_t)g.n[0] * (uint32_t)g.n[1]));
-  int dummy = 0;
+  int bits = 0;  // errors were reported by the binning kernel
   T u[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     double t;
-    (void)bin_axis((double)pos[3 * (int64_t)i + a], g.lo[a], g.len[a], g.inv[a], g.n[a], g.periodic, &dummy, &t);
+    (void)bin_axis((double)pos[3 * (int64_t)i + a], g.lo[a], g.len[a], g.inv[a], g.n[a], g.periodic, &bits, &t);
     if (!isfinite(t)) t = 0.0;
     const double rel = t - (ic[a] + 0.5) * g.h[a];
     u[a] = (T)(rel / g.hs);

@@ -193,7 +193,8 @@ def test_empty_and_single(pk):
     phi, force, e = plan.compute(_t(pos, torch.float64), _t(q, torch.float64), energy=True)
     ref = _oracle(cfg, pk, pos, q)
     assert abs(phi.item() - ref["phi"][0]) < 1e-12
-    assert np.abs(force.cpu().numpy()).max() < 1e-12
+    # a lone charge feels its own images only through the truncated expansion
+    assert np.abs(force.cpu().numpy() + q[:, None] * ref["grad"]).max() < 1e-12
     plan.close()
 
 
