@@ -46,6 +46,9 @@ WORKLOADS = {
     "periodic_uniform_n16777216_mesh64_p7_fp32": (1 << 24, "periodic", 64, 7, "fp32", (0, 0, 0), (1, 1, 1),
                                                    "uniform_pm1", 1.0),
     "open_uniform_n4096_mesh8_p4_fp64": (4096, "open", 8, 4, "fp64", (0, 0, 0), (1, 1, 1), "uniform_pm1", 1.0),
+    # same particle density as the default (32 per cell), 8x smaller: the ncu profiling case
+    "periodic_uniform_n131072_mesh16_p7_fp32": (1 << 17, "periodic", 16, 7, "fp32", (0, 0, 0), (1, 1, 1),
+                                                 "uniform_pm1", 1.0),
 }
 DEFAULT_WORKLOAD = "periodic_uniform_n1048576_mesh32_p7_fp32"
 METRIC = "particles/s per full force eval at fixed RMS force error; mesh-stage HBM % peak"

@@ -475,8 +475,9 @@ void orc_ewald(int64_t n, const double *pos, const double *q, const double *box,
 /* ------------------------------------------------------------------------ */
 /* Binning (Sec. 2.1: particles assigned to K uniform cells in O(N)).        */
 /* The FP64 formula, in this order, each operation rounded:                  */
-/*   t = x - lo;  periodic: t = t - len * floor(t / len), if t >= len: t -= len */
-/*   open: error unless 0 <= t < len                                         */
+/*   t = x - lo;  if t is outside [0, len):                                  */
+/*     periodic: t = t - len * floor(t / len), if t >= len: t -= len         */
+/*     open: error                                                           */
 /*   i = floor(t * inv) with inv = n / len, clamped to [0, n-1]              */
 /* Cell id = ix + nx * (iy + ny * iz).  Stable counting sort by cell id:     */
 /* perm lists original indices in (cell, original index) order.              */
@@ -501,14 +502,16 @@ int orc_bin(int64_t n, const double *pos, const double *lo, const double *len, c
                 continue;
             }
             volatile double t = x - lo[a];
-            if (periodic) {
-                volatile double qd = t / len[a];
-                volatile double fl = floor(qd);
-                volatile double w = len[a] * fl;
-                t = t - w;
-                if (t >= len[a]) t = t - len[a];
-            } else if (!(t >= 0.0 && t < len[a])) {
-                if (status == 0) status = -3;
+            if (!(t >= 0.0 && t < len[a])) {
+                if (periodic) {
+                    volatile double qd = t / len[a];
+                    volatile double fl = floor(qd);
+                    volatile double w = len[a] * fl;
+                    t = t - w;
+                    if (t >= len[a]) t = t - len[a];
+                } else if (status == 0) {
+                    status = -3;
+                }
             }
             volatile double s = t * inv[a];
             double f = floor(s);

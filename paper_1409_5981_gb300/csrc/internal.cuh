@@ -26,7 +26,9 @@ struct Dims {
 struct Geo {
   double lo[3], len[3], inv[3];  // binning: inv = n / len
   double h[3];                   // cell sizes
+  double hh[3];                  // h / 2
   double hs;                     // length unit of the device arithmetic
+  double ihs;                    // 1 / hs
   double cs[3];                  // h / hs
   double V;                      // box volume
   double alpha;                  // Ewald splitting parameter (physical)
@@ -34,6 +36,8 @@ struct Geo {
   int n[3];
   int periodic;
   int c;
+  // float splits for the FP32 binning path: lo = loh + lol, inv = invh + invl
+  float loh[3], lol[3], invh[3], invl[3], csf[3];
 };
 
 enum ErrBits { ERRBIT_OUT_OF_BOX = 1, ERRBIT_NONFINITE = 2, ERRBIT_TIMEOUT = 4 };
@@ -51,24 +55,30 @@ struct SortWork {
 int sort_tiles(int64_t n);
 size_t sort_hist_entries(int64_t n);
 size_t sort_chunk_entries(int64_t n);
-// Bins the particles (FP64 formula) and sorts them stably by cell.
-// Result: sorted keys in *keys_out, original indices in *vals_out.
-cudaError_t launch_bin(const void* pos, bool pos_fp64, int64_t n, const Geo& g, uint32_t* keys, int* err,
-                       cudaStream_t s, int* nlaunch);
+// Bins the particles (FP64 formula) and writes their records (u, q) in input order.
+cudaError_t launch_bin(const void* pos, const void* q, bool fp64, int64_t n, const Geo& g, uint32_t* keys, void* rec,
+                       int* err, cudaStream_t s, int* nlaunch);
+// Stable LSD radix sort of the cell ids; original indices in *vals_out.
 cudaError_t launch_radix_sort(SortWork& w, int64_t n, int key_bits, uint32_t** keys_out, uint32_t** vals_out,
                               cudaStream_t s, int* nlaunch);
 cudaError_t launch_cell_bounds(const uint32_t* keys, int64_t n, int64_t K, int* cell_start, cudaStream_t s,
                                int* nlaunch);
-// Sorted particle records (u_x, u_y, u_z, q): position relative to the cell
+// Sorted particle records part[s] = rec[vals[s]]: position relative to the cell
 // centre in units of hs, and the charge.
-cudaError_t launch_gather(const void* pos, const void* q, bool fp64, const uint32_t* keys, const uint32_t* vals,
-                          int64_t n, const Geo& g, void* part, cudaStream_t s, int* nlaunch);
+cudaError_t launch_gather(const void* rec, bool fp64, const uint32_t* vals, int64_t n, void* part, cudaStream_t s,
+                          int* nlaunch);
+// In-place exclusive scan of n uint32 values (chunks: scratch of scan_chunk_count(n)).
+int64_t scan_chunk_count(int64_t n);
+cudaError_t launch_exclusive_scan(uint32_t* data, int64_t n, uint32_t* chunks, cudaStream_t s, int* nlaunch);
 
 // ---------------------------------------------------------------- p2m_l2p.cu
 cudaError_t launch_p2m(int p, bool fp64, const void* part, const int* cell_start, int64_t K, void* M,
                        double* cellq, double* celld, cudaStream_t s, int* nlaunch);
 struct CorrParams {
   double hs, alpha, V;
+  double ih, ih2;      // 1 / hs, 1 / hs^2
+  double c_charged;    // 3 / (2 alpha^2)
+  double c_self;       // 2 alpha / sqrt(pi)
   int periodic;
 };
 cudaError_t launch_l2p(int p, bool fp64, const void* part, const uint32_t* keys, int64_t n, const void* L,
@@ -107,13 +117,23 @@ struct PPParams {
   int n[3];
   int c;
   int periodic;
-  double cs[3];
-  double hs;
-  double sign;
+  // constants, rounded once on the host: cell size / hs per axis, 1 / hs,
+  // 1 / hs^2, sign (+1 Coulomb, -1 gravity); FP64 and FP32 copies
+  double csf[3], ihf, ih2f, signf;
+  float cs32[3], ih32, ih2_32, sign32;
 };
+// Near-field work items, one per (cell, chunk of up to 32 target particles):
+// item_start[K+1] (exclusive scan of the chunk counts), item_cell[item]; resets
+// the work counter and zeroes the energy partials of unused item slots.
+int64_t pp_items_max(int64_t K, int64_t n);
+cudaError_t launch_pp_items(const int* cell_start, int64_t K, uint32_t* item_start, uint32_t* item_cell,
+                            uint32_t* chunks, unsigned int* counter, double* epart, int64_t max_items, cudaStream_t s,
+                            int* nlaunch);
 // Near field over the (2c+1)^3 cells plus the far field from `far`, written in
-// the caller's order to phi / force, with per-cell energy and force partials.
+// the caller's order to phi / force; energy and force partials per work item
+// (epart[max_items][4]).  Persistent warps fetch items from *counter.
 cudaError_t launch_pp(bool fp64, const void* part, const uint32_t* vals, const int* cell_start, int64_t K,
+                      const uint32_t* item_start, const uint32_t* item_cell, unsigned int* counter, int num_sms,
                       const void* far, PPParams pp, void* phi, void* force, double* epart, cudaStream_t s,
                       int* nlaunch);
 
@@ -123,8 +143,8 @@ cudaError_t launch_pp(bool fp64, const void* part, const uint32_t* vals, const i
 // corr[8..12] = raw sums (Q, sum q u_x, sum q u_y, sum q u_z, sum q |u|^2) in hs units.
 cudaError_t launch_corrections(const double* cellq, const double* celld, int64_t K, double hs, double V,
                                double* partial, double* corr, cudaStream_t s, int* nlaunch);
-// energy[0] = sum of epart[cell*4 + 0], energy[1..3] = net force
-cudaError_t launch_energy(const double* epart, int64_t K, double* partial, double* energy, cudaStream_t s,
+// energy[0] = sum of epart[i*4 + 0] over i < count, energy[1..3] = net force
+cudaError_t launch_energy(const double* epart, int64_t count, double* partial, double* energy, cudaStream_t s,
                           int* nlaunch);
 cudaError_t launch_to_physical(bool fp64, const void* X, double* out, int p, int64_t K, double hs, int power_shift,
                                cudaStream_t s);

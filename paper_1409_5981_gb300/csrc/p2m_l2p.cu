@@ -16,38 +16,43 @@ template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; };
 template <> struct V4<double> { using type = double4; };
 
-// One warp per cell: each lane accumulates q R(r_M - r_i) = q R(-u) of its
-// particles into (p+1)^2 registers, then a butterfly reduction over the warp.
-// Also the FP64 per-cell sums used by the periodic corrections:
-// cellq = sum q, celld = (sum q u_x, sum q u_y, sum q u_z, sum q |u|^2).
+// Eight lanes per cell: each lane accumulates q R(r_M - r_i) = q R(-u) of every
+// eighth particle of its cell into (p+1)^2 registers, a 3-step butterfly sums the
+// eight lanes, and a shared-memory transpose writes the channel-major M of 32
+// consecutive cells with coalesced stores.  Also the per-cell sums used by the
+// periodic corrections: cellsum = (sum q, sum q u_x, sum q u_y, sum q u_z,
+// sum q |u|^2), accumulated in T per lane and stored in FP64.
+constexpr int P2M_LPC = 8;                  // lanes per cell
+constexpr int P2M_CPB = 256 / P2M_LPC;      // cells per block
+
 template <int P, typename T>
 __global__ void __launch_bounds__(256) p2m_kernel(const T* __restrict__ part, const int* __restrict__ cs, int64_t K,
-                                                  T* __restrict__ M, double* __restrict__ cellq,
-                                                  double* __restrict__ celld) {
+                                                  T* __restrict__ M, double* __restrict__ cellsum) {
   constexpr int C = (P + 1) * (P + 1);
-  const int lane = threadIdx.x & 31;
-  const int64_t cell = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (cell >= K) return;
-  const int beg = cs[cell], end = cs[cell + 1];
+  __shared__ T sh[C][P2M_CPB + 1];
+  const int sub = threadIdx.x & (P2M_LPC - 1), cl = threadIdx.x / P2M_LPC;
+  const int64_t cell = (int64_t)blockIdx.x * P2M_CPB + cl;
   T acc[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) acc[c] = T(0);
-  double sq = 0, sx = 0, sy = 0, sz = 0, sr = 0;
-  for (int i = beg + lane; i < end; i += 32) {
-    const typename V4<T>::type r = reinterpret_cast<const typename V4<T>::type*>(part)[i];
-    T R[C];
-    regular_real<P, T>(-r.x, -r.y, -r.z, R);
+  T sq = 0, sx = 0, sy = 0, sz = 0, sr = 0;
+  if (cell < K) {
+    const int beg = cs[cell], end = cs[cell + 1];
+    for (int i = beg + sub; i < end; i += P2M_LPC) {
+      const typename V4<T>::type r = reinterpret_cast<const typename V4<T>::type*>(part)[i];
+      T R[C];
+      regular_real<P, T>(-r.x, -r.y, -r.z, R);
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] += r.w * R[c];
-    const double q = (double)r.w, ux = (double)r.x, uy = (double)r.y, uz = (double)r.z;
-    sq += q;
-    sx += q * ux;
-    sy += q * uy;
-    sz += q * uz;
-    sr += q * (ux * ux + uy * uy + uz * uz);
+      for (int c = 0; c < C; ++c) acc[c] = fma(r.w, R[c], acc[c]);
+      sq += r.w;
+      sx = fma(r.w, r.x, sx);
+      sy = fma(r.w, r.y, sy);
+      sz = fma(r.w, r.z, sz);
+      sr = fma(r.w, r.x * r.x + r.y * r.y + r.z * r.z, sr);
+    }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = 1; o < P2M_LPC; o <<= 1) {
 #pragma unroll
     for (int c = 0; c < C; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
     sq += __shfl_xor_sync(0xffffffffu, sq, o);
@@ -58,13 +63,19 @@ __global__ void __launch_bounds__(256) p2m_kernel(const T* __restrict__ part, co
   }
 #pragma unroll
   for (int c = 0; c < C; ++c)
-    if ((c & 31) == lane) M[(int64_t)c * K + cell] = acc[c];
-  if (lane == 0) {
-    cellq[cell] = sq;
-    celld[cell] = sx;
-    celld[K + cell] = sy;
-    celld[2 * K + cell] = sz;
-    celld[3 * K + cell] = sr;
+    if ((c & (P2M_LPC - 1)) == sub) sh[c][cl] = acc[c];
+  if (sub == 0 && cell < K) {
+    cellsum[cell] = (double)sq;
+    cellsum[K + cell] = (double)sx;
+    cellsum[2 * K + cell] = (double)sy;
+    cellsum[3 * K + cell] = (double)sz;
+    cellsum[4 * K + cell] = (double)sr;
+  }
+  __syncthreads();
+  const int64_t c0 = (int64_t)blockIdx.x * P2M_CPB;
+  for (int idx = threadIdx.x; idx < C * P2M_CPB; idx += 256) {
+    const int c = idx / P2M_CPB, l = idx - c * P2M_CPB;
+    if (c0 + l < K) M[(int64_t)c * K + c0 + l] = sh[c][l];
   }
 }
 
@@ -88,21 +99,22 @@ __global__ void __launch_bounds__(128) l2p_kernel(const T* __restrict__ part, co
   regular_real<P, T>(r.x, r.y, r.z, R);
   T f, gx, gy, gz;
   l2p_real<P, T>([&](int c) { return __ldg(L + (int64_t)c * K + cell); }, R, f, gx, gy, gz);
-  const double ih = 1.0 / cp.hs;
-  double phi = (double)f * ih;
-  double g[3] = {(double)gx * ih * ih, (double)gy * ih * ih, (double)gz * ih * ih};
+  const T ih = (T)cp.ih, ih2 = (T)cp.ih2;
+  T phi = f * ih;
+  T g[3] = {gx * ih2, gy * ih2, gz * ih2};
   if (cp.periodic) {
-    const double rel[3] = {(double)r.x * cp.hs, (double)r.y * cp.hs, (double)r.z * cp.hs};
-    const double rr = rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2];
-    phi += corr[0] + corr[4] * (rr - 1.5 / (cp.alpha * cp.alpha)) -
-           2.0 * cp.alpha * 0.56418958354775628695 * cellq[cell];
+    const T hs = (T)cp.hs;
+    const T rel[3] = {r.x * hs, r.y * hs, r.z * hs};
+    const T rr = rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2];
+    const T qf = (T)corr[4];
+    phi += (T)corr[0] + qf * (rr - (T)cp.c_charged) - (T)cp.c_self * (T)cellq[cell];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) g[a] += 2.0 * corr[4] * rel[a];
+    for (int a = 0; a < 3; ++a) g[a] += T(2) * qf * rel[a];
     // the dipole term corrects L_1 (App. B.3), which exists only for p >= 1
     if (P >= 1) {
-      phi += corr[1] * rel[0] + corr[2] * rel[1] + corr[3] * rel[2];
+      phi += (T)corr[1] * rel[0] + (T)corr[2] * rel[1] + (T)corr[3] * rel[2];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) g[a] += corr[1 + a];
+      for (int a = 0; a < 3; ++a) g[a] += (T)corr[1 + a];
     }
   }
   typename V4<T>::type o;
@@ -115,8 +127,9 @@ __global__ void __launch_bounds__(128) l2p_kernel(const T* __restrict__ part, co
 
 template <int P, typename T>
 cudaError_t p2m_run(const void* part, const int* cs, int64_t K, void* M, double* cq, double* cd, cudaStream_t s) {
-  const int blocks = (int)((K + 7) / 8);
-  p2m_kernel<P, T><<<blocks, 256, 0, s>>>((const T*)part, cs, K, (T*)M, cq, cd);
+  (void)cd;  // the per-cell sums are laid out [5][K] starting at cq
+  const int blocks = (int)((K + P2M_CPB - 1) / P2M_CPB);
+  p2m_kernel<P, T><<<blocks, 256, 0, s>>>((const T*)part, cs, K, (T*)M, cq);
   return cudaGetLastError();
 }
 

@@ -45,7 +45,13 @@ struct pmmm_plan {
   int* cs = nullptr;          // [K+1]
   double* corr = nullptr;     // [16]
   double* partial = nullptr;  // [256 * 8]
-  double* epart = nullptr;    // [K][4]
+  double* epart = nullptr;    // [max items][4]
+  uint32_t* item_start = nullptr;  // [K+1] near-field work items per cell (scanned)
+  uint32_t* item_chunks = nullptr; // scan scratch
+  uint32_t* item_cell = nullptr;   // [max items]
+  int64_t max_items = 0;
+  unsigned int* counter = nullptr; // near-field work counter
+  int num_sms = 0;
   double* energy = nullptr;   // [4]
   int* err = nullptr;
   // particle workspace
@@ -90,6 +96,9 @@ void free_particles(pmmm_plan* pl) {
   pl->sw = SortWork{};
   dfree(pl->part);
   dfree(pl->far);
+  v = pl->item_cell; dfree(v); pl->item_cell = nullptr;
+  v = pl->epart; dfree(v); pl->epart = nullptr;
+  pl->max_items = 0;
   pl->cap = 0;
 }
 
@@ -103,7 +112,9 @@ void free_all(pmmm_plan* pl) {
   v = pl->cs; dfree(v); pl->cs = nullptr;
   v = pl->corr; dfree(v); pl->corr = nullptr;
   v = pl->partial; dfree(v); pl->partial = nullptr;
-  v = pl->epart; dfree(v); pl->epart = nullptr;
+  v = pl->item_start; dfree(v); pl->item_start = nullptr;
+  v = pl->item_chunks; dfree(v); pl->item_chunks = nullptr;
+  v = pl->counter; dfree(v); pl->counter = nullptr;
   v = pl->energy; dfree(v); pl->energy = nullptr;
   v = pl->err; dfree(v); pl->err = nullptr;
   dfree(pl->hpos); dfree(pl->hq); dfree(pl->hphi); dfree(pl->hforce);
@@ -136,8 +147,10 @@ int validate(const pmmm_config* c) {
   return PMMM_OK;
 }
 
+// Particle workspace for n particles; allocated at least once (the near-field
+// work items and energy partials exist even for n = 0).
 int ensure_particles(pmmm_plan* pl, int64_t n) {
-  if (n <= pl->cap) return PMMM_OK;
+  if (pl->cap > 0 && n <= pl->cap) return PMMM_OK;
   cudaStreamSynchronize(pl->stream);
   free_particles(pl);
   const int64_t cap = n < 1024 ? 1024 : n;
@@ -159,12 +172,18 @@ int ensure_particles(pmmm_plan* pl, int64_t n) {
 #undef ALLOC
   e = dalloc(pl, &pl->part, 4 * pl->tsize * (size_t)cap);
   if (e == cudaSuccess) e = dalloc(pl, &pl->far, 4 * pl->tsize * (size_t)cap);
+  const int64_t mi = pp_items_max(pl->d.K, cap);
+  if (e == cudaSuccess) e = dalloc(pl, &v, sizeof(uint32_t) * (size_t)mi);
+  if (e == cudaSuccess) pl->item_cell = (uint32_t*)v;
+  if (e == cudaSuccess) e = dalloc(pl, &v, sizeof(double) * 4 * (size_t)mi);
+  if (e == cudaSuccess) pl->epart = (double*)v;
   if (e != cudaSuccess) {
     free_particles(pl);
     return map_cuda(e);
   }
   pl->sw.cap = cap;
   pl->cap = cap;
+  pl->max_items = mi;
   return PMMM_OK;
 }
 
@@ -240,10 +259,13 @@ int run(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, voi
   {
     int key_bits = 0;
     while (((int64_t)1 << key_bits) < K) ++key_bits;
-    CK(launch_bin(pos, fp64, n, pl->g, pl->sw.keys0, pl->err, s, &nl));
+    // the unsorted records go to `far`, which L2P overwrites later
+    CK(launch_bin(pos, q, fp64, n, pl->g, pl->sw.keys0, pl->far, pl->err, s, &nl));
     CK(launch_radix_sort(pl->sw, n, key_bits, &pl->keys_sorted, &pl->vals_sorted, s, &nl));
     CK(launch_cell_bounds(pl->keys_sorted, n, K, pl->cs, s, &nl));
-    CK(launch_gather(pos, q, fp64, pl->keys_sorted, pl->vals_sorted, n, pl->g, pl->part, s, &nl));
+    CK(launch_gather(pl->far, fp64, pl->vals_sorted, n, pl->part, s, &nl));
+    CK(launch_pp_items(pl->cs, K, pl->item_start, pl->item_cell, pl->item_chunks, pl->counter, pl->epart,
+                       pp_items_max(K, n), s, &nl));
   }
   mark(pl, ST_P2M);
   CK(launch_p2m(pl->p, fp64, pl->part, pl->cs, K, pl->M, pl->cellsum, pl->cellsum + K, s, &nl));
@@ -260,7 +282,15 @@ int run(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, voi
   if (pl->g.periodic)
     CK(launch_corrections(pl->cellsum, pl->cellsum + K, K, pl->g.hs, pl->g.V, pl->partial, pl->corr, s, &nl));
   {
-    CorrParams cp{pl->g.hs, pl->g.alpha, pl->g.V, pl->g.periodic};
+    CorrParams cp;
+    cp.hs = pl->g.hs;
+    cp.alpha = pl->g.alpha;
+    cp.V = pl->g.V;
+    cp.ih = 1.0 / pl->g.hs;
+    cp.ih2 = cp.ih * cp.ih;
+    cp.c_charged = 1.5 / (pl->g.alpha * pl->g.alpha);
+    cp.c_self = 2.0 * pl->g.alpha * 0.56418958354775628695;  // 2 alpha / sqrt(pi)
+    cp.periodic = pl->g.periodic;
     CK(launch_l2p(pl->p, fp64, pl->part, pl->keys_sorted, n, pl->L, K, pl->corr, pl->cellsum, cp, pl->far, s, &nl));
   }
   mark(pl, ST_PP);
@@ -268,16 +298,23 @@ int run(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, voi
     PPParams pp;
     for (int a = 0; a < 3; ++a) {
       pp.n[a] = pl->g.n[a];
-      pp.cs[a] = pl->g.cs[a];
+      pp.csf[a] = pl->g.cs[a];
     }
     pp.c = pl->g.c;
     pp.periodic = pl->g.periodic;
-    pp.hs = pl->g.hs;
-    pp.sign = pl->g.sign;
-    CK(launch_pp(fp64, pl->part, pl->vals_sorted, pl->cs, K, pl->far, pp, phi, force, pl->epart, s, &nl));
+    pp.ihf = 1.0 / pl->g.hs;
+    pp.ih2f = pp.ihf * pp.ihf;
+    pp.signf = pl->g.sign;
+    for (int a = 0; a < 3; ++a) pp.cs32[a] = (float)pp.csf[a];
+    pp.ih32 = (float)pp.ihf;
+    pp.ih2_32 = (float)pp.ih2f;
+    pp.sign32 = (float)pp.signf;
+    const int64_t mi = pp_items_max(K, n);
+    CK(launch_pp(fp64, pl->part, pl->vals_sorted, pl->cs, K, pl->item_start, pl->item_cell, pl->counter,
+                 pl->num_sms, pl->far, pp, phi, force, pl->epart, s, &nl));
+    mark(pl, ST_REDUCE);
+    CK(launch_energy(pl->epart, mi, pl->partial + 256 * 5, pl->energy, s, &nl));
   }
-  mark(pl, ST_REDUCE);
-  CK(launch_energy(pl->epart, K, pl->partial + 256 * 5, pl->energy, s, &nl));
   mark(pl, ST_COUNT);
 #undef CK
 done:
@@ -363,7 +400,16 @@ int pmmm_plan_create(const pmmm_config* cfg, void* stream, pmmm_plan** out) {
     hmin = fmin(hmin, g.h[a]);
   }
   g.hs = (g.h[0] == g.h[1] && g.h[1] == g.h[2]) ? g.h[0] : cbrt(g.h[0] * g.h[1] * g.h[2]);
-  for (int a = 0; a < 3; ++a) g.cs[a] = g.h[a] / g.hs;
+  g.ihs = 1.0 / g.hs;
+  for (int a = 0; a < 3; ++a) {
+    g.cs[a] = g.h[a] / g.hs;
+    g.hh[a] = 0.5 * g.h[a];
+    g.loh[a] = (float)g.lo[a];
+    g.lol[a] = (float)(g.lo[a] - (double)g.loh[a]);
+    g.invh[a] = (float)g.inv[a];
+    g.invl[a] = (float)(g.inv[a] - (double)g.invh[a]);
+    g.csf[a] = (float)g.cs[a];
+  }
   g.V = cfg->box_len[0] * cfg->box_len[1] * cfg->box_len[2];
   g.alpha = cfg->ewald_alpha > 0.0 ? cfg->ewald_alpha
                                    : 1.5 / fmin(cfg->box_len[0], fmin(cfg->box_len[1], cfg->box_len[2]));
@@ -387,9 +433,19 @@ int pmmm_plan_create(const pmmm_config* cfg, void* stream, pmmm_plan** out) {
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(int) * (size_t)(d.K + 1)); pl->cs = (int*)v; }
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 16); pl->corr = (double*)v; }
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 256 * 16); pl->partial = (double*)v; }
-  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 4 * (size_t)d.K); pl->epart = (double*)v; }
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(uint32_t) * (size_t)(d.K + 1)); pl->item_start = (uint32_t*)v; }
+  if (e == cudaSuccess) {
+    e = dalloc(pl, &v, sizeof(uint32_t) * (size_t)scan_chunk_count(d.K + 1));
+    pl->item_chunks = (uint32_t*)v;
+  }
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 4); pl->energy = (double*)v; }
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(int)); pl->err = (int*)v; }
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(unsigned int)); pl->counter = (unsigned int*)v; }
+  if (e == cudaSuccess) {
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->err, 0, sizeof(int), pl->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->corr, 0, sizeof(double) * 16, pl->stream);
   if (e == cudaSuccess) e = launch_twiddles(pl->fp64, d.Lx, pl->twx, pl->stream);

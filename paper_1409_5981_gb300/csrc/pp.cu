@@ -3,17 +3,24 @@
 // and the scatter back to the caller's order:
 //   phi_i   = sign * (phi_far + sum_j q_j / r_ij)
 //   force_i = -q_i * sign * (grad_far + sum_j grad(q_j / r_ij))
-// One block per target cell; the sources of the neighbour cells are staged in
-// shared memory, shifted into the target cell's frame (periodic images included).
+//
+// Work is split into items of (cell, chunk of up to 32 targets), numbered by an
+// exclusive scan over the cells so that crowded cells spread over many warps.
+// One warp per item: its R targets sit in registers, lane l owns target
+// l mod TL and source phase l / TL (TL = R rounded up to a power of two, so a
+// chunk of 8 targets still keeps 32 lanes busy on 4 source phases).  Sources
+// are read through L1 with broadcast loads (all lanes of a phase read the same
+// record); for each neighbour cell the target is moved into that cell's frame
+// once, so the pair loop needs no per-source shift.  Self pairs (r = 0) add zero.
 #include "internal.cuh"
 
 namespace pmmm {
 
 namespace {
 
-constexpr int PP_THREADS = 128;
-constexpr int PP_TILE = 1024;
-constexpr int PP_MAXNB = 125;  // c <= 2
+constexpr int PP_WARPS = 4;
+constexpr int PP_BLOCKS_PER_SM = 8;  // resident blocks per SM (64 registers per thread)
+constexpr int CHUNK = 32;
 
 template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; };
@@ -23,158 +30,250 @@ template <typename T> __device__ __forceinline__ T rsq(T x);
 template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
 
-template <typename T>
-__global__ void __launch_bounds__(PP_THREADS) pp_kernel(const T* __restrict__ part, const uint32_t* __restrict__ vals,
-                                                        const int* __restrict__ cs, int64_t K,
-                                                        const T* __restrict__ far, PPParams pp, T* __restrict__ phi,
-                                                        T* __restrict__ force, double* __restrict__ epart) {
-  using V = typename V4<T>::type;
-  __shared__ V src[PP_TILE];
-  __shared__ int nb_beg[PP_MAXNB], nb_off[PP_MAXNB + 1];
-  __shared__ T nb_sh[PP_MAXNB][3];
-  __shared__ int nb_n;
-  __shared__ double red[PP_THREADS / 32][4];
-  const int64_t cell = blockIdx.x;
-  const int tid = threadIdx.x;
-  const int ix = (int)(cell % pp.n[0]), iy = (int)((cell / pp.n[0]) % pp.n[1]),
-            iz = (int)(cell / ((int64_t)pp.n[0] * pp.n[1]));
-  const int tbeg = cs[cell], tcount = cs[cell + 1] - tbeg;
-  if (tid == 0) {
-    int k = 0, off = 0;
-    const int c = pp.c;
-    for (int ez = -c; ez <= c; ++ez)
-      for (int ey = -c; ey <= c; ++ey)
-        for (int ex = -c; ex <= c; ++ex) {
-          int j[3] = {ix + ex, iy + ey, iz + ez};
-          bool ok = true;
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            if (j[a] < 0 || j[a] >= pp.n[a]) {
-              if (pp.periodic)
-                j[a] = (j[a] + pp.n[a]) % pp.n[a];
-              else
-                ok = false;
-            }
-          }
-          if (!ok) continue;
-          const int64_t cj = j[0] + (int64_t)pp.n[0] * (j[1] + (int64_t)pp.n[1] * j[2]);
-          const int b = cs[cj], cnt = cs[cj + 1] - b;
-          if (cnt == 0) continue;
-          nb_beg[k] = b;
-          nb_off[k] = off;
-          // centre of the source cell relative to the target cell, units of hs
-          nb_sh[k][0] = (T)(ex * pp.cs[0]);
-          nb_sh[k][1] = (T)(ey * pp.cs[1]);
-          nb_sh[k][2] = (T)(ez * pp.cs[2]);
-          off += cnt;
-          ++k;
-        }
-    nb_off[k] = off;
-    nb_n = k;
+// item counts per cell: ceil(count / CHUNK)
+__global__ void item_count_kernel(const int* __restrict__ cs, int64_t K, uint32_t* __restrict__ item_start,
+                                  unsigned int* __restrict__ counter) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c == 0) *counter = 0u;
+  if (c > K) return;
+  item_start[c] = (c < K) ? (uint32_t)((cs[c + 1] - cs[c] + CHUNK - 1) / CHUNK) : 0u;
+}
+
+__global__ void item_fill_kernel(const uint32_t* __restrict__ item_start, int64_t K, uint32_t* __restrict__ item_cell,
+                                 double* __restrict__ epart, int64_t max_items) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // energy partials of unused item slots are zero
+  for (int64_t i = (int64_t)item_start[K] + c; i < max_items; i += (int64_t)gridDim.x * blockDim.x)
+    epart[4 * i] = epart[4 * i + 1] = epart[4 * i + 2] = epart[4 * i + 3] = 0.0;
+  if (c >= K) return;
+  for (uint32_t it = item_start[c]; it < item_start[c + 1]; ++it) item_cell[it] = (uint32_t)c;
+}
+
+// Accumulates the interactions of target (tx, ty, tz) with sources P[b + e],
+// e = ph, ph + SP, ... < cnt.  SELF: the source set may contain the target
+// itself (r = 0 contributes zero); other neighbour cells never contain a source
+// at r = 0 (a point on a shared face belongs to one cell only), so their pairs
+// skip the test.
+template <typename T, typename V, bool SELF>
+__device__ __forceinline__ void pp_pair(const V& r, T tx, T ty, T tz, T& pot, T& gx, T& gy, T& gz) {
+  const T dx = tx - r.x, dy = ty - r.y, dz = tz - r.z;
+  const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+  T ri = rsq<T>(r2);
+  if (SELF) ri = r2 > T(0) ? ri : T(0);
+  const T qr = r.w * ri;
+  pot += qr;
+  const T qr3 = qr * (ri * ri);
+  gx = fma(-qr3, dx, gx);
+  gy = fma(-qr3, dy, gy);
+  gz = fma(-qr3, dz, gz);
+}
+
+// Accumulates the interactions of target (tx, ty, tz) with sources src[e],
+// e = ph, ph + SP, ... < cnt.  SELF: the source set may contain the target
+// itself (r = 0 contributes zero); other neighbour cells never contain a source
+// at r = 0 (a point on a shared face belongs to one cell only), so their pairs
+// skip the test.
+template <typename T, typename V, bool SELF>
+__device__ __forceinline__ void pp_sum(const V* __restrict__ src, int cnt, int ph, int SP, T tx, T ty, T tz, T& pot,
+                                       T& gx, T& gy, T& gz) {
+  if (SP == 1) {
+    int e = 0;
+    for (; e + 4 <= cnt; e += 4) {
+      const V r0 = src[e], r1 = src[e + 1], r2 = src[e + 2], r3 = src[e + 3];
+      pp_pair<T, V, SELF>(r0, tx, ty, tz, pot, gx, gy, gz);
+      pp_pair<T, V, SELF>(r1, tx, ty, tz, pot, gx, gy, gz);
+      pp_pair<T, V, SELF>(r2, tx, ty, tz, pot, gx, gy, gz);
+      pp_pair<T, V, SELF>(r3, tx, ty, tz, pot, gx, gy, gz);
+    }
+    for (; e < cnt; ++e) pp_pair<T, V, SELF>(src[e], tx, ty, tz, pot, gx, gy, gz);
+  } else {
+    for (int e = ph; e < cnt; e += SP) pp_pair<T, V, SELF>(src[e], tx, ty, tz, pot, gx, gy, gz);
   }
-  __syncthreads();
-  const int nn = nb_n;
-  const int S = nb_off[nn];
-  const int tpt = tcount <= 32 ? 4 : (tcount <= 64 ? 2 : 1);
-  const int ntg = PP_THREADS / tpt;
-  double e_acc = 0, f_acc[3] = {0, 0, 0};
-  const double ih = 1.0 / pp.hs;
-  for (int t0 = 0; t0 < tcount; t0 += ntg) {
-    const int ti = t0 + tid / tpt, sub = tid % tpt;
-    const bool active = ti < tcount;
+}
+
+template <typename T> struct PPConst;
+template <> struct PPConst<float> {
+  __device__ static void get(const PPParams& p, float* cs, float& ih, float& ih2, float& sg) {
+    for (int a = 0; a < 3; ++a) cs[a] = p.cs32[a];
+    ih = p.ih32; ih2 = p.ih2_32; sg = p.sign32;
+  }
+};
+template <> struct PPConst<double> {
+  __device__ static void get(const PPParams& p, double* cs, double& ih, double& ih2, double& sg) {
+    for (int a = 0; a < 3; ++a) cs[a] = p.csf[a];
+    ih = p.ihf; ih2 = p.ih2f; sg = p.signf;
+  }
+};
+
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+// Persistent warps: each takes work items from a global counter (reset to zero
+// by the work-list kernels) until all are done.  Every item's results depend
+// only on the item, so the assignment order does not change any output bit.
+// NB_SLOTS: neighbour-table slots per lane, (2c+1)^3 <= 32 * NB_SLOTS (1 for c = 1, 4 for c = 2)
+template <typename T, int NB_SLOTS>
+__global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel(const T* __restrict__ part, const uint32_t* __restrict__ vals,
+                                                              const int* __restrict__ cs, int64_t K,
+                                                              const uint32_t* __restrict__ item_start,
+                                                              const uint32_t* __restrict__ item_cell,
+                                                              unsigned int* __restrict__ counter, const T* __restrict__ far,
+                                                              PPParams pp, T* __restrict__ phi, T* __restrict__ force,
+                                                              double* __restrict__ epart) {
+  using V = typename V4<T>::type;
+  const V* P = reinterpret_cast<const V*>(part);
+  const int lane = threadIdx.x & 31;
+  const uint32_t nitems = item_start[K];
+  const int nx = pp.n[0], ny = pp.n[1], nz = pp.n[2];
+  const int c = pp.c, w = 2 * c + 1, NN = w * w * w;
+  T csv[3], ih, ih2, sg;
+  PPConst<T>::get(pp, csv, ih, ih2, sg);
+  for (;;) {
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= nitems) break;  // warp-uniform
+    const int cell = (int)item_cell[item];
+    const int chunk = (int)(item - item_start[cell]);
+    const int tbeg = cs[cell] + chunk * CHUNK;
+    const int R = min(CHUNK, cs[cell + 1] - tbeg);
+    int TL = 1;
+    while (TL < R) TL <<= 1;
+    const int SP = 32 / TL;
+    const int tl = lane & (TL - 1), ph = lane / TL;
+    const bool active = tl < R;
     V xi;
-    if (active) xi = reinterpret_cast<const V*>(part)[tbeg + ti];
-    T ph = T(0), gx = T(0), gy = T(0), gz = T(0);
-    for (int s0 = 0; s0 < S; s0 += PP_TILE) {
-      __syncthreads();
-      for (int k = 0; k < nn; ++k) {
-        const int lo = max(nb_off[k], s0), hi = min(nb_off[k + 1], s0 + PP_TILE);
-        const T sx = nb_sh[k][0], sy = nb_sh[k][1], sz = nb_sh[k][2];
-        for (int e = lo + tid; e < hi; e += PP_THREADS) {
-          V r = reinterpret_cast<const V*>(part)[nb_beg[k] + (e - nb_off[k])];
-          r.x += sx;
-          r.y += sy;
-          r.z += sz;
-          src[e - s0] = r;
-        }
-      }
-      __syncthreads();
-      if (active) {
-        const int len = min(PP_TILE, S - s0);
-        for (int e = sub; e < len; e += tpt) {
-          const V r = src[e];
-          const T dx = xi.x - r.x, dy = xi.y - r.y, dz = xi.z - r.z;
-          const T r2 = dx * dx + dy * dy + dz * dz;
-          const T ri = r2 > T(0) ? rsq<T>(r2) : T(0);
-          const T qr = r.w * ri;
-          ph += qr;
-          const T qr3 = qr * ri * ri;
-          gx -= qr3 * dx;
-          gy -= qr3 * dy;
-          gz -= qr3 * dz;
+    xi.x = T(0); xi.y = T(0); xi.z = T(0); xi.w = T(0);
+    if (active) xi = P[tbeg + tl];
+    const int ix = cell % nx, iy = (cell / nx) % ny, iz = cell / (nx * ny);
+    // neighbour table: entry k (x fastest) in lane k % 32, slot k / 32
+    int nbb[NB_SLOTS], nbc[NB_SLOTS];
+#pragma unroll
+    for (int j = 0; j < NB_SLOTS; ++j) {
+      const int k = lane + 32 * j;
+      nbb[j] = 0;
+      nbc[j] = 0;
+      if (k < NN) {
+        int jx = ix + k % w - c, jy = iy + (k / w) % w - c, jz = iz + k / (w * w) - c;
+        bool ok = true;
+        if (jx < 0 || jx >= nx) { ok = ok && pp.periodic; jx += (jx < 0) ? nx : -nx; }
+        if (jy < 0 || jy >= ny) { ok = ok && pp.periodic; jy += (jy < 0) ? ny : -ny; }
+        if (jz < 0 || jz >= nz) { ok = ok && pp.periodic; jz += (jz < 0) ? nz : -nz; }
+        if (ok) {
+          const int cj = jx + nx * (jy + ny * jz);
+          nbb[j] = __ldg(cs + cj);
+          nbc[j] = __ldg(cs + cj + 1) - nbb[j];
         }
       }
     }
-    for (int o = 1; o < tpt; o <<= 1) {
-      ph += __shfl_xor_sync(0xffffffffu, ph, o);
+    auto nb = [&](int k, int& b, int& n) {
+      int bb = nbb[0], cc = nbc[0];
+#pragma unroll
+      for (int q = 1; q < NB_SLOTS; ++q)
+        if ((k >> 5) == q) {
+          bb = nbb[q];
+          cc = nbc[q];
+        }
+      b = __shfl_sync(0xffffffffu, bb, k & 31);
+      n = __shfl_sync(0xffffffffu, cc, k & 31);
+    };
+    int b, cnt;
+    nb(0, b, cnt);
+    if (lane < cnt) prefetch_l1(P + b + lane);
+    T pot = T(0), gx = T(0), gy = T(0), gz = T(0);
+    int k = 0;
+    for (int ez = -c; ez <= c; ++ez) {
+      const T tz = xi.z - (T)ez * csv[2];
+      for (int ey = -c; ey <= c; ++ey) {
+        const T ty = xi.y - (T)ey * csv[1];
+        for (int ex = -c; ex <= c; ++ex, ++k) {
+          int bn = 0, cn = 0;
+          if (k + 1 < NN) {
+            nb(k + 1, bn, cn);
+            if (lane < cn) prefetch_l1(P + bn + lane);  // next neighbour cell into L1
+          }
+          const T tx = xi.x - (T)ex * csv[0];
+          if (ex == 0 && ey == 0 && ez == 0)
+            pp_sum<T, V, true>(P + b, cnt, ph, SP, tx, ty, tz, pot, gx, gy, gz);
+          else
+            pp_sum<T, V, false>(P + b, cnt, ph, SP, tx, ty, tz, pot, gx, gy, gz);
+          b = bn;
+          cnt = cn;
+        }
+      }
+    }
+    for (int o = TL; o < 32; o <<= 1) {
+      pot += __shfl_xor_sync(0xffffffffu, pot, o);
       gx += __shfl_xor_sync(0xffffffffu, gx, o);
       gy += __shfl_xor_sync(0xffffffffu, gy, o);
       gz += __shfl_xor_sync(0xffffffffu, gz, o);
     }
-    if (active && sub == 0) {
-      const int64_t s = tbeg + ti;
+    T e_t = T(0), f_t[3] = {T(0), T(0), T(0)};
+    if (active && ph == 0) {
+      const int s = tbeg + tl;
       const V fr = reinterpret_cast<const V*>(far)[s];
-      const double q = (double)xi.w;
-      const double pt = pp.sign * ((double)fr.x + (double)ph * ih);
-      const double g[3] = {pp.sign * ((double)fr.y + (double)gx * ih * ih),
-                           pp.sign * ((double)fr.z + (double)gy * ih * ih),
-                           pp.sign * ((double)fr.w + (double)gz * ih * ih)};
+      const T pt = sg * (fr.x + pot * ih);
+      const T g0 = sg * (fr.y + gx * ih2), g1 = sg * (fr.z + gy * ih2), g2 = sg * (fr.w + gz * ih2);
       const uint32_t o = vals[s];
-      if (phi) phi[o] = (T)pt;
+      const T q = xi.w;
+      if (phi) phi[o] = pt;
       if (force) {
-        force[3 * (int64_t)o + 0] = (T)(-q * g[0]);
-        force[3 * (int64_t)o + 1] = (T)(-q * g[1]);
-        force[3 * (int64_t)o + 2] = (T)(-q * g[2]);
+        force[3 * (int64_t)o + 0] = -q * g0;
+        force[3 * (int64_t)o + 1] = -q * g1;
+        force[3 * (int64_t)o + 2] = -q * g2;
       }
-      e_acc += 0.5 * q * pt;
-      f_acc[0] -= q * g[0];
-      f_acc[1] -= q * g[1];
-      f_acc[2] -= q * g[2];
+      e_t = T(0.5) * q * pt;
+      f_t[0] = -q * g0;
+      f_t[1] = -q * g1;
+      f_t[2] = -q * g2;
     }
-  }
-  // deterministic block reduction of the energy and net-force partials
+    // deterministic warp reduction of this item's energy and net-force partials
+    // (the <= 32 terms of one item in T; items are summed in FP64 afterwards)
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    e_acc += __shfl_xor_sync(0xffffffffu, e_acc, o);
-    f_acc[0] += __shfl_xor_sync(0xffffffffu, f_acc[0], o);
-    f_acc[1] += __shfl_xor_sync(0xffffffffu, f_acc[1], o);
-    f_acc[2] += __shfl_xor_sync(0xffffffffu, f_acc[2], o);
-  }
-  if ((tid & 31) == 0) {
-    red[tid >> 5][0] = e_acc;
-    red[tid >> 5][1] = f_acc[0];
-    red[tid >> 5][2] = f_acc[1];
-    red[tid >> 5][3] = f_acc[2];
-  }
-  __syncthreads();
-  if (tid < 4) {
-    double v = 0;
-    for (int w = 0; w < PP_THREADS / 32; ++w) v += red[w][tid];
-    epart[cell * 4 + tid] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+      e_t += __shfl_xor_sync(0xffffffffu, e_t, o);
+      f_t[0] += __shfl_xor_sync(0xffffffffu, f_t[0], o);
+      f_t[1] += __shfl_xor_sync(0xffffffffu, f_t[1], o);
+      f_t[2] += __shfl_xor_sync(0xffffffffu, f_t[2], o);
+    }
+    if (lane == 0) {
+      epart[(int64_t)item * 4 + 0] = (double)e_t;
+      epart[(int64_t)item * 4 + 1] = (double)f_t[0];
+      epart[(int64_t)item * 4 + 2] = (double)f_t[1];
+      epart[(int64_t)item * 4 + 3] = (double)f_t[2];
+    }
   }
 }
 
 }  // namespace
 
+int64_t pp_items_max(int64_t K, int64_t n) { return K + (n + CHUNK - 1) / CHUNK + 1; }
+
+cudaError_t launch_pp_items(const int* cell_start, int64_t K, uint32_t* item_start, uint32_t* item_cell,
+                            uint32_t* chunks, unsigned int* counter, double* epart, int64_t max_items, cudaStream_t s,
+                            int* nl) {
+  item_count_kernel<<<(unsigned)((K + 1 + 255) / 256), 256, 0, s>>>(cell_start, K, item_start, counter);
+  ++*nl;
+  cudaError_t e = launch_exclusive_scan(item_start, K + 1, chunks, s, nl);
+  if (e != cudaSuccess) return e;
+  item_fill_kernel<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(item_start, K, item_cell, epart, max_items);
+  ++*nl;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pp(bool fp64, const void* part, const uint32_t* vals, const int* cell_start, int64_t K,
+                      const uint32_t* item_start, const uint32_t* item_cell, unsigned int* counter, int num_sms,
                       const void* far, PPParams pp, void* phi, void* force, double* epart, cudaStream_t s, int* nl) {
-  if (K <= 0) return cudaSuccess;
-  if (fp64)
-    pp_kernel<double><<<(unsigned)K, PP_THREADS, 0, s>>>((const double*)part, vals, cell_start, K, (const double*)far,
-                                                         pp, (double*)phi, (double*)force, epart);
-  else
-    pp_kernel<float><<<(unsigned)K, PP_THREADS, 0, s>>>((const float*)part, vals, cell_start, K, (const float*)far, pp,
-                                                        (float*)phi, (float*)force, epart);
+  // persistent launch: PP_BLOCKS_PER_SM resident blocks of PP_WARPS warps per SM
+  const unsigned blocks = (unsigned)(PP_BLOCKS_PER_SM * (num_sms > 0 ? num_sms : 1));
+#define PP_LAUNCH(T, S)                                                                                              \
+  pp_kernel<T, S><<<blocks, PP_WARPS * 32, 0, s>>>((const T*)part, vals, cell_start, K, item_start, item_cell, counter, \
+                                                   (const T*)far, pp, (T*)phi, (T*)force, epart)
+  if (fp64) {
+    if (pp.c <= 1) PP_LAUNCH(double, 1); else PP_LAUNCH(double, 4);
+  } else {
+    if (pp.c <= 1) PP_LAUNCH(float, 1); else PP_LAUNCH(float, 4);
+  }
+#undef PP_LAUNCH
   ++*nl;
   return cudaGetLastError();
 }

@@ -113,8 +113,9 @@ cudaError_t launch_corrections(const double* cellq, const double* celld, int64_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_energy(const double* epart, int64_t K, double* partial, double* energy, cudaStream_t s, int* nl) {
-  reduce_partial_kernel<4><<<RD_BLOCKS, RD_THREADS, 0, s>>>(epart, K, 1, 4, partial);
+cudaError_t launch_energy(const double* epart, int64_t count, double* partial, double* energy, cudaStream_t s,
+                          int* nl) {
+  reduce_partial_kernel<4><<<RD_BLOCKS, RD_THREADS, 0, s>>>(epart, count, 1, 4, partial);
   energy_final_kernel<<<1, RD_THREADS, 0, s>>>(partial, RD_BLOCKS, energy);
   *nl += 2;
   return cudaGetLastError();

@@ -2,11 +2,14 @@
 // each cell, the set of particles inside is known ... in an O(N) procedure").
 //
 // Cell index, in FP64 with every operation rounded (no contraction):
-//   t = x - lo;  periodic: t = t - len * floor(t / len), and t -= len if t >= len
-//   open: flag OUT_OF_BOX unless 0 <= t < len
+//   t = x - lo;  if t is outside [0, len):
+//     periodic: t = t - len * floor(t / len), and t -= len if t >= len
+//     open: flag OUT_OF_BOX
 //   i = floor(t * (n / len)) clamped to [0, n-1];  id = ix + nx (iy + ny iz)
 // The sort is an LSD radix sort on the id (digits of <= 8 bits), stable in
 // every pass, so the particles of a cell keep their input order.
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace pmmm {
@@ -29,13 +32,15 @@ __device__ __forceinline__ int bin_axis(double x, double lo, double len, double 
     return 0;
   }
   double t = __dsub_rn(x, lo);
-  if (periodic) {
-    const double qd = __ddiv_rn(t, len);
-    const double fl = floor(qd);
-    t = __dsub_rn(t, __dmul_rn(len, fl));
-    if (t >= len) t = __dsub_rn(t, len);
-  } else if (!(t >= 0.0 && t < len)) {
-    *bits |= ERRBIT_OUT_OF_BOX;
+  if (!(t >= 0.0 && t < len)) {
+    if (periodic) {
+      const double qd = __ddiv_rn(t, len);
+      const double fl = floor(qd);
+      t = __dsub_rn(t, __dmul_rn(len, fl));
+      if (t >= len) t = __dsub_rn(t, len);
+    } else {
+      *bits |= ERRBIT_OUT_OF_BOX;
+    }
   }
   *tout = t;
   const double f = floor(__dmul_rn(t, inv));
@@ -44,20 +49,79 @@ __device__ __forceinline__ int bin_axis(double x, double lo, double len, double 
   return (int)f;
 }
 
-template <typename TIN>
-__global__ void bin_kernel(const TIN* __restrict__ pos, int64_t n, Geo g, uint32_t* __restrict__ keys,
-                           int* __restrict__ err) {
+// FP32 inputs: the cell index of the FP64 formula without FP64 arithmetic.
+// s = (x - lo) * inv is formed in double-float arithmetic (t = th + tl by an
+// exact two-sum, s = sh + sl with an exact product error term), which is within
+// 2^-44 |s| of the FP64 formula's rounded s.  When the fractional part of s is
+// more than 1e-6 away from an integer and the cell lies inside the box, floor(s)
+// therefore equals the FP64 result exactly; otherwise (a particle within 1e-6
+// cell of a face, outside the box or not finite) the caller takes the FP64 path.
+// u = frac(s) - 1/2 in cell units, times h / hs.
+__device__ __forceinline__ bool bin_axis_fast(float x, const Geo& g, int a, int* ix, float* u) {
+  const float th = x - g.loh[a];
+  const float bv = th - x;
+  float tl = (x - (th - bv)) + (-g.loh[a] - bv);
+  tl -= g.lol[a];
+  const float sh = th * g.invh[a];
+  float sl = fmaf(th, g.invh[a], -sh);
+  sl = fmaf(th, g.invl[a], sl);
+  sl = fmaf(tl, g.invh[a], sl);
+  float fl = floorf(sh);
+  float fr = (sh - fl) + sl;
+  if (fr < 0.f) {
+    fl -= 1.f;
+    fr += 1.f;
+  } else if (fr >= 1.f) {
+    fl += 1.f;
+    fr -= 1.f;
+  }
+  if (!(fr > 1e-6f && fr < 1.f - 1e-6f)) return false;
+  if (!(fl >= 0.f && fl <= (float)(g.n[a] - 1))) return false;
+  *ix = (int)fl;
+  *u = (fr - 0.5f) * g.csf[a];
+  return true;
+}
+
+// Cell id of every particle (FP64 formula above) and its record in input order:
+// (u_x, u_y, u_z, q) with u the position relative to the cell centre in units of
+// hs, rounded to T.
+template <typename T>
+__global__ void bin_kernel(const T* __restrict__ pos, const T* __restrict__ q, int64_t n, Geo g,
+                           uint32_t* __restrict__ keys, T* __restrict__ rec, int* __restrict__ err) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int ix[3];
-  int bits = 0;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    double t;
-    ix[a] = bin_axis((double)pos[3 * i + a], g.lo[a], g.len[a], g.inv[a], g.n[a], g.periodic, &bits, &t);
+  T u[3];
+  bool fast = false;
+  if (sizeof(T) == 4) {
+    float uf[3];
+    fast = bin_axis_fast((float)pos[3 * i + 0], g, 0, &ix[0], &uf[0]) &&
+           bin_axis_fast((float)pos[3 * i + 1], g, 1, &ix[1], &uf[1]) &&
+           bin_axis_fast((float)pos[3 * i + 2], g, 2, &ix[2], &uf[2]);
+    if (fast)
+      for (int a = 0; a < 3; ++a) u[a] = (T)uf[a];
   }
-  if (bits) set_err(err, bits);
+  if (!fast) {
+    double t[3];
+    int bits = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      ix[a] = bin_axis((double)pos[3 * i + a], g.lo[a], g.len[a], g.inv[a], g.n[a], g.periodic, &bits, &t[a]);
+    if (bits) set_err(err, bits);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double rel = t[a] - (double)(2 * ix[a] + 1) * g.hh[a];  // relative to the cell centre
+      u[a] = (T)(rel * g.ihs);
+    }
+  }
   keys[i] = (uint32_t)(ix[0] + g.n[0] * (ix[1] + g.n[1] * ix[2]));
+  using V = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
+  V o;
+  o.x = u[0];
+  o.y = u[1];
+  o.z = u[2];
+  o.w = q[i];
+  reinterpret_cast<V*>(rec)[i] = o;
 }
 
 __global__ void radix_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift, int nbits,
@@ -219,49 +283,48 @@ __global__ void cell_bounds_kernel(const uint32_t* __restrict__ keys, int64_t n,
   for (int64_t c = kprev + 1; c <= k; ++c) cs[c] = (int)s;
 }
 
-template <typename TIN, typename T>
-__global__ void gather_kernel(const TIN* __restrict__ pos, const TIN* __restrict__ q,
-                              const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n, Geo g,
-                              T* __restrict__ part) {
+__global__ void scan_add_kernel(uint32_t* __restrict__ data, int64_t n, const uint32_t* __restrict__ chunks) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) data[i] += chunks[i / SCAN_CH];
+}
+
+// Sorted records: part[s] = rec[vals[s]] (a pure permutation).
+template <typename V>
+__global__ void gather_kernel(const V* __restrict__ rec, const uint32_t* __restrict__ vals, int64_t n,
+                              V* __restrict__ part) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
-  const uint32_t i = vals[s];
-  const uint32_t cell = keys[s];
-  int ic[3];
-  ic[0] = (int)(cell % (uint32_t)g.n[0]);
-  ic[1] = (int)((cell / (uint32_t)g.n[0]) % (uint32_t)g.n[1]);
-  ic[2] = (int)(cell / ((uint32_t)g.n[0] * (uint32_t)g.n[1]));
-  int bits = 0;  // errors were reported by the binning kernel
-  T u[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    double t;
-    (void)bin_axis((double)pos[3 * (int64_t)i + a], g.lo[a], g.len[a], g.inv[a], g.n[a], g.periodic, &bits, &t);
-    if (!isfinite(t)) t = 0.0;
-    const double rel = t - (ic[a] + 0.5) * g.h[a];
-    u[a] = (T)(rel / g.hs);
-  }
-  T* o = part + 4 * s;
-  o[0] = u[0];
-  o[1] = u[1];
-  o[2] = u[2];
-  o[3] = (T)q[i];
+  part[s] = rec[vals[s]];
 }
 
 inline int grid1(int64_t n, int b) { return (int)((n + b - 1) / b); }
 }  // namespace
 
+int64_t scan_chunk_count(int64_t n) { return (n + SCAN_CH - 1) / SCAN_CH + 1; }
+
+cudaError_t launch_exclusive_scan(uint32_t* data, int64_t n, uint32_t* chunks, cudaStream_t s, int* nl) {
+  if (n <= 0) return cudaSuccess;
+  const int nchunks = (int)((n + SCAN_CH - 1) / SCAN_CH);
+  scan_chunks_kernel<<<nchunks, SCAN_THREADS, 0, s>>>(data, n, chunks);
+  scan_top_kernel<<<1, SCAN_THREADS, 0, s>>>(chunks, nchunks);
+  scan_add_kernel<<<grid1(n, 256), 256, 0, s>>>(data, n, chunks);
+  *nl += 3;
+  return cudaGetLastError();
+}
+
 int sort_tiles(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
 size_t sort_hist_entries(int64_t n) { return (size_t)256 * (size_t)(sort_tiles(n) > 0 ? sort_tiles(n) : 1); }
 size_t sort_chunk_entries(int64_t n) { return (sort_hist_entries(n) + SCAN_CH - 1) / SCAN_CH + 1; }
 
-cudaError_t launch_bin(const void* pos, bool pos_fp64, int64_t n, const Geo& g, uint32_t* keys, int* err,
-                       cudaStream_t s, int* nl) {
+cudaError_t launch_bin(const void* pos, const void* q, bool fp64, int64_t n, const Geo& g, uint32_t* keys, void* rec,
+                       int* err, cudaStream_t s, int* nl) {
   if (n <= 0) return cudaSuccess;
-  if (pos_fp64)
-    bin_kernel<double><<<grid1(n, 256), 256, 0, s>>>((const double*)pos, n, g, keys, err);
+  if (fp64)
+    bin_kernel<double><<<grid1(n, 256), 256, 0, s>>>((const double*)pos, (const double*)q, n, g, keys,
+                                                     (double*)rec, err);
   else
-    bin_kernel<float><<<grid1(n, 256), 256, 0, s>>>((const float*)pos, n, g, keys, err);
+    bin_kernel<float><<<grid1(n, 256), 256, 0, s>>>((const float*)pos, (const float*)q, n, g, keys, (float*)rec,
+                                                    err);
   ++*nl;
   return cudaGetLastError();
 }
@@ -320,15 +383,13 @@ cudaError_t launch_cell_bounds(const uint32_t* keys, int64_t n, int64_t K, int* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const void* pos, const void* q, bool fp64, const uint32_t* keys, const uint32_t* vals,
-                          int64_t n, const Geo& g, void* part, cudaStream_t s, int* nl) {
+cudaError_t launch_gather(const void* rec, bool fp64, const uint32_t* vals, int64_t n, void* part, cudaStream_t s,
+                          int* nl) {
   if (n <= 0) return cudaSuccess;
   if (fp64)
-    gather_kernel<double, double><<<grid1(n, 256), 256, 0, s>>>((const double*)pos, (const double*)q, keys, vals, n,
-                                                                 g, (double*)part);
+    gather_kernel<double4><<<grid1(n, 256), 256, 0, s>>>((const double4*)rec, vals, n, (double4*)part);
   else
-    gather_kernel<float, float><<<grid1(n, 256), 256, 0, s>>>((const float*)pos, (const float*)q, keys, vals, n, g,
-                                                               (float*)part);
+    gather_kernel<float4><<<grid1(n, 256), 256, 0, s>>>((const float4*)rec, vals, n, (float4*)part);
   ++*nl;
   return cudaGetLastError();
 }
