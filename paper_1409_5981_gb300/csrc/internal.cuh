@@ -126,16 +126,22 @@ struct PPParams {
 // item_start[K+1] (exclusive scan of the chunk counts), item_cell[item]; resets
 // the work counter and zeroes the energy partials of unused item slots.
 int64_t pp_items_max(int64_t K, int64_t n);
+// source pairs of the FP32 near field: at most (n + K) / 2 + 1
+int64_t pp_pairs_max(int64_t K, int64_t n);
 cudaError_t launch_pp_items(const int* cell_start, int64_t K, uint32_t* item_start, uint32_t* item_cell,
-                            uint32_t* chunks, unsigned int* counter, double* epart, int64_t max_items, cudaStream_t s,
-                            int* nlaunch);
+                            uint32_t* pair_start, uint32_t* chunks, unsigned int* counter, double* epart,
+                            int64_t max_items, cudaStream_t s, int* nlaunch);
+// pair-interleaved FP32 source records (see pp.cu), src2: 32 bytes per pair
+cudaError_t launch_pair_pack(const void* part, const uint32_t* keys, const int* cell_start, const uint32_t* pair_start,
+                             int64_t n, void* src2, cudaStream_t s, int* nlaunch);
 // Near field over the (2c+1)^3 cells plus the far field from `far`, written in
 // the caller's order to phi / force; energy and force partials per work item
-// (epart[max_items][4]).  Persistent warps fetch items from *counter.
-cudaError_t launch_pp(bool fp64, const void* part, const uint32_t* vals, const int* cell_start, int64_t K,
-                      const uint32_t* item_start, const uint32_t* item_cell, unsigned int* counter, int num_sms,
-                      const void* far, PPParams pp, void* phi, void* force, double* epart, cudaStream_t s,
-                      int* nlaunch);
+// (epart[max_items][4]).  Persistent warps fetch items from *counter.  With
+// FP32, c = 1 and src2 given, the packed-FP32 kernel on the pair layout is used.
+cudaError_t launch_pp(bool fp64, const void* part, const void* src2, const uint32_t* pair_start, const uint32_t* vals,
+                      const int* cell_start, int64_t K, const uint32_t* item_start, const uint32_t* item_cell,
+                      unsigned int* counter, int num_sms, const void* far, PPParams pp, void* phi, void* force,
+                      double* epart, cudaStream_t s, int* nlaunch);
 
 // ---------------------------------------------------------------- reduce.cu
 // Sums per-cell FP64 quantities and builds the periodic correction terms:

@@ -51,6 +51,8 @@ struct pmmm_plan {
   uint32_t* item_cell = nullptr;   // [max items]
   int64_t max_items = 0;
   unsigned int* counter = nullptr; // near-field work counter
+  uint32_t* pair_start = nullptr;  // [K+1] FP32 near-field source pairs per cell (scanned)
+  void* src2 = nullptr;            // pair-interleaved FP32 sources
   int num_sms = 0;
   double* energy = nullptr;   // [4]
   int* err = nullptr;
@@ -97,6 +99,7 @@ void free_particles(pmmm_plan* pl) {
   dfree(pl->part);
   dfree(pl->far);
   v = pl->item_cell; dfree(v); pl->item_cell = nullptr;
+  dfree(pl->src2);
   v = pl->epart; dfree(v); pl->epart = nullptr;
   pl->max_items = 0;
   pl->cap = 0;
@@ -115,6 +118,7 @@ void free_all(pmmm_plan* pl) {
   v = pl->item_start; dfree(v); pl->item_start = nullptr;
   v = pl->item_chunks; dfree(v); pl->item_chunks = nullptr;
   v = pl->counter; dfree(v); pl->counter = nullptr;
+  v = pl->pair_start; dfree(v); pl->pair_start = nullptr;
   v = pl->energy; dfree(v); pl->energy = nullptr;
   v = pl->err; dfree(v); pl->err = nullptr;
   dfree(pl->hpos); dfree(pl->hq); dfree(pl->hphi); dfree(pl->hforce);
@@ -177,6 +181,7 @@ int ensure_particles(pmmm_plan* pl, int64_t n) {
   if (e == cudaSuccess) pl->item_cell = (uint32_t*)v;
   if (e == cudaSuccess) e = dalloc(pl, &v, sizeof(double) * 4 * (size_t)mi);
   if (e == cudaSuccess) pl->epart = (double*)v;
+  if (e == cudaSuccess && !pl->fp64) e = dalloc(pl, &pl->src2, 32 * (size_t)pp_pairs_max(pl->d.K, cap));
   if (e != cudaSuccess) {
     free_particles(pl);
     return map_cuda(e);
@@ -264,8 +269,9 @@ int run(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, voi
     CK(launch_radix_sort(pl->sw, n, key_bits, &pl->keys_sorted, &pl->vals_sorted, s, &nl));
     CK(launch_cell_bounds(pl->keys_sorted, n, K, pl->cs, s, &nl));
     CK(launch_gather(pl->far, fp64, pl->vals_sorted, n, pl->part, s, &nl));
-    CK(launch_pp_items(pl->cs, K, pl->item_start, pl->item_cell, pl->item_chunks, pl->counter, pl->epart,
-                       pp_items_max(K, n), s, &nl));
+    CK(launch_pp_items(pl->cs, K, pl->item_start, pl->item_cell, pl->pair_start, pl->item_chunks, pl->counter,
+                       pl->epart, pp_items_max(K, n), s, &nl));
+    if (!fp64) CK(launch_pair_pack(pl->part, pl->keys_sorted, pl->cs, pl->pair_start, n, pl->src2, s, &nl));
   }
   mark(pl, ST_P2M);
   CK(launch_p2m(pl->p, fp64, pl->part, pl->cs, K, pl->M, pl->cellsum, pl->cellsum + K, s, &nl));
@@ -310,8 +316,8 @@ int run(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, voi
     pp.ih2_32 = (float)pp.ih2f;
     pp.sign32 = (float)pp.signf;
     const int64_t mi = pp_items_max(K, n);
-    CK(launch_pp(fp64, pl->part, pl->vals_sorted, pl->cs, K, pl->item_start, pl->item_cell, pl->counter,
-                 pl->num_sms, pl->far, pp, phi, force, pl->epart, s, &nl));
+    CK(launch_pp(fp64, pl->part, pl->src2, pl->pair_start, pl->vals_sorted, pl->cs, K, pl->item_start,
+                 pl->item_cell, pl->counter, pl->num_sms, pl->far, pp, phi, force, pl->epart, s, &nl));
     mark(pl, ST_REDUCE);
     CK(launch_energy(pl->epart, mi, pl->partial + 256 * 5, pl->energy, s, &nl));
   }
@@ -441,6 +447,10 @@ int pmmm_plan_create(const pmmm_config* cfg, void* stream, pmmm_plan** out) {
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 4); pl->energy = (double*)v; }
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(int)); pl->err = (int*)v; }
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(unsigned int)); pl->counter = (unsigned int*)v; }
+  if (e == cudaSuccess && !pl->fp64) {
+    e = dalloc(pl, &v, sizeof(uint32_t) * (size_t)(d.K + 1));
+    pl->pair_start = (uint32_t*)v;
+  }
   if (e == cudaSuccess) {
     int dev = 0;
     e = cudaGetDevice(&dev);

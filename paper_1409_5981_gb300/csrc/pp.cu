@@ -19,6 +19,7 @@ namespace pmmm {
 namespace {
 
 constexpr int PP_WARPS = 4;
+constexpr int PP_BATCH = 4;  // work items taken per atomic by the FP32 near-field warps
 constexpr int PP_BLOCKS_PER_SM = 8;  // resident blocks per SM (64 registers per thread)
 constexpr int CHUNK = 32;
 
@@ -32,11 +33,41 @@ template <> __device__ __forceinline__ double rsq<double>(double x) { return rsq
 
 // item counts per cell: ceil(count / CHUNK)
 __global__ void item_count_kernel(const int* __restrict__ cs, int64_t K, uint32_t* __restrict__ item_start,
-                                  unsigned int* __restrict__ counter) {
+                                  uint32_t* __restrict__ pair_start, unsigned int* __restrict__ counter) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c == 0) *counter = 0u;
   if (c > K) return;
-  item_start[c] = (c < K) ? (uint32_t)((cs[c + 1] - cs[c] + CHUNK - 1) / CHUNK) : 0u;
+  const int cnt = (c < K) ? cs[c + 1] - cs[c] : 0;
+  item_start[c] = (uint32_t)((cnt + CHUNK - 1) / CHUNK);
+  if (pair_start) pair_start[c] = (uint32_t)((cnt + 1) / 2);
+}
+
+// Pair-interleaved source records for the FP32 near field: the particles of
+// cell c occupy pairs pair_start[c] ... (a cell with an odd count ends with a
+// dummy of zero charge far outside the box).  Pair j is two 16-byte words
+// {x_a, x_b, y_a, y_b}, {z_a, z_b, q_a, q_b}, so that one 128-bit load yields
+// the packed operands of two sources.
+__global__ void pair_pack_kernel(const float4* __restrict__ part, const uint32_t* __restrict__ keys,
+                                 const int* __restrict__ cs, const uint32_t* __restrict__ pair_start, int64_t n,
+                                 float* __restrict__ src2) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint32_t cell = keys[s];
+  const int j = (int)(s - cs[cell]);
+  const int64_t pj = (int64_t)pair_start[cell] + j / 2;
+  const int slot = j & 1;
+  const float4 r = part[s];
+  float* o = src2 + 8 * pj;
+  o[0 + slot] = r.x;
+  o[2 + slot] = r.y;
+  o[4 + slot] = r.z;
+  o[6 + slot] = r.w;
+  if (slot == 0 && s + 1 == (int64_t)cs[cell + 1]) {  // odd count: dummy partner
+    o[1] = 1.0e4f;
+    o[3] = 1.0e4f;
+    o[5] = 1.0e4f;
+    o[7] = 0.0f;
+  }
 }
 
 __global__ void item_fill_kernel(const uint32_t* __restrict__ item_start, int64_t K, uint32_t* __restrict__ item_cell,
@@ -244,36 +275,270 @@ __global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel(con
   }
 }
 
+typedef unsigned long long f2;  // two packed floats (low word = first)
+__device__ __forceinline__ f2 pk2(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void up2(f2 r, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// Two sources per step with packed FP32 arithmetic (each lane of f32x2 is an
+// IEEE fp32 operation, so results equal the scalar path's).  gx/gy/gz
+// accumulate +q r / r^3 (negated by the caller).
+template <bool SELF>
+__device__ __forceinline__ void pp_pair2(const ulonglong2& A, const ulonglong2& B, f2 tx, f2 ty, f2 tz, f2& pot,
+                                         f2& gx, f2& gy, f2& gz) {
+  const f2 dx = sub2(tx, A.x), dy = sub2(ty, A.y), dz = sub2(tz, B.x);
+  const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+  float a, b;
+  up2(r2, a, b);
+  float ra = rsqrtf(a), rb = rsqrtf(b);
+  if (SELF) {
+    ra = a > 0.f ? ra : 0.f;
+    rb = b > 0.f ? rb : 0.f;
+  }
+  const f2 ri = pk2(ra, rb);
+  const f2 qr = mul2(B.y, ri);
+  pot = add2(pot, qr);
+  const f2 qr3 = mul2(qr, mul2(ri, ri));
+  gx = fma2(qr3, dx, gx);
+  gy = fma2(qr3, dy, gy);
+  gz = fma2(qr3, dz, gz);
+}
+
+template <bool SELF>
+__device__ __forceinline__ void pp_sum2(const ulonglong2* __restrict__ src, int npair, int ph, int SP, f2 tx, f2 ty,
+                                        f2 tz, f2& pot, f2& gx, f2& gy, f2& gz) {
+  if (SP == 1) {
+    int j = 0;
+    for (; j + 2 <= npair; j += 2) {
+      const ulonglong2 A0 = src[2 * j], B0 = src[2 * j + 1], A1 = src[2 * j + 2], B1 = src[2 * j + 3];
+      pp_pair2<SELF>(A0, B0, tx, ty, tz, pot, gx, gy, gz);
+      pp_pair2<SELF>(A1, B1, tx, ty, tz, pot, gx, gy, gz);
+    }
+    if (j < npair) pp_pair2<SELF>(src[2 * j], src[2 * j + 1], tx, ty, tz, pot, gx, gy, gz);
+  } else {
+    for (int j = ph; j < npair; j += SP) pp_pair2<SELF>(src[2 * j], src[2 * j + 1], tx, ty, tz, pot, gx, gy, gz);
+  }
+}
+
+// FP32 near field (c = 1) on the pair-interleaved sources; same work items,
+// lane mapping and output as pp_kernel.  The warp walks its 27 neighbour cells
+// in pieces of up to 16 source pairs (32 words of 16 bytes): every piece is
+// fetched with one coalesced 128-bit load per lane one piece ahead of its use,
+// stored to a per-warp double buffer in shared memory and read back with
+// broadcast loads, so each warp keeps a whole cell's sources in flight.
+constexpr int PIECE = 16;  // source pairs per piece (one 16-byte word per lane)
+
+__global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel_f32x2(
+    const float* __restrict__ part, const float* __restrict__ src2f, const uint32_t* __restrict__ pair_start,
+    const uint32_t* __restrict__ vals, const int* __restrict__ cs, int64_t K, const uint32_t* __restrict__ item_start,
+    const uint32_t* __restrict__ item_cell, unsigned int* __restrict__ counter, const float* __restrict__ far,
+    PPParams pp, float* __restrict__ phi, float* __restrict__ force, double* __restrict__ epart) {
+  __shared__ ulonglong2 stage[PP_WARPS][2][2 * PIECE];
+  const float4* P = reinterpret_cast<const float4*>(part);
+  const ulonglong2* S2 = reinterpret_cast<const ulonglong2*>(src2f);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t nitems = item_start[K];
+  const int nx = pp.n[0], ny = pp.n[1], nz = pp.n[2];
+  const float csx = pp.cs32[0], csy = pp.cs32[1], csz = pp.cs32[2];
+  uint32_t item = 0, batch_end = 0;
+  for (;;) {
+    // consecutive items (neighbouring cells, mostly shared sources) stay on one
+    // warp, PP_BATCH per atomic
+    if (item >= batch_end) {
+      if (lane == 0) item = atomicAdd(counter, (unsigned)PP_BATCH);
+      item = __shfl_sync(0xffffffffu, item, 0);
+      batch_end = item + PP_BATCH;
+    }
+    if (item >= nitems) break;  // warp-uniform
+    const int cell = (int)item_cell[item];
+    const int chunk = (int)(item - item_start[cell]);
+    const int tbeg = cs[cell] + chunk * CHUNK;
+    const int R = min(CHUNK, cs[cell + 1] - tbeg);
+    int TL = 1;
+    while (TL < R) TL <<= 1;
+    const int SP = 32 / TL;
+    const int tl = lane & (TL - 1), ph = lane / TL;
+    const bool active = tl < R;
+    float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (active) xi = P[tbeg + tl];
+    const int ix = cell % nx, iy = (cell / nx) % ny, iz = cell / (nx * ny);
+    // neighbour table: lane k < 27 holds the first pair and pair count of cell
+    // (ix + k%3 - 1, iy + (k/3)%3 - 1, iz + k/9 - 1)
+    int nbb = 0, nbc = 0;
+    if (lane < 27) {
+      int jx = ix + lane % 3 - 1, jy = iy + (lane / 3) % 3 - 1, jz = iz + lane / 9 - 1;
+      bool ok = true;
+      if (jx < 0 || jx >= nx) { ok = ok && pp.periodic; jx += (jx < 0) ? nx : -nx; }
+      if (jy < 0 || jy >= ny) { ok = ok && pp.periodic; jy += (jy < 0) ? ny : -ny; }
+      if (jz < 0 || jz >= nz) { ok = ok && pp.periodic; jz += (jz < 0) ? nz : -nz; }
+      if (ok) {
+        const int cj = jx + nx * (jy + ny * jz);
+        nbb = (int)__ldg(pair_start + cj);
+        nbc = (int)__ldg(pair_start + cj + 1) - nbb;
+      }
+    }
+    // piece iterator over (neighbour k, pair offset off)
+    int k = 0, off = 0;
+    int b = __shfl_sync(0xffffffffu, nbb, 0), n = __shfl_sync(0xffffffffu, nbc, 0);
+    while (k < 27 && n == 0) {
+      ++k;
+      if (k < 27) {
+        b = __shfl_sync(0xffffffffu, nbb, k);
+        n = __shfl_sync(0xffffffffu, nbc, k);
+      }
+    }
+    ulonglong2 reg = make_ulonglong2(0ull, 0ull);
+    if (k < 27 && lane < 2 * min(PIECE, n - off)) reg = S2[2 * (b + off) + lane];
+    f2 pot = pk2(0.f, 0.f), gx = pot, gy = pot, gz = pot;
+    int cur = 0;
+    while (k < 27) {
+      const int kc = k, len = min(PIECE, n - off);
+      stage[warp][cur][lane] = reg;
+      __syncwarp();
+      // advance to the next piece and fetch it
+      off += PIECE;
+      while (k < 27 && off >= n) {
+        ++k;
+        off = 0;
+        if (k < 27) {
+          b = __shfl_sync(0xffffffffu, nbb, k);
+          n = __shfl_sync(0xffffffffu, nbc, k);
+        }
+      }
+      if (k < 27 && lane < 2 * min(PIECE, n - off)) reg = S2[2 * (b + off) + lane];
+      // target in the frame of the source cell centre (units of hs)
+      const float txs = xi.x - (float)(kc % 3 - 1) * csx;
+      const float tys = xi.y - (float)((kc / 3) % 3 - 1) * csy;
+      const float tzs = xi.z - (float)(kc / 9 - 1) * csz;
+      const f2 tx = pk2(txs, txs), ty = pk2(tys, tys), tz = pk2(tzs, tzs);
+      if (kc == 13)
+        pp_sum2<true>(stage[warp][cur], len, ph, SP, tx, ty, tz, pot, gx, gy, gz);
+      else
+        pp_sum2<false>(stage[warp][cur], len, ph, SP, tx, ty, tz, pot, gx, gy, gz);
+      cur ^= 1;
+    }
+    float pa, pb, xa, xb, ya, yb, za, zb;
+    up2(pot, pa, pb);
+    up2(gx, xa, xb);
+    up2(gy, ya, yb);
+    up2(gz, za, zb);
+    float ps = pa + pb, gxs = -(xa + xb), gys = -(ya + yb), gzs = -(za + zb);
+    for (int o = TL; o < 32; o <<= 1) {
+      ps += __shfl_xor_sync(0xffffffffu, ps, o);
+      gxs += __shfl_xor_sync(0xffffffffu, gxs, o);
+      gys += __shfl_xor_sync(0xffffffffu, gys, o);
+      gzs += __shfl_xor_sync(0xffffffffu, gzs, o);
+    }
+    float e_t = 0.f, f_t[3] = {0.f, 0.f, 0.f};
+    if (active && ph == 0) {
+      const int s = tbeg + tl;
+      const float4 fr = reinterpret_cast<const float4*>(far)[s];
+      const float ih = pp.ih32, ih2 = pp.ih2_32, sg = pp.sign32;
+      const float pt = sg * (fr.x + ps * ih);
+      const float g0 = sg * (fr.y + gxs * ih2), g1 = sg * (fr.z + gys * ih2), g2 = sg * (fr.w + gzs * ih2);
+      const uint32_t o = vals[s];
+      const float q = xi.w;
+      if (phi) phi[o] = pt;
+      if (force) {
+        force[3 * (int64_t)o + 0] = -q * g0;
+        force[3 * (int64_t)o + 1] = -q * g1;
+        force[3 * (int64_t)o + 2] = -q * g2;
+      }
+      e_t = 0.5f * q * pt;
+      f_t[0] = -q * g0;
+      f_t[1] = -q * g1;
+      f_t[2] = -q * g2;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e_t += __shfl_xor_sync(0xffffffffu, e_t, o);
+      f_t[0] += __shfl_xor_sync(0xffffffffu, f_t[0], o);
+      f_t[1] += __shfl_xor_sync(0xffffffffu, f_t[1], o);
+      f_t[2] += __shfl_xor_sync(0xffffffffu, f_t[2], o);
+    }
+    if (lane == 0) {
+      epart[(int64_t)item * 4 + 0] = (double)e_t;
+      epart[(int64_t)item * 4 + 1] = (double)f_t[0];
+      epart[(int64_t)item * 4 + 2] = (double)f_t[1];
+      epart[(int64_t)item * 4 + 3] = (double)f_t[2];
+    }
+    __syncwarp();  // the stage buffers are rewritten by the next item
+    ++item;        // next item of this warp's batch
+  }
+}
+
 }  // namespace
 
 int64_t pp_items_max(int64_t K, int64_t n) { return K + (n + CHUNK - 1) / CHUNK + 1; }
 
+int64_t pp_pairs_max(int64_t K, int64_t n) { return (n + K) / 2 + 1; }
+
 cudaError_t launch_pp_items(const int* cell_start, int64_t K, uint32_t* item_start, uint32_t* item_cell,
-                            uint32_t* chunks, unsigned int* counter, double* epart, int64_t max_items, cudaStream_t s,
-                            int* nl) {
-  item_count_kernel<<<(unsigned)((K + 1 + 255) / 256), 256, 0, s>>>(cell_start, K, item_start, counter);
+                            uint32_t* pair_start, uint32_t* chunks, unsigned int* counter, double* epart,
+                            int64_t max_items, cudaStream_t s, int* nl) {
+  item_count_kernel<<<(unsigned)((K + 1 + 255) / 256), 256, 0, s>>>(cell_start, K, item_start, pair_start, counter);
   ++*nl;
   cudaError_t e = launch_exclusive_scan(item_start, K + 1, chunks, s, nl);
+  if (e == cudaSuccess && pair_start) e = launch_exclusive_scan(pair_start, K + 1, chunks, s, nl);
   if (e != cudaSuccess) return e;
   item_fill_kernel<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(item_start, K, item_cell, epart, max_items);
   ++*nl;
   return cudaGetLastError();
 }
 
-cudaError_t launch_pp(bool fp64, const void* part, const uint32_t* vals, const int* cell_start, int64_t K,
-                      const uint32_t* item_start, const uint32_t* item_cell, unsigned int* counter, int num_sms,
-                      const void* far, PPParams pp, void* phi, void* force, double* epart, cudaStream_t s, int* nl) {
+cudaError_t launch_pair_pack(const void* part, const uint32_t* keys, const int* cell_start, const uint32_t* pair_start,
+                             int64_t n, void* src2, cudaStream_t s, int* nl) {
+  if (n <= 0) return cudaSuccess;
+  pair_pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float4*)part, keys, cell_start, pair_start, n,
+                                                               (float*)src2);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pp(bool fp64, const void* part, const void* src2, const uint32_t* pair_start, const uint32_t* vals,
+                      const int* cell_start, int64_t K, const uint32_t* item_start, const uint32_t* item_cell,
+                      unsigned int* counter, int num_sms, const void* far, PPParams pp, void* phi, void* force,
+                      double* epart, cudaStream_t s, int* nl) {
   // persistent launch: PP_BLOCKS_PER_SM resident blocks of PP_WARPS warps per SM
   const unsigned blocks = (unsigned)(PP_BLOCKS_PER_SM * (num_sms > 0 ? num_sms : 1));
+  if (!fp64 && pp.c <= 1 && src2 != nullptr) {
+    pp_kernel_f32x2<<<blocks, PP_WARPS * 32, 0, s>>>((const float*)part, (const float*)src2, pair_start, vals,
+                                                     cell_start, K, item_start, item_cell, counter, (const float*)far,
+                                                     pp, (float*)phi, (float*)force, epart);
+  } else {
 #define PP_LAUNCH(T, S)                                                                                              \
   pp_kernel<T, S><<<blocks, PP_WARPS * 32, 0, s>>>((const T*)part, vals, cell_start, K, item_start, item_cell, counter, \
                                                    (const T*)far, pp, (T*)phi, (T*)force, epart)
-  if (fp64) {
-    if (pp.c <= 1) PP_LAUNCH(double, 1); else PP_LAUNCH(double, 4);
-  } else {
-    if (pp.c <= 1) PP_LAUNCH(float, 1); else PP_LAUNCH(float, 4);
-  }
+    if (fp64) {
+      if (pp.c <= 1) PP_LAUNCH(double, 1); else PP_LAUNCH(double, 4);
+    } else {
+      if (pp.c <= 1) PP_LAUNCH(float, 1); else PP_LAUNCH(float, 4);
+    }
 #undef PP_LAUNCH
+  }
   ++*nl;
   return cudaGetLastError();
 }
