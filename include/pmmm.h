@@ -176,6 +176,30 @@ int pmmm_plan_set_timing(pmmm_plan* plan, int enable);
 int pmmm_plan_stage_times(pmmm_plan* plan, float* ms, int max_stages);
 const char* pmmm_stage_name(int i);
 
+/* Binning and stable sort by cell WITHOUT ANY DEVICE ALLOCATION.  The paper has
+ * no counterpart: this is a service for callers that cannot call cudaMalloc --
+ * code running inside a CUDA-graph capture that must not allocate, under a
+ * memory pool or framework that owns all device memory, or in a loop that must
+ * never block in the allocator.  It computes the first step of pmmm_compute
+ * (same FP64 cell-index formula, same stable order) for the geometry of cfg
+ * (box, mesh, boundary, precision; p and cutoff are ignored):
+ *   n           number of particles, 0 <= n <= PMMM_STATIC_SORT_MAX_N
+ *   pos         device, n x 3 positions (double for PMMM_FP64, float otherwise)
+ *   perm        device int32[n] output: original index of each sorted slot
+ *   cell_start  device int32[K+1] output: first sorted slot of each cell, [K] = n
+ *   cuda_stream cudaStream_t or NULL; the call synchronises it and returns the
+ *               device-side status (PMMM_ERR_OUT_OF_BOX / _NONFINITE_INPUT as in
+ *               pmmm_compute).
+ * All scratch lives in one file-scope device array of about 3 MiB that every
+ * GPU loading this library keeps until the process exits; n above
+ * PMMM_STATIC_SORT_MAX_N returns PMMM_ERR_UNSUPPORTED.  The first call on a
+ * device looks up the array's device address (with that device current): make
+ * it before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU (other streams or host threads) race and must not be made. */
+#define PMMM_STATIC_SORT_MAX_N 65536
+int pmmm_bin_sort_static(const pmmm_config* cfg, int64_t n, const void* pos, int32_t* perm, int32_t* cell_start,
+                         void* cuda_stream);
+
 /* Human-readable name of a status code (static string). */
 const char* pmmm_strerror(int status);
 

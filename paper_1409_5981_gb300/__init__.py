@@ -69,6 +69,8 @@ _SIGS = {
     "pmmm_plan_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "pmmm_plan_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
     "pmmm_stage_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "pmmm_bin_sort_static": (ctypes.c_int, [ctypes.POINTER(_Config), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p]),
     "pmmm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -97,6 +99,23 @@ def build(force: bool = False) -> str:
     """Compiles libpmmm.so in-tree (see buildlib.py)."""
     from . import buildlib
     return buildlib.build(force=force)
+
+
+STATIC_SORT_MAX_N = 65536
+
+
+def bin_sort_static(cfg: Config, pos, perm, cell_start, stream=None) -> int:
+    """Binning and stable cell sort with no device allocation (pmmm_bin_sort_static):
+    pos (n, 3) CUDA tensor in the precision's dtype; perm int32 (n,) and cell_start
+    int32 (K+1,) CUDA tensors receive the results.  Returns the status code."""
+    import torch
+    c = cfg.to_c()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    n = int(pos.shape[0])
+    return int(_lib().pmmm_bin_sort_static(ctypes.byref(c), n, ctypes.c_void_p(pos.data_ptr()),
+                                           ctypes.c_void_p(perm.data_ptr()), ctypes.c_void_p(cell_start.data_ptr()),
+                                           ctypes.c_void_p(stream.cuda_stream)))
 
 
 def stage_names():
