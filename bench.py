@@ -43,7 +43,13 @@ WORKLOADS = {
                                                   "uniform_pm1", 1.0),
     "open_plummer_n1048576_mesh64_p5_fp32": (1 << 20, "open", 64, 5, "fp32", (-1, -1, -1), (2, 2, 2), "plummer",
                                              -1.0),
+    "periodic_uniform_n16777216_mesh64_p5_fp32": (1 << 24, "periodic", 64, 5, "fp32", (0, 0, 0), (1, 1, 1),
+                                                   "uniform_pm1", 1.0),
     "periodic_uniform_n16777216_mesh64_p7_fp32": (1 << 24, "periodic", 64, 7, "fp32", (0, 0, 0), (1, 1, 1),
+                                                   "uniform_pm1", 1.0),
+    "periodic_uniform_n16777216_mesh64_p11_fp32": (1 << 24, "periodic", 64, 11, "fp32", (0, 0, 0), (1, 1, 1),
+                                                    "uniform_pm1", 1.0),
+    "periodic_uniform_n16777216_mesh64_p7_fp64": (1 << 24, "periodic", 64, 7, "fp64", (0, 0, 0), (1, 1, 1),
                                                    "uniform_pm1", 1.0),
     "open_uniform_n4096_mesh8_p4_fp64": (4096, "open", 8, 4, "fp64", (0, 0, 0), (1, 1, 1), "uniform_pm1", 1.0),
     # same particle density as the default (32 per cell), 8x smaller: the ncu profiling case

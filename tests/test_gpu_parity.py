@@ -271,3 +271,47 @@ def test_config2b_plummer_open_sampled(pk):
     print(f"plummer sampled {sel.sum()} particles: force {e_f:.2e} phi {e_p:.2e}")
     assert e_f < FP32_TOL[5] and e_p < FP32_TOL[5]
     plan.close()
+
+
+# ----------------------------------------------------------------------------- precision sweep (2^24, 64^3)
+def test_fp64_gpu_path_high_order_vs_oracle(pk):
+    """The FP64 GPU path at p = 11 (orders up to 22 in the kernel) against the oracle on a
+    16^3 periodic mesh: the reference used for the 64^3 precision sweep below."""
+    pos, q = synth.uniform_pm1(20000, synth.seed(3, 1))
+    cfg = pk.Config(mesh=(16, 16, 16), p=11, boundary=pk.PERIODIC, precision=pk.FP64, ewald_nmax=4)
+    plan, phi, force, _ = _run(pk, cfg, pos, q)
+    cells = synth.rng(207).choice(16 ** 3, size=6, replace=False)
+    ref = _oracle(cfg, pk, pos, q, target_cells=cells)
+    sel = ~np.isnan(ref["phi"])
+    e_f = _rel(force[sel], -(q[sel, None] * ref["grad"][sel]))
+    e_p = _rel(phi[sel], ref["phi"][sel])
+    print(f"fp64 p=11 16^3 vs oracle: force {e_f:.2e} phi {e_p:.2e}")
+    assert e_f < FP64_TOL and e_p < FP64_TOL
+    plan.close()
+
+
+@pytest.mark.parametrize("p", [5, 7, 11])
+def test_config3_precision_sweep(pk, p):
+    """N = 2^24 uniform +-1, periodic, mesh 64^3: the FP32 path against the FP64 GPU path
+    on every particle (relative RMS force and potential error, reported per p)."""
+    import torch
+    n = 1 << 24
+    pos, q = synth.uniform_pm1(n, synth.seed(3, 0))
+    pos32 = pos.astype(np.float32)
+    res = {}
+    for prec in (pk.FP64, pk.FP32):
+        cfg = pk.Config(mesh=(64, 64, 64), p=p, boundary=pk.PERIODIC, precision=prec)
+        dt = torch.float64 if prec == pk.FP64 else torch.float32
+        src = pos32.astype(np.float64) if prec == pk.FP64 else pos32
+        plan = pk.Plan(cfg)
+        phi, force, e = plan.compute(torch.tensor(src, dtype=dt, device="cuda"),
+                                     torch.tensor(q, dtype=dt, device="cuda"), energy=True)
+        res[prec] = (phi.double().cpu().numpy(), force.double().cpu().numpy(), e)
+        plan.close()
+        del phi, force
+        torch.cuda.empty_cache()
+    e_f = _rel(res[pk.FP32][1], res[pk.FP64][1])
+    e_p = _rel(res[pk.FP32][0], res[pk.FP64][0])
+    e_u = abs(res[pk.FP32][2] - res[pk.FP64][2]) / abs(res[pk.FP64][2])
+    print(f"config3 p={p}: FP32 vs FP64 GPU: force {e_f:.2e} phi {e_p:.2e} energy {e_u:.2e}")
+    assert e_f < FP32_TOL[p] and e_p < FP32_TOL[p] and e_u < 1e-6
