@@ -56,6 +56,11 @@ WORKLOADS = {
     "periodic_uniform_n131072_mesh16_p7_fp32": (1 << 17, "periodic", 16, 7, "fp32", (0, 0, 0), (1, 1, 1),
                                                  "uniform_pm1", 1.0),
 }
+# Batched form: name -> (systems, log2 N range, mesh, p, precision); systems are
+# independent periodic unit boxes of neutral uniform +-1 charges, N log-uniform.
+BATCHED = {
+    "periodic_batched64_logN14to18_mesh32_p7_fp32": (64, 14.0, 18.0, 32, 7, "fp32"),
+}
 DEFAULT_WORKLOAD = "periodic_uniform_n1048576_mesh32_p7_fp32"
 METRIC = "particles/s per full force eval at fixed RMS force error; mesh-stage HBM % peak"
 UNIT = "particles/s"
@@ -222,15 +227,32 @@ def _cpu_baseline(name: str, pos, q, g, budget_s: float = 20.0):
                       f"table; {dt:.1f} s"}
 
 
+def _batched_inputs(name: str, rank: int):
+    nsys, lo_e, hi_e, mesh, p, prec = BATCHED[name]
+    sizes = synth.batched_sizes(nsys, synth.seed(4, 100 * rank), lo_e, hi_e)
+    pos, q, off = synth.batched_uniform_pm1(sizes, 4, rep=rank)
+    return pos, q, off
+
+
 def run_reference(args, rank, world):
     """Reference arm: the oracle on the host cores, same config and metric."""
     if rank != 0:
         return 0
     import oracle
     name = args.workload
-    n, boundary, mesh, p, prec, lo, ln, gen, sign = WORKLOADS[name]
-    per = boundary == "periodic"
-    pos, q = _inputs(name, 0)
+    if name in BATCHED:
+        # the oracle on the batch: each step is one oracle evaluation of a bounded set
+        # of target cells of one system (systems taken in turn)
+        nsys, lo_e, hi_e, mesh, p, prec = BATCHED[name]
+        posb, qb, off = _batched_inputs(name, 0)
+        n, boundary, lo, ln = int(off[-1]), "periodic", (0, 0, 0), (1, 1, 1)
+        per = True
+        systems = [(posb[off[s]:off[s + 1]], qb[off[s]:off[s + 1]]) for s in range(nsys)]
+    else:
+        n, boundary, mesh, p, prec, lo, ln, gen, sign = WORKLOADS[name]
+        per = boundary == "periodic"
+        systems = [_inputs(name, 0)]
+    pos, q = systems[0]
     g = oracle.green_table(lo, ln, (mesh,) * 3, p, 1, per)
     rng = synth.rng(777)
     # size one step to ~3 s so that warmup + steps end within a few minutes
@@ -246,6 +268,7 @@ def run_reference(args, rank, world):
     times, done = [], []
     for it in range(args.warmup + args.steps):
         cells = rng.choice(mesh ** 3, size=ncell, replace=False)
+        pos, q = systems[it % len(systems)]
         t0 = time.perf_counter()
         r = oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, 1, per, target_cells=cells, green=g)
         dt = time.perf_counter() - t0
@@ -259,13 +282,24 @@ def run_reference(args, rank, world):
             "config": _config(name, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                              "sample": f"each step: one oracle evaluation restricted to {ncell} random target cells "
-                                       f"of the {n}-particle workload (Green table precomputed once)"},
+                                       f"of the {n}-particle workload"
+                                       + (f" (one of its {len(systems)} systems per step, in turn)"
+                                          if len(systems) > 1 else "")
+                                       + " (Green table precomputed once)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def _config(name, world):
+    if name in BATCHED:
+        nsys, lo_e, hi_e, mesh, p, prec = BATCHED[name]
+        _, _, off = _batched_inputs(name, 0)
+        return {"workload": name, "systems": nsys, "n_particles": int(off[-1]),
+                "n_per_system": f"log-uniform 2^{lo_e:g}..2^{hi_e:g}, even", "boundary": "periodic",
+                "mesh": [mesh] * 3, "fft_grid": [mesh] * 3, "p": p, "cutoff_cells": 27, "distribution": "uniform_pm1",
+                "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
+                "launch": "CUDA graph of the whole batched evaluation"}
     n, boundary, mesh, p, prec, lo, ln, gen, sign = WORKLOADS[name]
     return {"workload": name, "n_particles": n, "boundary": boundary, "mesh": [mesh] * 3,
             "fft_grid": [mesh if boundary == "periodic" else 2 * mesh] * 3, "p": p, "cutoff_cells": 27,
@@ -431,13 +465,202 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def run_ours_batched(args, rank, world, local_rank):
+    """The batched form: all systems in one evaluation replayed from a CUDA graph,
+    against the plain method (one pmmm_compute per system) on the same GPU."""
+    import torch
+    import paper_1409_5981_gb300 as pk
+
+    name = args.workload
+    nsys, lo_e, hi_e, mesh, p, prec = BATCHED[name]
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    pk._lib()
+    fp64 = prec == "fp64"
+    dt = torch.float64 if fp64 else torch.float32
+    npdt = np.float64 if fp64 else np.float32
+    cfg = pk.Config(mesh=(mesh,) * 3, p=p, cutoff=1, boundary=pk.PERIODIC, precision=pk.FP64 if fp64 else pk.FP32)
+    stream = torch.cuda.Stream(dev)
+    plan = pk.Plan(cfg, stream)
+    pos_np, q_np, off = _batched_inputs(name, rank)
+    counts = np.diff(off)
+    n = int(off[-1])
+    with torch.cuda.stream(stream):
+        pos = torch.tensor(pos_np.astype(npdt), device=dev)
+        q = torch.tensor(q_np.astype(npdt), device=dev)
+        phi = torch.empty(n, dtype=dt, device=dev)
+        force = torch.empty((n, 3), dtype=dt, device=dev)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream.synchronize()
+    plan.reserve_batched(nsys, n)
+
+    def step(graph=True):
+        st = plan.compute_batched_raw(off, pos.data_ptr(), q.data_ptr(), phi.data_ptr(), force.data_ptr(), graph)
+        if st != 0:
+            raise pk.PmmmError(st, "pmmm_compute_batched")
+
+    def timed(fn, steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            evs[k][0].record(stream)
+            fn()
+            evs[k][1].record(stream)
+        stream.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    # stage times of one plain (uncaptured) batched evaluation
+    plan.set_timing(True)
+    for _ in range(3):
+        step(graph=False)
+    stage = plan.stage_times()
+    plan.set_timing(False)
+    launches = plan.info(pk.INFO_LAUNCHES)
+    plain_ms = statistics.median(timed(lambda: step(graph=False), max(3, min(args.steps, 20))))
+
+    sampler = ClockSampler(_gpu_id(torch, local_rank))
+    sampler.start()
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    st = plan.status()
+    if st != 0:
+        raise pk.PmmmError(st, "warm-up")
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0w = time.time()
+    step_ms = timed(step, args.steps)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t1w = time.time()
+    sampler.stop()
+    clocks = sampler.summary(t0w, t1w)
+    st = plan.status()
+    if st != 0:
+        raise pk.PmmmError(st, "timed region")
+    total_ms = sum(step_ms)
+
+    # the plain method on the same GPU: one single-system plan evaluation per system
+    single = pk.Plan(cfg, stream)
+    single.reserve(int(counts.max()))
+
+    def seq():
+        for s_ in range(nsys):
+            a = int(off[s_])
+            m = int(counts[s_])
+            stq = single.compute_raw(m, pos.data_ptr() + 3 * a * pos.element_size(),
+                                     q.data_ptr() + a * q.element_size(), phi.data_ptr() + a * phi.element_size(),
+                                     force.data_ptr() + 3 * a * force.element_size())
+            if stq != 0:
+                raise pk.PmmmError(stq, "pmmm_compute")
+    for _ in range(2):
+        seq()
+    seq_ms = statistics.median(timed(seq, max(3, min(args.steps, 10))))
+    single.close()
+
+    # end to end through the host-buffer batched call (pinned memory)
+    pos_h = torch.tensor(pos_np.astype(npdt)).pin_memory()
+    q_h = torch.tensor(q_np.astype(npdt)).pin_memory()
+    phi_h = torch.empty(n, dtype=dt).pin_memory()
+    force_h = torch.empty((n, 3), dtype=dt).pin_memory()
+    plan.compute_batched_host(counts, pos_h, q_h, phi_h, force_h)
+    e2e_ms = []
+    for k in range(max(3, min(args.steps, 20))):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        t = time.perf_counter()
+        plan.compute_batched_host(counts, pos_h, q_h, phi_h, force_h)
+        e2e_ms.append(1e3 * (time.perf_counter() - t))
+    esz = 8 if fp64 else 4
+
+    # near-field pairs over all systems (dominant kernel) and the mesh byte model
+    step()
+    stream.synchronize()
+    cs = plan.export(pk.EXPORT_CELL_START)
+    K = mesh ** 3
+    pairs = sum(_pairs(cs[s_ * K:(s_ + 1) * K + 1] - cs[s_ * K], mesh, True) for s_ in range(nsys))
+    C, CG, Kh = plan.info(pk.INFO_C), plan.info(pk.INFO_CG), plan.info(pk.INFO_KH)
+    hbm, sm_max, peak_kind = _peaks()
+    alu_peak = 2.0 * FP32_LANES_PER_SM * NUM_SMS * sm_max * 1e6 / 1e12
+    pp_ms = stage.get("near_field", float("nan"))
+    pp_tf = PP_FLOPS_PER_PAIR * pairs / (pp_ms * 1e-3) / 1e12
+    mesh_ms = sum(stage.get(k, 0.0) for k in ("fft_forward", "m2l", "fft_inverse"))
+    mesh_bytes = esz * nsys * (2 * C * K + 4 * 2 * C * Kh) + esz * 2 * CG * Kh
+    m2l_bytes = esz * 2 * (2 * C * Kh * nsys + CG * Kh)
+
+    tmax, e2e_tot = total_ms, sum(e2e_ms) / len(e2e_ms) * args.steps
+    if world > 1:
+        tt = torch.tensor([total_ms, e2e_tot], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        tmax, e2e_tot = float(tt[0]), float(tt[1])
+    value = world * n * args.steps / (tmax * 1e-3)
+    if rank != 0:
+        plan.close()
+        return 0
+
+    err, green = None, None
+    if not (args.no_accuracy and args.no_cpu_baseline):
+        import oracle
+        green = oracle.green_table((0, 0, 0), (1, 1, 1), (mesh,) * 3, p, 1, True)
+    f_all = force.double().cpu().numpy()
+    pos64 = pos_np.astype(npdt).astype(np.float64)
+    q64 = q_np.astype(npdt).astype(np.float64)
+    if not args.no_accuracy:
+        import oracle
+        s0 = int(np.argmin(counts))
+        a, b = int(off[s0]), int(off[s0 + 1])
+        cells = synth.rng(98).choice(K, size=4, replace=False)
+        r = oracle.pmmm(pos64[a:b], q64[a:b], (0, 0, 0), (1, 1, 1), (mesh,) * 3, p, 1, True, target_cells=cells,
+                        green=green)
+        sel = ~np.isnan(r["phi"])
+        f = f_all[a:b][sel]
+        rf = -q64[a:b][sel, None] * r["grad"][sel]
+        err = float(np.sqrt(((f - rf) ** 2).sum() / (rf ** 2).sum()))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
+        "config": _config(name, world),
+        "rel_rms_force_err_vs_fp64_oracle_pmmm": err,
+        "stage_ms": stage,
+        "plain_batched_ms": plain_ms,
+        "plain_method_sequential_ms": seq_ms,
+        "speedup_vs_plain_method": seq_ms / (tmax / args.steps),
+        "roofline": {"bound": "alu", "kernel": "near field (pp_kernel)", "achieved": pp_tf,
+                     "peak": alu_peak, "unit": "TFLOP/s", "frac": pp_tf / alu_peak, "traffic": None,
+                     "per_launch": f"{pairs} pair interactions x {PP_FLOPS_PER_PAIR} flop",
+                     "peak_basis": f"{NUM_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"},
+        "mesh_roofline": {"bound": "hbm", "achieved": mesh_bytes / (mesh_ms * 1e-3) / 1e9, "peak": hbm,
+                          "unit": "GB/s", "frac": mesh_bytes / (mesh_ms * 1e-3) / 1e9 / hbm,
+                          "stages": "fft_forward + m2l + fft_inverse", "peak_kind": peak_kind,
+                          "m2l_ms": stage.get("m2l"), "m2l_GBps": m2l_bytes / (stage.get("m2l", 1.0) * 1e-3) / 1e9},
+        "e2e": {"value": world * n / (statistics.median(e2e_ms) * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 4 * esz * n, "d2h_bytes_per_step": 4 * esz * n + 8 * nsys},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        a, b = int(off[int(np.argmax(counts))]), int(off[int(np.argmax(counts)) + 1])
+        WORKLOADS["_batched_sample"] = (b - a, "periodic", mesh, p, prec, (0, 0, 0), (1, 1, 1), "uniform_pm1", 1.0)
+        cb = _cpu_baseline("_batched_sample", pos64[a:b], q64[a:b], green)
+        cb["sample"] = f"largest system of the batch: " + cb["sample"]
+        line["cpu_baseline"] = cb
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCHED), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     args = ap.parse_args()
@@ -451,6 +674,8 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     try:
+        if args.workload in BATCHED:
+            return run_ours_batched(args, rank, world, local_rank)
         return run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:

@@ -124,12 +124,58 @@ int pmmm_compute(pmmm_plan* plan, int64_t n, const void* pos, const void* q, voi
 int pmmm_compute_host(pmmm_plan* plan, int64_t n, const void* pos, const void* q, void* phi, void* force,
                       double* energy);
 
+/* The batched form: nsys independent systems in one evaluation.  They share the
+ * plan's box, mesh, p, cutoff, boundary and precision; system s holds the
+ * particles offsets[s] ... offsets[s+1]-1 of the concatenated arrays, and its
+ * results are those of pmmm_compute on its particles alone (up to rounding).
+ * Every step runs once over all systems, laid side by side as nsys meshes of K
+ * cells (system s owns cells s*K ... s*K + K-1 in the exports below).  The M2L
+ * of Sec. 2.1 becomes, per wavevector k, one complex matrix product
+ * L~(k) = A~(k) M~(k) with M~(k) a (p+1)^2 x nsys matrix and A~(k) the
+ * real-matrix M2L of App. A.8 on the shared Green spectra.
+ *   nsys      1 <= nsys <= PMMM_MAX_SYSTEMS, nsys * K <= 2^30 (else PMMM_ERR_UNSUPPORTED)
+ *   offsets   HOST int64[nsys+1]: offsets[0] = 0, non-decreasing,
+ *             n = offsets[nsys] <= 2^31 - 1; systems may be empty
+ *   pos, q, phi, force  device arrays of the n particles, as in pmmm_compute
+ *   energies  HOST double[nsys] or NULL: U of each system; if given, the call
+ *             synchronises and returns the device-side status.
+ * The plan grows its mesh workspace to nsys systems on first use (allocation,
+ * stream synchronised).  New offsets are uploaded through a plan-owned staging
+ * buffer after a stream synchronisation; offsets equal to the previous call's
+ * are not uploaded again, so a call with unchanged offsets queues only kernels
+ * (it can be captured into a CUDA graph once pmmm_plan_reserve_batched and one
+ * uncaptured call with the same offsets and no larger n have been made). */
+#define PMMM_MAX_SYSTEMS 65535
+int pmmm_compute_batched(pmmm_plan* plan, int32_t nsys, const int64_t* offsets, const void* pos, const void* q,
+                         void* phi, void* force, double* energies);
+
+/* pmmm_compute_batched with HOST pos, q, phi, force (see pmmm_compute_host);
+ * synchronises and returns the device-side status. */
+int pmmm_compute_batched_host(pmmm_plan* plan, int32_t nsys, const int64_t* offsets, const void* pos, const void* q,
+                              void* phi, void* force, double* energies);
+
+/* pmmm_compute_batched replayed from a CUDA graph: the first call (and any call
+ * whose offsets or array pointers differ from the previous graph call's) uploads
+ * the offsets, reserves the workspace, captures the whole evaluation on the
+ * plan's stream into a graph and instantiates it; every call then launches the
+ * graph, so one host call queues every kernel of the evaluation.  The plan's
+ * stream must not be the legacy default stream (PMMM_ERR_UNSUPPORTED).  The
+ * graph reads the arrays at the pointers it was captured with: reuse the same
+ * buffers to avoid a new capture.  Per-stage timing is not recorded. */
+int pmmm_compute_batched_graph(pmmm_plan* plan, int32_t nsys, const int64_t* offsets, const void* pos,
+                               const void* q, void* phi, void* force, double* energies);
+
+/* Pre-allocates the workspace for nsys systems and n_max particles in total. */
+int pmmm_plan_reserve_batched(pmmm_plan* plan, int32_t nsys, int64_t n_max);
+
 /* Synchronises the plan's stream and returns (and clears) the first error
  * recorded on the device by earlier pmmm_compute calls. */
 int pmmm_plan_status(pmmm_plan* plan);
 
-/* Copies an internal result of the last pmmm_compute to host memory, for
- * tests and diagnostics (synchronises).  bytes must equal the size stated:
+/* Copies an internal result of the last evaluation to host memory, for tests
+ * and diagnostics (synchronises).  bytes must equal the size stated; K below is
+ * the cell count of all systems of that evaluation (nsys * cells per system),
+ * and a cell id of system s is s * (cells per system) + its own id:
  *   PMMM_EXPORT_PERM        int32[n]     original index of each sorted slot
  *   PMMM_EXPORT_SORTED_CELL int32[n]     cell id (ix + nx (iy + ny iz)) of each sorted slot
  *   PMMM_EXPORT_CELL_START  int32[K+1]   first sorted slot of each cell; [K] = n
@@ -137,8 +183,8 @@ int pmmm_plan_status(pmmm_plan* plan);
  *                                        ([c][cell]), physical units (C = (p+1)^2)
  *   PMMM_EXPORT_LOCAL       double[C*K]  L after the cell convolution, before the
  *                                        periodic corrections, same layout and units
- *   PMMM_EXPORT_CORR        double[8]    total charge Q, sum_cells M_1^0, Re and Im of
- *                                        sum_cells M_1^1, sum q |r_rel|^2, alpha, V, unused
+ *   PMMM_EXPORT_CORR        double[8*nsys] per system: total charge Q, sum_cells M_1^0, Re
+ *                                        and Im of sum_cells M_1^1, sum q |r_rel|^2, alpha, V, unused
  *   PMMM_EXPORT_FAR         double[4*n]  per sorted slot: far-field phi and grad phi
  *                                        (Coulomb sign, corrections included)
  */
@@ -156,7 +202,8 @@ int pmmm_plan_export(pmmm_plan* plan, int what, void* host_dst, size_t bytes);
 /* Integer facts about a plan: PMMM_INFO_K (cells), PMMM_INFO_C ((p+1)^2),
  * PMMM_INFO_CG ((2p+1)^2), PMMM_INFO_KH (stored wavevectors per channel),
  * PMMM_INFO_N (particles of the last compute), PMMM_INFO_WORKSPACE_BYTES,
- * PMMM_INFO_LAUNCHES (kernels launched by the last compute). */
+ * PMMM_INFO_LAUNCHES (kernels launched by the last compute), PMMM_INFO_SYSTEMS
+ * (systems of the last compute). */
 enum {
   PMMM_INFO_K = 1,
   PMMM_INFO_C = 2,
@@ -164,7 +211,8 @@ enum {
   PMMM_INFO_KH = 4,
   PMMM_INFO_N = 5,
   PMMM_INFO_WORKSPACE_BYTES = 6,
-  PMMM_INFO_LAUNCHES = 7
+  PMMM_INFO_LAUNCHES = 7,
+  PMMM_INFO_SYSTEMS = 8
 };
 int pmmm_plan_info(pmmm_plan* plan, int what, int64_t* value);
 

@@ -24,6 +24,8 @@ FP64, FP32, FP32_SPLITBF16_M2L = 0, 1, 2
 EXPORT_PERM, EXPORT_SORTED_CELL, EXPORT_CELL_START = 1, 2, 3
 EXPORT_MULTIPOLE, EXPORT_LOCAL, EXPORT_CORR, EXPORT_FAR = 4, 5, 6, 7
 INFO_K, INFO_C, INFO_CG, INFO_KH, INFO_N, INFO_WORKSPACE_BYTES, INFO_LAUNCHES = 1, 2, 3, 4, 5, 6, 7
+INFO_SYSTEMS = 8
+MAX_SYSTEMS = 65535
 
 
 class PmmmError(RuntimeError):
@@ -63,6 +65,15 @@ _SIGS = {
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "pmmm_compute_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "pmmm_compute_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pmmm_compute_batched_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p]),
+    "pmmm_compute_batched_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_void_p]),
+    "pmmm_plan_reserve_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     "pmmm_plan_status": (ctypes.c_int, [ctypes.c_void_p]),
     "pmmm_plan_export": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
     "pmmm_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
@@ -247,6 +258,78 @@ class Plan:
         _check(st, "pmmm_compute_host")
         return phi, force, (e.value if energy else None)
 
+    # ------------------------------------------------------------------ batched form
+    @staticmethod
+    def _offsets(counts):
+        off = np.zeros(len(counts) + 1, dtype=np.int64)
+        off[1:] = np.cumsum(np.asarray(counts, dtype=np.int64))
+        return off
+
+    def reserve_batched(self, nsys: int, n: int):
+        _check(_lib().pmmm_plan_reserve_batched(self._h, int(nsys), int(n)), "pmmm_plan_reserve_batched")
+
+    def compute_batched(self, counts, pos, q, phi=None, force=None, energies: bool = False):
+        """Systems of counts[s] particles, concatenated in pos (n, 3) and q (n,) CUDA
+        tensors; returns (phi, force, per-system energies as numpy or None)."""
+        import torch
+        off = self._offsets(counts)
+        n = int(off[-1])
+        for t, nm in ((pos, "pos"), (q, "q")):
+            if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous()):
+                raise ValueError(f"{nm} must be a contiguous CUDA {self.dtype} tensor")
+        if pos.shape != (n, 3) or q.shape != (n,):
+            raise ValueError("pos must be (n, 3) and q (n,) with n = sum(counts)")
+        if phi is None:
+            phi = torch.empty(n, dtype=self.dtype, device=q.device)
+        if force is None:
+            force = torch.empty((n, 3), dtype=self.dtype, device=q.device)
+        e = np.zeros(len(counts), dtype=np.float64)
+        st = _lib().pmmm_compute_batched(self._h, len(counts), ctypes.c_void_p(off.ctypes.data),
+                                         ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(q.data_ptr()),
+                                         ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(force.data_ptr()),
+                                         ctypes.c_void_p(e.ctypes.data) if energies else None)
+        _check(st, "pmmm_compute_batched")
+        return phi, force, (e if energies else None)
+
+    def compute_batched_raw(self, offsets: np.ndarray, pos_ptr: int, q_ptr: int, phi_ptr: int, force_ptr: int,
+                            graph: bool = False) -> int:
+        """Queue one batched evaluation on raw device pointers (offsets: int64 numpy, nsys+1);
+        graph=True replays a CUDA graph of the evaluation (pmmm_compute_batched_graph)."""
+        f = _lib().pmmm_compute_batched_graph if graph else _lib().pmmm_compute_batched
+        return f(self._h, len(offsets) - 1, ctypes.c_void_p(offsets.ctypes.data), ctypes.c_void_p(pos_ptr),
+                 ctypes.c_void_p(q_ptr), ctypes.c_void_p(phi_ptr), ctypes.c_void_p(force_ptr), None)
+
+    def compute_batched_graph(self, counts, pos, q, phi, force, energies: bool = False):
+        """compute_batched through a CUDA graph (pmmm_compute_batched_graph); phi and
+        force must be given, and the same tensors reused to replay without a new capture."""
+        off = self._offsets(counts)
+        e = np.zeros(len(counts), dtype=np.float64)
+        st = _lib().pmmm_compute_batched_graph(self._h, len(counts), ctypes.c_void_p(off.ctypes.data),
+                                               ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(q.data_ptr()),
+                                               ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(force.data_ptr()),
+                                               ctypes.c_void_p(e.ctypes.data) if energies else None)
+        _check(st, "pmmm_compute_batched_graph")
+        return phi, force, (e if energies else None)
+
+    def compute_batched_host(self, counts, pos, q, phi=None, force=None):
+        """Host arrays in and out (numpy or pinned CPU tensors); synchronous; returns
+        (phi, force, per-system energies)."""
+        def ptr(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        off = self._offsets(counts)
+        n = int(off[-1])
+        if phi is None:
+            phi = np.empty(n, dtype=self.np_dtype)
+        if force is None:
+            force = np.empty((n, 3), dtype=self.np_dtype)
+        e = np.zeros(len(counts), dtype=np.float64)
+        st = _lib().pmmm_compute_batched_host(self._h, len(counts), ctypes.c_void_p(off.ctypes.data),
+                                              ctypes.c_void_p(ptr(pos)), ctypes.c_void_p(ptr(q)),
+                                              ctypes.c_void_p(ptr(phi)), ctypes.c_void_p(ptr(force)),
+                                              ctypes.c_void_p(e.ctypes.data))
+        _check(st, "pmmm_compute_batched_host")
+        return phi, force, e
+
     def status(self) -> int:
         return int(_lib().pmmm_plan_status(self._h))
 
@@ -257,14 +340,15 @@ class Plan:
         return int(v.value)
 
     def export(self, what: int) -> np.ndarray:
-        n, K, C = self.info(INFO_N), self.info(INFO_K), self.info(INFO_C)
+        n, C, B = self.info(INFO_N), self.info(INFO_C), self.info(INFO_SYSTEMS)
+        K = self.info(INFO_K) * B
         shapes = {
             EXPORT_PERM: ((n,), np.int32),
             EXPORT_SORTED_CELL: ((n,), np.int32),
             EXPORT_CELL_START: ((K + 1,), np.int32),
             EXPORT_MULTIPOLE: ((C, K), np.float64),
             EXPORT_LOCAL: ((C, K), np.float64),
-            EXPORT_CORR: ((8,), np.float64),
+            EXPORT_CORR: ((8,) if B == 1 else (B, 8), np.float64),
             EXPORT_FAR: ((n, 4), np.float64),
         }
         shape, dt = shapes[what]

@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "common.cuh"
 #include "fft.cuh"
 #include "pmmm.h"
@@ -80,6 +82,7 @@ struct CorrParams {
   double c_charged;    // 3 / (2 alpha^2)
   double c_self;       // 2 alpha / sqrt(pi)
   int periodic;
+  int64_t ksys;        // cells per system (corrections corr[16 s ...] of system s = cell / ksys)
 };
 cudaError_t launch_l2p(int p, bool fp64, const void* part, const uint32_t* keys, int64_t n, const void* L,
                        int64_t K, const double* corr, const double* cellq, CorrParams cp, void* far,
@@ -102,6 +105,28 @@ cudaError_t launch_twiddles(bool fp64, int L, void* tw, cudaStream_t s);
 // ---------------------------------------------------------------- m2l.cu
 cudaError_t launch_m2l(int p, bool fp64, const void* Mt, const void* Gt, void* Lt, int64_t Kh, cudaStream_t s,
                        int* nlaunch);
+// nsys systems sharing Gt, spectra laid out [c][system][k] (thread per (k, l, system))
+cudaError_t launch_m2l_systems(int p, bool fp64, const void* Mt, const void* Gt, void* Lt, int64_t Kh, int nsys,
+                               cudaStream_t s, int* nlaunch);
+
+// ---------------------------------------------------------------- batch.cu
+// Many systems on one plan: system s owns cells s*Ksys ... s*Ksys + Ksys - 1 of
+// a mesh of nsys*Ksys cells; the particles of system s are offsets[s] ...
+// offsets[s+1]-1 (device array of nsys+1 entries).
+cudaError_t launch_bin_batched(const void* pos, const void* q, bool fp64, int64_t n, const int64_t* offsets, int nsys,
+                               const Geo& g, int64_t Ksys, uint32_t* keys, void* rec, int* err, cudaStream_t s,
+                               int* nlaunch);
+// Entry table of the real-matrix M2L as 4 ints per entry (i1, s1, i2, s2), C*C entries.
+std::vector<int> build_m2l_table_int4(int p);
+// L~(k) = A~(k) M~(k) for all systems at once (spectra [c][system][k]); tab on the device.
+cudaError_t launch_m2l_batched(bool fp64, const void* Mt, const void* Gt, void* Lt, const int* tab, int p, int nsys,
+                               int64_t Kh, cudaStream_t s, int* nlaunch);
+// corr[16 s + ...] of every system (the single-system layout of launch_corrections)
+cudaError_t launch_corrections_batched(const double* cellsum, int64_t Ktot, int64_t Ksys, int nsys, double hs,
+                                       double V, double* corr, cudaStream_t s, int* nlaunch);
+// energies[4 s + ...] = energy and net force of system s from the near-field partials
+cudaError_t launch_energy_batched(const double* epart, const uint32_t* item_start, int64_t Ksys, int nsys,
+                                  double* energies, cudaStream_t s, int* nlaunch);
 
 // ---------------------------------------------------------------- green.cu
 // Builds the real-space Green components G[s][Kt] (FP64, units of hs), s < (2p+1)^2.
@@ -117,6 +142,7 @@ struct PPParams {
   int n[3];
   int c;
   int periodic;
+  int ksys;  // cells per system: neighbours are taken within the target's own system
   // constants, rounded once on the host: cell size / hs per axis, 1 / hs,
   // 1 / hs^2, sign (+1 Coulomb, -1 gravity); FP64 and FP32 copies
   double csf[3], ihf, ih2f, signf;

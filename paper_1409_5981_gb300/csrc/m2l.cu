@@ -1,7 +1,8 @@
 // Per-wavevector M2L (Sec. 2.1: L~_k = G~_k M~_k) in the real-matrix form of
 // App. A.8, one thread per (wavevector, output order l).  Spectra are stored
 // channel-major ([c][k]), so the threads of a warp read consecutive k of a
-// channel: every load and store is coalesced.
+// channel: every load and store is coalesced.  Several systems that share the
+// kernel spectra are laid out [c][system][k] and taken by blockIdx.z.
 #include "internal.cuh"
 #include "translations.cuh"
 
@@ -11,26 +12,28 @@ namespace {
 
 template <int P, typename T>
 __global__ void __launch_bounds__(128) m2l_kernel(const cpx<T>* __restrict__ Mt, const cpx<T>* __restrict__ Gt,
-                                                  cpx<T>* __restrict__ Lt, int64_t Kh, int p) {
+                                                  cpx<T>* __restrict__ Lt, int64_t Kh, int nsys, int p) {
   const int l = blockIdx.y;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= Kh) return;
+  const int64_t cstride = (int64_t)nsys * Kh, mk0 = (int64_t)blockIdx.z * Kh + k;
   m2l_order<P, T>(
-      l, p, [&](int c) { return Mt[(int64_t)c * Kh + k]; }, [&](int s) { return Gt[(int64_t)s * Kh + k]; },
-      [&](int c, cpx<T> v) { Lt[(int64_t)c * Kh + k] = v; });
+      l, p, [&](int c) { return Mt[c * cstride + mk0]; }, [&](int s) { return Gt[(int64_t)s * Kh + k]; },
+      [&](int c, cpx<T> v) { Lt[c * cstride + mk0] = v; });
 }
 
 template <int P, typename T>
-cudaError_t run(const void* Mt, const void* Gt, void* Lt, int64_t Kh, cudaStream_t s) {
-  dim3 grid((unsigned)((Kh + 127) / 128), P + 1);
-  m2l_kernel<P, T><<<grid, 128, 0, s>>>((const cpx<T>*)Mt, (const cpx<T>*)Gt, (cpx<T>*)Lt, Kh, P);
+cudaError_t run(const void* Mt, const void* Gt, void* Lt, int64_t Kh, int nsys, cudaStream_t s) {
+  dim3 grid((unsigned)((Kh + 127) / 128), P + 1, (unsigned)nsys);
+  m2l_kernel<P, T><<<grid, 128, 0, s>>>((const cpx<T>*)Mt, (const cpx<T>*)Gt, (cpx<T>*)Lt, Kh, nsys, P);
   return cudaGetLastError();
 }
 
 template <int P>
-cudaError_t dispatch(int p, bool fp64, const void* Mt, const void* Gt, void* Lt, int64_t Kh, cudaStream_t s) {
-  if (p == P) return fp64 ? run<P, double>(Mt, Gt, Lt, Kh, s) : run<P, float>(Mt, Gt, Lt, Kh, s);
-  if constexpr (P < PMMM_PMAX) return dispatch<P + 1>(p, fp64, Mt, Gt, Lt, Kh, s);
+cudaError_t dispatch(int p, bool fp64, const void* Mt, const void* Gt, void* Lt, int64_t Kh, int nsys,
+                     cudaStream_t s) {
+  if (p == P) return fp64 ? run<P, double>(Mt, Gt, Lt, Kh, nsys, s) : run<P, float>(Mt, Gt, Lt, Kh, nsys, s);
+  if constexpr (P < PMMM_PMAX) return dispatch<P + 1>(p, fp64, Mt, Gt, Lt, Kh, nsys, s);
   return cudaErrorInvalidValue;
 }
 
@@ -39,7 +42,14 @@ cudaError_t dispatch(int p, bool fp64, const void* Mt, const void* Gt, void* Lt,
 cudaError_t launch_m2l(int p, bool fp64, const void* Mt, const void* Gt, void* Lt, int64_t Kh, cudaStream_t s,
                        int* nl) {
   ++*nl;
-  return dispatch<0>(p, fp64, Mt, Gt, Lt, Kh, s);
+  return dispatch<0>(p, fp64, Mt, Gt, Lt, Kh, 1, s);
+}
+
+cudaError_t launch_m2l_systems(int p, bool fp64, const void* Mt, const void* Gt, void* Lt, int64_t Kh, int nsys,
+                               cudaStream_t s, int* nl) {
+  if (nsys < 1 || nsys > 65535) return cudaErrorInvalidValue;
+  ++*nl;
+  return dispatch<0>(p, fp64, Mt, Gt, Lt, Kh, nsys, s);
 }
 
 }  // namespace pmmm

@@ -88,13 +88,14 @@ __global__ void __launch_bounds__(256) p2m_kernel(const T* __restrict__ part, co
 template <int P, typename T>
 __global__ void __launch_bounds__(128) l2p_kernel(const T* __restrict__ part, const uint32_t* __restrict__ keys,
                                                   int64_t n, const T* __restrict__ L, int64_t K,
-                                                  const double* __restrict__ corr, const double* __restrict__ cellq,
+                                                  const double* __restrict__ corr_all, const double* __restrict__ cellq,
                                                   CorrParams cp, T* __restrict__ far) {
   constexpr int C = (P + 1) * (P + 1);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const typename V4<T>::type r = reinterpret_cast<const typename V4<T>::type*>(part)[i];
   const int64_t cell = keys[i];
+  const double* corr = corr_all + 16 * (cell / cp.ksys);  // this particle's system
   T R[C];
   regular_real<P, T>(r.x, r.y, r.z, R);
   T f, gx, gy, gz;

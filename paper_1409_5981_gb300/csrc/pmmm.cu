@@ -6,7 +6,7 @@
 #include <string.h>
 
 #include <new>
-
+#include <unordered_map>
 #include <vector>
 
 #include "internal.cuh"
@@ -54,8 +54,21 @@ struct pmmm_plan {
   uint32_t* pair_start = nullptr;  // [K+1] FP32 near-field source pairs per cell (scanned)
   void* src2 = nullptr;            // pair-interleaved FP32 sources
   int num_sms = 0;
-  double* energy = nullptr;   // [4]
+  double* energy = nullptr;   // [4 * bcap]: energy and net force per system
   int* err = nullptr;
+  // systems: the mesh workspace above holds bcap systems side by side
+  int bcap = 0;
+  int nsys_last = 1;
+  int64_t* offsets_d = nullptr;       // [bcap + 1] particle offsets of the systems
+  int64_t* offsets_pinned = nullptr;  // host staging of the offsets
+  std::vector<int64_t> offsets_up;    // offsets of the last upload
+  int* m2l_tab = nullptr;             // batched M2L entry table, 4 ints per entry
+  std::unordered_map<void*, size_t> sizes;
+  // CUDA graph of one batched evaluation, and the arguments it was captured for
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<int64_t> gkey_off;
+  const void* gkey_ptr[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool capturing = false;
   // particle workspace
   int64_t cap = 0;
   SortWork sw{};
@@ -78,52 +91,123 @@ cudaError_t dalloc(pmmm_plan* pl, void** ptr, size_t bytes) {
   *ptr = nullptr;
   if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMalloc(ptr, bytes);
-  if (e == cudaSuccess) pl->ws_bytes += bytes;
+  if (e == cudaSuccess) {
+    pl->ws_bytes += bytes;
+    pl->sizes[*ptr] = bytes;
+  }
   return e;
 }
 
-void dfree(void*& p) {
-  if (p) cudaFree(p);
+template <typename P>
+void dfree(pmmm_plan* pl, P*& p) {
+  if (p) {
+    auto it = pl->sizes.find((void*)p);
+    if (it != pl->sizes.end()) {
+      pl->ws_bytes -= it->second;
+      pl->sizes.erase(it);
+    }
+    cudaFree((void*)p);
+  }
   p = nullptr;
 }
 
 void free_particles(pmmm_plan* pl) {
-  void* v;
-  v = pl->sw.keys0; dfree(v);
-  v = pl->sw.keys1; dfree(v);
-  v = pl->sw.vals0; dfree(v);
-  v = pl->sw.vals1; dfree(v);
-  v = pl->sw.hist; dfree(v);
-  v = pl->sw.chunks; dfree(v);
+  dfree(pl, pl->sw.keys0);
+  dfree(pl, pl->sw.keys1);
+  dfree(pl, pl->sw.vals0);
+  dfree(pl, pl->sw.vals1);
+  dfree(pl, pl->sw.hist);
+  dfree(pl, pl->sw.chunks);
   pl->sw = SortWork{};
-  dfree(pl->part);
-  dfree(pl->far);
-  v = pl->item_cell; dfree(v); pl->item_cell = nullptr;
-  dfree(pl->src2);
-  v = pl->epart; dfree(v); pl->epart = nullptr;
+  dfree(pl, pl->part);
+  dfree(pl, pl->far);
+  dfree(pl, pl->item_cell);
+  dfree(pl, pl->src2);
+  dfree(pl, pl->epart);
   pl->max_items = 0;
   pl->cap = 0;
+}
+
+// Buffers whose size scales with the number of systems.
+void free_mesh(pmmm_plan* pl) {
+  dfree(pl, pl->M); dfree(pl, pl->L); dfree(pl, pl->specM); dfree(pl, pl->specL);
+  dfree(pl, pl->cellsum);
+  dfree(pl, pl->cs);
+  dfree(pl, pl->corr);
+  dfree(pl, pl->item_start);
+  dfree(pl, pl->item_chunks);
+  dfree(pl, pl->pair_start);
+  dfree(pl, pl->energy);
+  dfree(pl, pl->offsets_d);
+  if (pl->offsets_pinned) cudaFreeHost(pl->offsets_pinned);
+  pl->offsets_pinned = nullptr;
+  pl->offsets_up.clear();
+  pl->bcap = 0;
 }
 
 void free_all(pmmm_plan* pl) {
   if (!pl) return;
   free_particles(pl);
-  dfree(pl->M); dfree(pl->L); dfree(pl->specM); dfree(pl->specL); dfree(pl->G);
-  dfree(pl->twx); dfree(pl->twy); dfree(pl->twz);
-  void* v;
-  v = pl->cellsum; dfree(v); pl->cellsum = nullptr;
-  v = pl->cs; dfree(v); pl->cs = nullptr;
-  v = pl->corr; dfree(v); pl->corr = nullptr;
-  v = pl->partial; dfree(v); pl->partial = nullptr;
-  v = pl->item_start; dfree(v); pl->item_start = nullptr;
-  v = pl->item_chunks; dfree(v); pl->item_chunks = nullptr;
-  v = pl->counter; dfree(v); pl->counter = nullptr;
-  v = pl->pair_start; dfree(v); pl->pair_start = nullptr;
-  v = pl->energy; dfree(v); pl->energy = nullptr;
-  v = pl->err; dfree(v); pl->err = nullptr;
-  dfree(pl->hpos); dfree(pl->hq); dfree(pl->hphi); dfree(pl->hforce);
+  free_mesh(pl);
+  dfree(pl, pl->G);
+  dfree(pl, pl->twx); dfree(pl, pl->twy); dfree(pl, pl->twz);
+  dfree(pl, pl->partial);
+  dfree(pl, pl->counter);
+  dfree(pl, pl->err);
+  dfree(pl, pl->m2l_tab);
+  dfree(pl, pl->hpos); dfree(pl, pl->hq); dfree(pl, pl->hphi); dfree(pl, pl->hforce);
+  if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+  pl->gexec = nullptr;
   for (int i = 0; i <= ST_COUNT; ++i)
     if (pl->ev[i]) cudaEventDestroy(pl->ev[i]);
+}
+
+// Mesh workspace for B systems (B * K cells, C * B transform channels).
+cudaError_t alloc_mesh(pmmm_plan* pl, int B) {
+  const Dims& d = pl->d;
+  const size_t T = pl->tsize;
+  const int64_t Kb = d.K * B, Khb = d.Kh * B;
+  void* v;
+  cudaError_t e = dalloc(pl, &pl->M, T * pl->C * (size_t)Kb);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->L, T * pl->C * (size_t)Kb);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->specM, 2 * T * pl->C * (size_t)Khb);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->specL, 2 * T * pl->C * (size_t)Khb);
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 5 * (size_t)Kb); pl->cellsum = (double*)v; }
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(int) * (size_t)(Kb + 1)); pl->cs = (int*)v; }
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 16 * (size_t)B); pl->corr = (double*)v; }
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(uint32_t) * (size_t)(Kb + 1)); pl->item_start = (uint32_t*)v; }
+  if (e == cudaSuccess) {
+    e = dalloc(pl, &v, sizeof(uint32_t) * (size_t)scan_chunk_count(Kb + 1));
+    pl->item_chunks = (uint32_t*)v;
+  }
+  if (e == cudaSuccess && !pl->fp64) {
+    e = dalloc(pl, &v, sizeof(uint32_t) * (size_t)(Kb + 1));
+    pl->pair_start = (uint32_t*)v;
+  }
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 4 * (size_t)B); pl->energy = (double*)v; }
+  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(int64_t) * (size_t)(B + 1)); pl->offsets_d = (int64_t*)v; }
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&pl->offsets_pinned, sizeof(int64_t) * (size_t)(B + 1));
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->corr, 0, sizeof(double) * 16 * (size_t)B, pl->stream);
+  if (e == cudaSuccess) pl->bcap = B;
+  return e;
+}
+
+int ensure_particles(pmmm_plan* pl, int64_t n);
+
+// Grows the mesh workspace to B systems (the particle workspace, sized by the
+// cell count, is rebuilt with it).
+int ensure_systems(pmmm_plan* pl, int B) {
+  if (B <= pl->bcap) return PMMM_OK;
+  cudaStreamSynchronize(pl->stream);
+  const int64_t n = pl->cap;
+  free_particles(pl);
+  free_mesh(pl);
+  cudaError_t e = alloc_mesh(pl, B);
+  if (e != cudaSuccess) {
+    free_mesh(pl);
+    return map_cuda(e);
+  }
+  return ensure_particles(pl, n);
 }
 
 int validate(const pmmm_config* c) {
@@ -176,12 +260,13 @@ int ensure_particles(pmmm_plan* pl, int64_t n) {
 #undef ALLOC
   e = dalloc(pl, &pl->part, 4 * pl->tsize * (size_t)cap);
   if (e == cudaSuccess) e = dalloc(pl, &pl->far, 4 * pl->tsize * (size_t)cap);
-  const int64_t mi = pp_items_max(pl->d.K, cap);
+  const int64_t Kb = pl->d.K * pl->bcap;
+  const int64_t mi = pp_items_max(Kb, cap);
   if (e == cudaSuccess) e = dalloc(pl, &v, sizeof(uint32_t) * (size_t)mi);
   if (e == cudaSuccess) pl->item_cell = (uint32_t*)v;
   if (e == cudaSuccess) e = dalloc(pl, &v, sizeof(double) * 4 * (size_t)mi);
   if (e == cudaSuccess) pl->epart = (double*)v;
-  if (e == cudaSuccess && !pl->fp64) e = dalloc(pl, &pl->src2, 32 * (size_t)pp_pairs_max(pl->d.K, cap));
+  if (e == cudaSuccess && !pl->fp64) e = dalloc(pl, &pl->src2, 32 * (size_t)pp_pairs_max(Kb, cap));
   if (e != cudaSuccess) {
     free_particles(pl);
     return map_cuda(e);
@@ -244,17 +329,20 @@ int read_device_status(pmmm_plan* pl) {
 }
 
 void mark(pmmm_plan* pl, int st) {
-  if (pl->timing) cudaEventRecord(pl->ev[st], pl->stream);
+  if (pl->timing && !pl->capturing) cudaEventRecord(pl->ev[st], pl->stream);
 }
 
-int run(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, void* force) {
-  int rc = ensure_particles(pl, n);
+// One evaluation of B systems (B = 1: the single-system path; B > 1: the
+// systems' particle offsets are already on the device in offsets_d).
+int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* phi, void* force) {
+  int rc = ensure_systems(pl, B);
+  if (rc == PMMM_OK) rc = ensure_particles(pl, n);
   if (rc != PMMM_OK) return rc;
   cudaStream_t s = pl->stream;
   int nl = 0;
   cudaError_t e = cudaSuccess;
   const bool fp64 = pl->fp64;
-  const int64_t K = pl->d.K;
+  const int64_t Ks = pl->d.K, K = Ks * B;  // cells per system, cells of all systems
 #define CK(x)                    \
   do {                           \
     e = (x);                     \
@@ -265,7 +353,10 @@ int run(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, voi
     int key_bits = 0;
     while (((int64_t)1 << key_bits) < K) ++key_bits;
     // the unsorted records go to `far`, which L2P overwrites later
-    CK(launch_bin(pos, q, fp64, n, pl->g, pl->sw.keys0, pl->far, pl->err, s, &nl));
+    if (B == 1)
+      CK(launch_bin(pos, q, fp64, n, pl->g, pl->sw.keys0, pl->far, pl->err, s, &nl));
+    else
+      CK(launch_bin_batched(pos, q, fp64, n, pl->offsets_d, B, pl->g, Ks, pl->sw.keys0, pl->far, pl->err, s, &nl));
     CK(launch_radix_sort(pl->sw, n, key_bits, &pl->keys_sorted, &pl->vals_sorted, s, &nl));
     CK(launch_cell_bounds(pl->keys_sorted, n, K, pl->cs, s, &nl));
     CK(launch_gather(pl->far, fp64, pl->vals_sorted, n, pl->part, s, &nl));
@@ -278,15 +369,22 @@ int run(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, voi
   mark(pl, ST_FFT_FWD);
   {
     FftTw tw{pl->twx, pl->twy, pl->twz};
-    CK(launch_fft_forward(fp64, pl->M, pl->specM, pl->d, pl->C, tw, s, &nl));
+    CK(launch_fft_forward(fp64, pl->M, pl->specM, pl->d, pl->C * B, tw, s, &nl));
     mark(pl, ST_M2L);
-    CK(launch_m2l(pl->p, fp64, pl->specM, pl->G, pl->specL, pl->d.Kh, s, &nl));
+    if (B == 1)
+      CK(launch_m2l(pl->p, fp64, pl->specM, pl->G, pl->specL, pl->d.Kh, s, &nl));
+    else
+      CK(launch_m2l_batched(fp64, pl->specM, pl->G, pl->specL, pl->m2l_tab, pl->p, B, pl->d.Kh, s, &nl));
     mark(pl, ST_FFT_INV);
-    CK(launch_fft_inverse(fp64, pl->specL, pl->L, pl->d, pl->C, tw, s, &nl));
+    CK(launch_fft_inverse(fp64, pl->specL, pl->L, pl->d, pl->C * B, tw, s, &nl));
   }
   mark(pl, ST_L2P);
-  if (pl->g.periodic)
-    CK(launch_corrections(pl->cellsum, pl->cellsum + K, K, pl->g.hs, pl->g.V, pl->partial, pl->corr, s, &nl));
+  if (pl->g.periodic) {
+    if (B == 1)
+      CK(launch_corrections(pl->cellsum, pl->cellsum + K, K, pl->g.hs, pl->g.V, pl->partial, pl->corr, s, &nl));
+    else
+      CK(launch_corrections_batched(pl->cellsum, K, Ks, B, pl->g.hs, pl->g.V, pl->corr, s, &nl));
+  }
   {
     CorrParams cp;
     cp.hs = pl->g.hs;
@@ -297,6 +395,7 @@ int run(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, voi
     cp.c_charged = 1.5 / (pl->g.alpha * pl->g.alpha);
     cp.c_self = 2.0 * pl->g.alpha * 0.56418958354775628695;  // 2 alpha / sqrt(pi)
     cp.periodic = pl->g.periodic;
+    cp.ksys = Ks;
     CK(launch_l2p(pl->p, fp64, pl->part, pl->keys_sorted, n, pl->L, K, pl->corr, pl->cellsum, cp, pl->far, s, &nl));
   }
   mark(pl, ST_PP);
@@ -308,6 +407,7 @@ int run(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, voi
     }
     pp.c = pl->g.c;
     pp.periodic = pl->g.periodic;
+    pp.ksys = (int)Ks;
     pp.ihf = 1.0 / pl->g.hs;
     pp.ih2f = pp.ihf * pp.ihf;
     pp.signf = pl->g.sign;
@@ -319,14 +419,102 @@ int run(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, voi
     CK(launch_pp(fp64, pl->part, pl->src2, pl->pair_start, pl->vals_sorted, pl->cs, K, pl->item_start,
                  pl->item_cell, pl->counter, pl->num_sms, pl->far, pp, phi, force, pl->epart, s, &nl));
     mark(pl, ST_REDUCE);
-    CK(launch_energy(pl->epart, mi, pl->partial + 256 * 5, pl->energy, s, &nl));
+    if (B == 1)
+      CK(launch_energy(pl->epart, mi, pl->partial + 256 * 5, pl->energy, s, &nl));
+    else
+      CK(launch_energy_batched(pl->epart, pl->item_start, Ks, B, pl->energy, s, &nl));
   }
   mark(pl, ST_COUNT);
 #undef CK
 done:
   pl->launches = nl;
   pl->n_last = n;
-  pl->timed = pl->timing && e == cudaSuccess;
+  pl->nsys_last = B;
+  pl->timed = pl->timing && !pl->capturing && e == cudaSuccess;
+  return map_cuda(e);
+}
+
+// Validates host offsets of B systems and uploads them to offsets_d (skipped
+// when they equal the last upload).  Returns the particle count in *n.
+int upload_offsets(pmmm_plan* pl, int B, const int64_t* off, int64_t* n) {
+  if (!off || off[0] != 0) return PMMM_ERR_INVALID_ARG;
+  for (int s = 0; s < B; ++s)
+    if (off[s + 1] < off[s]) return PMMM_ERR_INVALID_ARG;
+  if (off[B] > INT32_MAX) return PMMM_ERR_INVALID_ARG;
+  *n = off[B];
+  int rc = ensure_systems(pl, B);
+  if (rc != PMMM_OK) return rc;
+  if (!pl->m2l_tab) {
+    std::vector<int> t = build_m2l_table_int4(pl->p);
+    void* v = nullptr;
+    cudaError_t e = dalloc(pl, &v, sizeof(int) * t.size());
+    if (e == cudaSuccess) e = cudaMemcpy(v, t.data(), sizeof(int) * t.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      dfree(pl, v);
+      return map_cuda(e);
+    }
+    pl->m2l_tab = (int*)v;
+  }
+  if (pl->offsets_up.size() == (size_t)B + 1 && memcmp(pl->offsets_up.data(), off, sizeof(int64_t) * (B + 1)) == 0)
+    return PMMM_OK;
+  // the staging buffer may still feed an earlier copy on the stream
+  cudaError_t e = cudaStreamSynchronize(pl->stream);
+  if (e == cudaSuccess) {
+    memcpy(pl->offsets_pinned, off, sizeof(int64_t) * (B + 1));
+    e = cudaMemcpyAsync(pl->offsets_d, pl->offsets_pinned, sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice,
+                        pl->stream);
+  }
+  if (e != cudaSuccess) {
+    pl->offsets_up.clear();
+    return map_cuda(e);
+  }
+  pl->offsets_up.assign(off, off + B + 1);
+  return PMMM_OK;
+}
+
+// Device-to-host copy of the per-system energies (synchronises), then the device status.
+int read_energies(pmmm_plan* pl, int B, double* out) {
+  std::vector<double> h(4 * (size_t)B);
+  cudaError_t e = cudaMemcpyAsync(h.data(), pl->energy, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, pl->stream);
+  if (e != cudaSuccess) return map_cuda(e);
+  const int rc = read_device_status(pl);
+  for (int s = 0; s < B; ++s) out[s] = h[4 * (size_t)s];
+  return rc;
+}
+
+// Plan-owned device buffers for host-array calls of n particles.
+int ensure_host_staging(pmmm_plan* pl, int64_t n) {
+  if (n <= pl->hcap) return PMMM_OK;
+  cudaStreamSynchronize(pl->stream);
+  dfree(pl, pl->hpos); dfree(pl, pl->hq); dfree(pl, pl->hphi); dfree(pl, pl->hforce);
+  pl->hcap = 0;
+  const size_t T = pl->tsize;
+  cudaError_t e = dalloc(pl, &pl->hpos, 3 * T * (size_t)n);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->hq, T * (size_t)n);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->hphi, T * (size_t)n);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->hforce, 3 * T * (size_t)n);
+  if (e != cudaSuccess) return map_cuda(e);
+  pl->hcap = n;
+  return PMMM_OK;
+}
+
+// Host arrays in, B systems evaluated, host arrays out (energies: 4 doubles per system on the device).
+int run_host(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* phi, void* force) {
+  int rc = ensure_host_staging(pl, n);
+  if (rc != PMMM_OK) return rc;
+  const size_t T = pl->tsize;
+  cudaStream_t s = pl->stream;
+  cudaError_t e = cudaSuccess;
+  if (n > 0) {
+    e = cudaMemcpyAsync(pl->hpos, pos, 3 * T * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pl->hq, q, T * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return map_cuda(e);
+  }
+  rc = run(pl, B, n, pl->hpos, pl->hq, phi ? pl->hphi : nullptr, force ? pl->hforce : nullptr);
+  if (rc != PMMM_OK) return rc;
+  if (phi && n > 0) e = cudaMemcpyAsync(phi, pl->hphi, T * (size_t)n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && force && n > 0)
+    e = cudaMemcpyAsync(force, pl->hforce, 3 * T * (size_t)n, cudaMemcpyDeviceToHost, s);
   return map_cuda(e);
 }
 
@@ -424,40 +612,22 @@ int pmmm_plan_create(const pmmm_config* cfg, void* stream, pmmm_plan** out) {
   g.c = cfg->cutoff;
   pl->nmax = cfg->ewald_nmax > 0 ? cfg->ewald_nmax : 5;
 
-  cudaError_t e = cudaSuccess;
   const size_t T = pl->tsize;
   void* v;
-  e = dalloc(pl, &pl->M, T * pl->C * (size_t)d.K);
-  if (e == cudaSuccess) e = dalloc(pl, &pl->L, T * pl->C * (size_t)d.K);
-  if (e == cudaSuccess) e = dalloc(pl, &pl->specM, 2 * T * pl->C * (size_t)d.Kh);
-  if (e == cudaSuccess) e = dalloc(pl, &pl->specL, 2 * T * pl->C * (size_t)d.Kh);
+  cudaError_t e = alloc_mesh(pl, 1);
   if (e == cudaSuccess) e = dalloc(pl, &pl->G, 2 * T * pl->CG * (size_t)d.Kh);
   if (e == cudaSuccess) e = dalloc(pl, &pl->twx, 2 * T * d.Lx);
   if (e == cudaSuccess) e = dalloc(pl, &pl->twy, 2 * T * d.Ly);
   if (e == cudaSuccess) e = dalloc(pl, &pl->twz, 2 * T * d.Lz);
-  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 5 * (size_t)d.K); pl->cellsum = (double*)v; }
-  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(int) * (size_t)(d.K + 1)); pl->cs = (int*)v; }
-  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 16); pl->corr = (double*)v; }
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 256 * 16); pl->partial = (double*)v; }
-  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(uint32_t) * (size_t)(d.K + 1)); pl->item_start = (uint32_t*)v; }
-  if (e == cudaSuccess) {
-    e = dalloc(pl, &v, sizeof(uint32_t) * (size_t)scan_chunk_count(d.K + 1));
-    pl->item_chunks = (uint32_t*)v;
-  }
-  if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 4); pl->energy = (double*)v; }
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(int)); pl->err = (int*)v; }
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(unsigned int)); pl->counter = (unsigned int*)v; }
-  if (e == cudaSuccess && !pl->fp64) {
-    e = dalloc(pl, &v, sizeof(uint32_t) * (size_t)(d.K + 1));
-    pl->pair_start = (uint32_t*)v;
-  }
   if (e == cudaSuccess) {
     int dev = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, dev);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(pl->err, 0, sizeof(int), pl->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(pl->corr, 0, sizeof(double) * 16, pl->stream);
   if (e == cudaSuccess) e = launch_twiddles(pl->fp64, d.Lx, pl->twx, pl->stream);
   if (e == cudaSuccess) e = launch_twiddles(pl->fp64, d.Ly, pl->twy, pl->stream);
   if (e == cudaSuccess) e = launch_twiddles(pl->fp64, d.Lz, pl->twz, pl->stream);
@@ -491,56 +661,105 @@ int pmmm_plan_reserve(pmmm_plan* pl, int64_t n) {
   return ensure_particles(pl, n);
 }
 
+int pmmm_plan_reserve_batched(pmmm_plan* pl, int32_t nsys, int64_t n) {
+  if (!pl || nsys < 1 || nsys > PMMM_MAX_SYSTEMS || n < 0 || n > INT32_MAX) return PMMM_ERR_INVALID_ARG;
+  if (pl->d.K * nsys > ((int64_t)1 << 30)) return PMMM_ERR_UNSUPPORTED;
+  int rc = ensure_systems(pl, nsys);
+  if (rc == PMMM_OK) rc = ensure_particles(pl, n);
+  return rc;
+}
+
 int pmmm_compute(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, void* force, double* energy) {
   if (!pl || n < 0 || n > INT32_MAX) return PMMM_ERR_INVALID_ARG;
   if (n > 0 && (!pos || !q)) return PMMM_ERR_INVALID_ARG;
-  int rc = run(pl, n, pos, q, phi, force);
+  int rc = run(pl, 1, n, pos, q, phi, force);
   if (rc != PMMM_OK) return rc;
-  if (energy) {
-    double h[4];
-    cudaError_t e = cudaMemcpyAsync(h, pl->energy, sizeof(h), cudaMemcpyDeviceToHost, pl->stream);
-    if (e != cudaSuccess) return map_cuda(e);
-    rc = read_device_status(pl);
-    *energy = h[0];
-    return rc;
-  }
-  return PMMM_OK;
+  return energy ? read_energies(pl, 1, energy) : PMMM_OK;
 }
 
 int pmmm_compute_host(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, void* force,
                       double* energy) {
   if (!pl || n < 0 || n > INT32_MAX) return PMMM_ERR_INVALID_ARG;
   if (n > 0 && (!pos || !q)) return PMMM_ERR_INVALID_ARG;
-  const size_t T = pl->tsize;
-  if (n > pl->hcap) {
-    cudaStreamSynchronize(pl->stream);
-    dfree(pl->hpos); dfree(pl->hq); dfree(pl->hphi); dfree(pl->hforce);
-    pl->hcap = 0;
-    cudaError_t e = dalloc(pl, &pl->hpos, 3 * T * (size_t)n);
-    if (e == cudaSuccess) e = dalloc(pl, &pl->hq, T * (size_t)n);
-    if (e == cudaSuccess) e = dalloc(pl, &pl->hphi, T * (size_t)n);
-    if (e == cudaSuccess) e = dalloc(pl, &pl->hforce, 3 * T * (size_t)n);
-    if (e != cudaSuccess) return map_cuda(e);
-    pl->hcap = n;
-  }
-  cudaStream_t s = pl->stream;
-  cudaError_t e = cudaSuccess;
-  if (n > 0) {
-    e = cudaMemcpyAsync(pl->hpos, pos, 3 * T * (size_t)n, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(pl->hq, q, T * (size_t)n, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return map_cuda(e);
-  }
-  int rc = run(pl, n, pl->hpos, pl->hq, phi ? pl->hphi : nullptr, force ? pl->hforce : nullptr);
+  int rc = run_host(pl, 1, n, pos, q, phi, force);
   if (rc != PMMM_OK) return rc;
-  double h[4] = {0, 0, 0, 0};
-  if (phi && n > 0) e = cudaMemcpyAsync(phi, pl->hphi, T * (size_t)n, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && force && n > 0)
-    e = cudaMemcpyAsync(force, pl->hforce, 3 * T * (size_t)n, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && energy) e = cudaMemcpyAsync(h, pl->energy, sizeof(h), cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return map_cuda(e);
-  rc = read_device_status(pl);
-  if (energy) *energy = h[0];
+  double e = 0.0;
+  rc = read_energies(pl, 1, &e);
+  if (energy) *energy = e;
   return rc;
+}
+
+int pmmm_compute_batched(pmmm_plan* pl, int32_t nsys, const int64_t* offsets, const void* pos, const void* q,
+                         void* phi, void* force, double* energies) {
+  if (!pl || nsys < 1 || nsys > PMMM_MAX_SYSTEMS || !offsets) return PMMM_ERR_INVALID_ARG;
+  if (pl->d.K * nsys > ((int64_t)1 << 30)) return PMMM_ERR_UNSUPPORTED;
+  int64_t n = 0;
+  int rc = upload_offsets(pl, nsys, offsets, &n);
+  if (rc != PMMM_OK) return rc;
+  if (n > 0 && (!pos || !q)) return PMMM_ERR_INVALID_ARG;
+  rc = run(pl, nsys, n, pos, q, phi, force);
+  if (rc != PMMM_OK) return rc;
+  return energies ? read_energies(pl, nsys, energies) : PMMM_OK;
+}
+
+int pmmm_compute_batched_host(pmmm_plan* pl, int32_t nsys, const int64_t* offsets, const void* pos, const void* q,
+                              void* phi, void* force, double* energies) {
+  if (!pl || nsys < 1 || nsys > PMMM_MAX_SYSTEMS || !offsets) return PMMM_ERR_INVALID_ARG;
+  if (pl->d.K * nsys > ((int64_t)1 << 30)) return PMMM_ERR_UNSUPPORTED;
+  int64_t n = 0;
+  int rc = upload_offsets(pl, nsys, offsets, &n);
+  if (rc != PMMM_OK) return rc;
+  if (n > 0 && (!pos || !q)) return PMMM_ERR_INVALID_ARG;
+  rc = run_host(pl, nsys, n, pos, q, phi, force);
+  if (rc != PMMM_OK) return rc;
+  std::vector<double> e((size_t)nsys);
+  rc = read_energies(pl, nsys, e.data());
+  if (energies) memcpy(energies, e.data(), sizeof(double) * nsys);
+  return rc;
+}
+
+int pmmm_compute_batched_graph(pmmm_plan* pl, int32_t nsys, const int64_t* offsets, const void* pos, const void* q,
+                               void* phi, void* force, double* energies) {
+  if (!pl || nsys < 1 || nsys > PMMM_MAX_SYSTEMS || !offsets) return PMMM_ERR_INVALID_ARG;
+  if (pl->d.K * nsys > ((int64_t)1 << 30)) return PMMM_ERR_UNSUPPORTED;
+  if (!pl->stream) return PMMM_ERR_UNSUPPORTED;  // the legacy default stream cannot be captured
+  int64_t n = 0;
+  int rc = upload_offsets(pl, nsys, offsets, &n);  // may synchronise: before any capture
+  if (rc != PMMM_OK) return rc;
+  if (n > 0 && (!pos || !q)) return PMMM_ERR_INVALID_ARG;
+  rc = ensure_particles(pl, n);
+  if (rc != PMMM_OK) return rc;
+  const void* ptrs[4] = {pos, q, phi, force};
+  const bool same = pl->gexec && pl->gkey_off.size() == (size_t)nsys + 1 &&
+                    memcmp(pl->gkey_off.data(), offsets, sizeof(int64_t) * (nsys + 1)) == 0 &&
+                    memcmp(pl->gkey_ptr, ptrs, sizeof(ptrs)) == 0;
+  cudaError_t e = cudaSuccess;
+  if (!same) {
+    if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+    pl->gexec = nullptr;
+    pl->gkey_off.clear();
+    e = cudaStreamBeginCapture(pl->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return map_cuda(e);
+    pl->capturing = true;
+    rc = run(pl, nsys, n, pos, q, phi, force);
+    pl->capturing = false;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(pl->stream, &graph);
+    if (e == cudaSuccess && rc == PMMM_OK) e = cudaGraphInstantiate(&pl->gexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != PMMM_OK) return rc;
+    if (e != cudaSuccess) {
+      pl->gexec = nullptr;
+      return map_cuda(e);
+    }
+    pl->gkey_off.assign(offsets, offsets + nsys + 1);
+    memcpy(pl->gkey_ptr, ptrs, sizeof(ptrs));
+  }
+  e = cudaGraphLaunch(pl->gexec, pl->stream);
+  if (e != cudaSuccess) return map_cuda(e);
+  pl->n_last = n;
+  pl->nsys_last = nsys;
+  return energies ? read_energies(pl, nsys, energies) : PMMM_OK;
 }
 
 int pmmm_plan_status(pmmm_plan* pl) {
@@ -552,7 +771,8 @@ int pmmm_plan_status(pmmm_plan* pl) {
 
 int pmmm_plan_export(pmmm_plan* pl, int what, void* dst, size_t bytes) {
   if (!pl || !dst) return PMMM_ERR_INVALID_ARG;
-  const int64_t n = pl->n_last, K = pl->d.K;
+  const int64_t n = pl->n_last, K = pl->d.K * pl->nsys_last;
+  const int B = pl->nsys_last;
   cudaStream_t s = pl->stream;
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return map_cuda(e);
@@ -583,19 +803,22 @@ int pmmm_plan_export(pmmm_plan* pl, int what, void* dst, size_t bytes) {
       break;
     }
     case PMMM_EXPORT_CORR: {
-      if (bytes != sizeof(double) * 8) return PMMM_ERR_INVALID_ARG;
-      double c[16] = {0};
-      e = cudaMemcpy(c, pl->corr, sizeof(c), cudaMemcpyDeviceToHost);
-      double* o = (double*)dst;
+      if (bytes != sizeof(double) * 8 * (size_t)B) return PMMM_ERR_INVALID_ARG;
+      std::vector<double> c(16 * (size_t)B);
+      e = cudaMemcpy(c.data(), pl->corr, sizeof(double) * c.size(), cudaMemcpyDeviceToHost);
       const double hs = pl->g.hs;
-      o[0] = c[8];                    // Q
-      o[1] = -c[11] * hs;             // sum M_1^0 = -sum q z_rel
-      o[2] = 0.5 * c[9] * hs;         // Re sum M_1^1 = sum q x_rel / 2
-      o[3] = 0.5 * c[10] * hs;        // Im sum M_1^1 = sum q y_rel / 2
-      o[4] = c[12] * hs * hs;         // sum q |r_rel|^2
-      o[5] = pl->g.alpha;
-      o[6] = pl->g.V;
-      o[7] = 0.0;
+      for (int b = 0; b < B; ++b) {
+        const double* cb = c.data() + 16 * (size_t)b;
+        double* o = (double*)dst + 8 * (size_t)b;
+        o[0] = cb[8];                    // Q
+        o[1] = -cb[11] * hs;             // sum M_1^0 = -sum q z_rel
+        o[2] = 0.5 * cb[9] * hs;         // Re sum M_1^1 = sum q x_rel / 2
+        o[3] = 0.5 * cb[10] * hs;        // Im sum M_1^1 = sum q y_rel / 2
+        o[4] = cb[12] * hs * hs;         // sum q |r_rel|^2
+        o[5] = pl->g.alpha;
+        o[6] = pl->g.V;
+        o[7] = 0.0;
+      }
       break;
     }
     case PMMM_EXPORT_FAR: {
@@ -626,6 +849,7 @@ int pmmm_plan_info(pmmm_plan* pl, int what, int64_t* value) {
     case PMMM_INFO_N: *value = pl->n_last; break;
     case PMMM_INFO_WORKSPACE_BYTES: *value = (int64_t)pl->ws_bytes; break;
     case PMMM_INFO_LAUNCHES: *value = pl->launches; break;
+    case PMMM_INFO_SYSTEMS: *value = pl->nsys_last; break;
     default: return PMMM_ERR_INVALID_ARG;
   }
   return PMMM_OK;

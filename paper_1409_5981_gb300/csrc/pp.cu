@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel(con
     V xi;
     xi.x = T(0); xi.y = T(0); xi.z = T(0); xi.w = T(0);
     if (active) xi = P[tbeg + tl];
-    const int ix = cell % nx, iy = (cell / nx) % ny, iz = cell / (nx * ny);
+    const int sbase = cell - cell % pp.ksys, lc = cell - sbase;  // system's first cell, local cell
+    const int ix = lc % nx, iy = (lc / nx) % ny, iz = lc / (nx * ny);
     // neighbour table: entry k (x fastest) in lane k % 32, slot k / 32
     int nbb[NB_SLOTS], nbc[NB_SLOTS];
 #pragma unroll
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel(con
         if (jy < 0 || jy >= ny) { ok = ok && pp.periodic; jy += (jy < 0) ? ny : -ny; }
         if (jz < 0 || jz >= nz) { ok = ok && pp.periodic; jz += (jz < 0) ? nz : -nz; }
         if (ok) {
-          const int cj = jx + nx * (jy + ny * jz);
+          const int cj = sbase + jx + nx * (jy + ny * jz);
           nbb[j] = __ldg(cs + cj);
           nbc[j] = __ldg(cs + cj + 1) - nbb[j];
         }
@@ -384,7 +385,8 @@ __global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel_f32
     const bool active = tl < R;
     float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
     if (active) xi = P[tbeg + tl];
-    const int ix = cell % nx, iy = (cell / nx) % ny, iz = cell / (nx * ny);
+    const int sbase = cell - cell % pp.ksys, lc = cell - sbase;  // system's first cell, local cell
+    const int ix = lc % nx, iy = (lc / nx) % ny, iz = lc / (nx * ny);
     // neighbour table: lane k < 27 holds the first pair and pair count of cell
     // (ix + k%3 - 1, iy + (k/3)%3 - 1, iz + k/9 - 1)
     int nbb = 0, nbc = 0;
@@ -395,7 +397,7 @@ __global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel_f32
       if (jy < 0 || jy >= ny) { ok = ok && pp.periodic; jy += (jy < 0) ? ny : -ny; }
       if (jz < 0 || jz >= nz) { ok = ok && pp.periodic; jz += (jz < 0) ? nz : -nz; }
       if (ok) {
-        const int cj = jx + nx * (jy + ny * jz);
+        const int cj = sbase + jx + nx * (jy + ny * jz);
         nbb = (int)__ldg(pair_start + cj);
         nbc = (int)__ldg(pair_start + cj + 1) - nbb;
       }

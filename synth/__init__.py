@@ -74,6 +74,21 @@ def batched_sizes(nsys: int, s: int, lo_exp: float = 14.0, hi_exp: float = 18.0)
     return (2 * np.round(2.0 ** (lo_exp + (hi_exp - lo_exp) * u) / 2.0)).astype(np.int64)
 
 
+def batched_uniform_pm1(sizes, config: int, rep: int = 0, lo=(0.0, 0.0, 0.0), length=(1.0, 1.0, 1.0)):
+    """Independent neutral uniform +-1 systems of the given sizes, system s drawn from
+    seed(config, 100 * rep + s); returns the concatenated (pos, q) and the offsets."""
+    pos, q = [], []
+    for s, n in enumerate(sizes):
+        a, b = uniform_pm1(int(n), seed(config, 100 * rep + s), lo, length)
+        pos.append(a)
+        q.append(b)
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(np.asarray(sizes, dtype=np.int64))
+    if not pos:
+        return np.zeros((0, 3)), np.zeros(0), off
+    return np.concatenate(pos, axis=0), np.concatenate(q), off
+
+
 def rock_salt(n: int, length: float = 1.0):
     """One ion at the centre of every cell of an n^3 mesh over [0, length)^3, charge
     (-1)^(ix+iy+iz): the NaCl lattice with spacing length/n."""

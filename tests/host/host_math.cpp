@@ -6,6 +6,7 @@
 #include "harmonics.cuh"
 #include "translations.cuh"
 #include "fft.cuh"
+#include "m2l_table.cuh"
 
 using namespace pmmm;
 
@@ -84,4 +85,21 @@ void h_fft(int L, int inverse, int single, double* data) {
 }
 void h_m2l_k(int p, const double* M, const double* G, double* L) { m2l_dispatch<0>(p, M, G, L); }
 void h_l2p(int p, const double* L, const double* u, double* out) { l2p_dispatch<0>(p, L, u, out); }
+// L = A M with A built from the entry table (complex k-space values)
+void h_m2l_table(int p, const double* M, const double* G, double* L) {
+  const int C = (p + 1) * (p + 1);
+  std::vector<M2LEntry> t = build_m2l_table(p);
+  for (int co = 0; co < C; ++co) {
+    double re = 0, im = 0;
+    for (int ci = 0; ci < C; ++ci) {
+      const M2LEntry& e = t[(size_t)co * C + ci];
+      const double ar = e.s1 * G[2 * e.i1] + e.s2 * G[2 * e.i2];
+      const double ai = e.s1 * G[2 * e.i1 + 1] + e.s2 * G[2 * e.i2 + 1];
+      re += ar * M[2 * ci] - ai * M[2 * ci + 1];
+      im += ar * M[2 * ci + 1] + ai * M[2 * ci];
+    }
+    L[2 * co] = re;
+    L[2 * co + 1] = im;
+  }
+}
 }

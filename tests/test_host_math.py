@@ -22,7 +22,8 @@ OUT = os.path.join(HERE, "_build", "libhostmath.so")
 @pytest.fixture(scope="module")
 def lib():
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
-    deps = [SRC] + [os.path.join(INC, f) for f in ("common.cuh", "harmonics.cuh", "translations.cuh", "fft.cuh")]
+    deps = [SRC] + [os.path.join(INC, f) for f in ("common.cuh", "harmonics.cuh", "translations.cuh", "fft.cuh",
+                                                   "m2l_table.cuh")]
     if not os.path.exists(OUT) or os.path.getmtime(OUT) < max(os.path.getmtime(d) for d in deps):
         tmp = OUT + f".{os.getpid()}"
         subprocess.run(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-I", INC, "-o", tmp, SRC], check=True)
@@ -34,6 +35,7 @@ def lib():
     L.h_fft.argtypes = [i, i, i, vp]
     L.h_m2l_k.argtypes = [i, vp, vp, vp]
     L.h_l2p.argtypes = [i, vp, vp, vp]
+    L.h_m2l_table.argtypes = [i, vp, vp, vp]
     return L
 
 
@@ -157,3 +159,18 @@ def test_l2p_real_form_vs_oracle(lib):
         assert abs(out[0] - phi) < 1e-12 * max(1, abs(phi))
         if p >= 1:
             assert np.abs(out[1:] - grad).max() < 1e-12 * max(1, np.abs(grad).max())
+
+
+def test_m2l_entry_table_matches_per_k_m2l(lib):
+    """The batched M2L's explicit matrix (entry table of App. A.8's real form) equals the
+    per-wavevector real-matrix M2L on complex (Fourier-space) inputs."""
+    g = synth.rng(107)
+    for p in (0, 1, 3, 7, 11):
+        C, CG = (p + 1) ** 2, (2 * p + 1) ** 2
+        M = np.ascontiguousarray(g.standard_normal(2 * C))
+        G = np.ascontiguousarray(g.standard_normal(2 * CG))
+        a = np.zeros(2 * C)
+        b = np.zeros(2 * C)
+        lib.h_m2l_k(p, P(M), P(G), P(a))
+        lib.h_m2l_table(p, P(M), P(G), P(b))
+        assert np.abs(a - b).max() < 1e-12 * max(1.0, np.abs(a).max()), p
