@@ -60,6 +60,8 @@ WORKLOADS = {
 # independent periodic unit boxes of neutral uniform +-1 charges, N log-uniform.
 BATCHED = {
     "periodic_batched64_logN14to18_mesh32_p7_fp32": (64, 14.0, 18.0, 32, 7, "fp32"),
+    # M2L as split-BF16 tensor-core GEMMs (FP32 accumulation), everything else FP32
+    "periodic_batched64_logN14to18_mesh32_p7_splitbf16": (64, 14.0, 18.0, 32, 7, "splitbf16"),
 }
 DEFAULT_WORKLOAD = "periodic_uniform_n1048576_mesh32_p7_fp32"
 METRIC = "particles/s per full force eval at fixed RMS force error; mesh-stage HBM % peak"
@@ -291,7 +293,7 @@ def run_reference(args, rank, world):
     return 0
 
 
-def _config(name, world):
+def _config(name, world, near="auto"):
     if name in BATCHED:
         nsys, lo_e, hi_e, mesh, p, prec = BATCHED[name]
         _, _, off = _batched_inputs(name, 0)
@@ -299,11 +301,16 @@ def _config(name, world):
                 "n_per_system": f"log-uniform 2^{lo_e:g}..2^{hi_e:g}, even", "boundary": "periodic",
                 "mesh": [mesh] * 3, "fft_grid": [mesh] * 3, "p": p, "cutoff_cells": 27, "distribution": "uniform_pm1",
                 "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
-                "launch": "CUDA graph of the whole batched evaluation"}
+                "launch": "CUDA graph of the whole batched evaluation", "near_field_kernel": near}
     n, boundary, mesh, p, prec, lo, ln, gen, sign = WORKLOADS[name]
     return {"workload": name, "n_particles": n, "boundary": boundary, "mesh": [mesh] * 3,
             "fft_grid": [mesh if boundary == "periodic" else 2 * mesh] * 3, "p": p, "cutoff_cells": 27,
-            "distribution": gen, "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)"}
+            "distribution": gen, "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
+            "near_field_kernel": near}
+
+
+def _near(pk, args):
+    return {"auto": pk.NEAR_AUTO, "items": pk.NEAR_CELL_ITEMS, "target": pk.NEAR_PER_TARGET}[args.near_field]
 
 
 def run_ours(args, rank, world, local_rank):
@@ -319,7 +326,7 @@ def run_ours(args, rank, world, local_rank):
     dt = torch.float64 if fp64 else torch.float32
     cfg = pk.Config(box_lo=lo, box_len=ln, mesh=(mesh,) * 3, p=p, cutoff=1,
                     boundary=pk.PERIODIC if boundary == "periodic" else pk.OPEN,
-                    precision=pk.FP64 if fp64 else pk.FP32, sign=sign)
+                    precision=pk.FP64 if fp64 else pk.FP32, sign=sign, near_field=_near(pk, args))
     stream = torch.cuda.current_stream()
     t_plan = time.perf_counter()
     plan = pk.Plan(cfg, stream)
@@ -438,7 +445,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
-        "config": _config(name, world),
+        "config": _config(name, world, args.near_field),
         "rel_rms_force_err_vs_fp64_oracle_pmmm": err,
         "stage_ms": {k: statistics.median(v) for k, v in stage_acc.items()},
         "plan_create_s": t_plan,
@@ -479,7 +486,9 @@ def run_ours_batched(args, rank, world, local_rank):
     fp64 = prec == "fp64"
     dt = torch.float64 if fp64 else torch.float32
     npdt = np.float64 if fp64 else np.float32
-    cfg = pk.Config(mesh=(mesh,) * 3, p=p, cutoff=1, boundary=pk.PERIODIC, precision=pk.FP64 if fp64 else pk.FP32)
+    precision = {"fp64": pk.FP64, "fp32": pk.FP32, "splitbf16": pk.FP32_SPLITBF16_M2L}[prec]
+    cfg = pk.Config(mesh=(mesh,) * 3, p=p, cutoff=1, boundary=pk.PERIODIC, precision=precision,
+                    near_field=_near(pk, args))
     stream = torch.cuda.Stream(dev)
     plan = pk.Plan(cfg, stream)
     pos_np, q_np, off = _batched_inputs(name, rank)
@@ -544,7 +553,8 @@ def run_ours_batched(args, rank, world, local_rank):
     total_ms = sum(step_ms)
 
     # the plain method on the same GPU: one single-system plan evaluation per system
-    single = pk.Plan(cfg, stream)
+    single = pk.Plan(pk.Config(mesh=(mesh,) * 3, p=p, cutoff=1, boundary=pk.PERIODIC,
+                               precision=pk.FP64 if fp64 else pk.FP32, near_field=_near(pk, args)), stream)
     single.reserve(int(counts.max()))
 
     def seq():
@@ -623,8 +633,9 @@ def run_ours_batched(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
-        "config": _config(name, world),
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "splitbf16": "f32+bf16x3"}[prec],
+        "data": "synthetic",
+        "config": _config(name, world, args.near_field),
         "rel_rms_force_err_vs_fp64_oracle_pmmm": err,
         "stage_ms": stage,
         "plain_batched_ms": plain_ms,
@@ -663,6 +674,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCHED), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--near-field", choices=["auto", "items", "target"], default="auto",
+                    help="near-field kernel: automatic by cell occupancy, cell items, or one thread per target")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -50,6 +50,17 @@ typedef enum { PMMM_OPEN = 0, PMMM_PERIODIC = 1 } pmmm_boundary;
  * tensor-core M2L and currently behaves as FP32. */
 typedef enum { PMMM_FP64 = 0, PMMM_FP32 = 1, PMMM_FP32_SPLITBF16_M2L = 2 } pmmm_precision;
 
+/* Near-field kernel (Sec. 2.2's direct sum over the (2c+1)^3 nearest cells; the
+ * choice changes only the order of floating-point sums):
+ *   PMMM_NEAR_CELL_ITEMS  one warp per work item (a cell and up to 32 of its
+ *                         particles), sources staged per warp: for filled cells
+ *   PMMM_NEAR_PER_TARGET  one thread per particle (FP32 precisions, c = 1 only):
+ *                         for sparsely filled cells
+ *   PMMM_NEAR_AUTO        per target when N < PMMM_NEAR_AUTO_OCCUPANCY x cells
+ *                         (and it applies), else cell items */
+typedef enum { PMMM_NEAR_AUTO = 0, PMMM_NEAR_CELL_ITEMS = 1, PMMM_NEAR_PER_TARGET = 2 } pmmm_near_field;
+#define PMMM_NEAR_AUTO_OCCUPANCY 8
+
 enum {
   PMMM_OK = 0,
   PMMM_ERR_INVALID_ARG = -1,     /* NULL pointer, bad size, bad config field */
@@ -70,7 +81,7 @@ typedef struct pmmm_config {
   int32_t cutoff;      /* c: minimum cell separation of the far field; 1 -> 27 near cells, 2 -> 125 */
   int32_t boundary;    /* pmmm_boundary */
   int32_t precision;   /* pmmm_precision */
-  int32_t reserved0;
+  int32_t near_field;  /* pmmm_near_field: near-field kernel (results agree to rounding) */
   double sign;         /* +1 Coulomb, -1 gravity */
   double ewald_alpha;  /* periodic splitting parameter; 0 -> 1.5 / min(box_len) (App. B.1 example) */
   int32_t ewald_nmax;  /* periodic lattice sums over |n|_2 <= nmax (both sums); 0 -> 5 */

@@ -21,6 +21,8 @@ ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OUT_OF_BOX, ERR_NONFINITE_INPUT = -1, -2, 
 ERR_CUDA, ERR_TIMEOUT, ERR_OOM = -5, -6, -7
 OPEN, PERIODIC = 0, 1
 FP64, FP32, FP32_SPLITBF16_M2L = 0, 1, 2
+NEAR_AUTO, NEAR_CELL_ITEMS, NEAR_PER_TARGET = 0, 1, 2
+NEAR_AUTO_OCCUPANCY = 8
 EXPORT_PERM, EXPORT_SORTED_CELL, EXPORT_CELL_START = 1, 2, 3
 EXPORT_MULTIPOLE, EXPORT_LOCAL, EXPORT_CORR, EXPORT_FAR = 4, 5, 6, 7
 INFO_K, INFO_C, INFO_CG, INFO_KH, INFO_N, INFO_WORKSPACE_BYTES, INFO_LAUNCHES = 1, 2, 3, 4, 5, 6, 7
@@ -44,7 +46,7 @@ class _Config(ctypes.Structure):
         ("cutoff", ctypes.c_int32),
         ("boundary", ctypes.c_int32),
         ("precision", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("near_field", ctypes.c_int32),
         ("sign", ctypes.c_double),
         ("ewald_alpha", ctypes.c_double),
         ("ewald_nmax", ctypes.c_int32),
@@ -152,6 +154,7 @@ class Config:
     sign: float = 1.0
     ewald_alpha: float = 0.0
     ewald_nmax: int = 0
+    near_field: int = NEAR_AUTO
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -162,6 +165,7 @@ class Config:
             c.mesh[a] = int(self.mesh[a])
         c.p, c.cutoff, c.boundary, c.precision = int(self.p), int(self.cutoff), int(self.boundary), int(self.precision)
         c.sign, c.ewald_alpha, c.ewald_nmax = float(self.sign), float(self.ewald_alpha), int(self.ewald_nmax)
+        c.near_field = int(self.near_field)
         return c
 
     @property

@@ -39,7 +39,8 @@ __global__ void bin_batched_kernel(const T* __restrict__ pos, const T* __restric
   bin_record<T>(pos, q, i, g, (uint32_t)((int64_t)s * Ksys), keys, rec, err);
 }
 
-// Batched M2L: block = KT consecutive wavevectors x BT systems.  Shared memory:
+// Batched M2L on wavevector-major spectra ([k][c][system]): block = KT
+// consecutive wavevectors x BT systems.  Shared memory:
 // Ms[c][kt][b] (M~ in, L~ out), At[c_in][c_out] (A~ of the current k), g[s].
 // Thread tiles of 4 output channels x 4 systems.
 template <typename T, int KT>
@@ -55,11 +56,12 @@ __global__ void __launch_bounds__(256) m2l_batched_kernel(const cpx<T>* __restri
   const int b0 = blockIdx.y * BT;
   const int nb = min(BT, B - b0);
   const int tid = threadIdx.x;
-  // M~ tile: element (c, b, kt) of system b0 + b at Mt[(c*B + b0 + b)*Kh + k0 + kt]
+  // M~ tile: element (c, b, kt) of system b0 + b at Mt[((k0 + kt)*C + c)*B + b0 + b]
+  // (wavevector-major spectra: consecutive threads read consecutive systems)
   for (int idx = tid; idx < C * nb * KT; idx += blockDim.x) {
-    const int kt = idx % KT, cb = idx / KT, b = cb % nb, c = cb / nb;
+    const int b = idx % nb, ck = idx / nb, c = ck % C, kt = ck / C;
     cpx<T> v = mk(T(0), T(0));
-    if (kt < kc) v = Mt[((int64_t)c * B + b0 + b) * Kh + k0 + kt];
+    if (kt < kc) v = Mt[((k0 + kt) * C + c) * B + b0 + b];
     Ms[((size_t)c * KT + kt) * BT + b] = v;
   }
   const int ntc = (C + 3) / 4, ntb = (nb + 3) / 4, ntile = ntc * ntb;
@@ -114,8 +116,8 @@ __global__ void __launch_bounds__(256) m2l_batched_kernel(const cpx<T>* __restri
     __syncthreads();
   }
   for (int idx = tid; idx < C * nb * KT; idx += blockDim.x) {
-    const int kt = idx % KT, cb = idx / KT, b = cb % nb, c = cb / nb;
-    if (kt < kc) Lt[((int64_t)c * B + b0 + b) * Kh + k0 + kt] = Ms[((size_t)c * KT + kt) * BT + b];
+    const int b = idx % nb, ck = idx / nb, c = ck % C, kt = ck / C;
+    if (kt < kc) Lt[((k0 + kt) * C + c) * B + b0 + b] = Ms[((size_t)c * KT + kt) * BT + b];
   }
 }
 
@@ -175,6 +177,26 @@ __global__ void __launch_bounds__(256) energy_batched_kernel(const double* __res
   if (threadIdx.x < 4) energies[4 * s + threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// out[k][r] = in[r][k] for an R x Kh matrix of complex values; 32 x 32 tiles
+// through shared memory so that both the reads and the writes are coalesced.
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_kernel(const cpx<T>* __restrict__ in, cpx<T>* __restrict__ out,
+                                                        int64_t R, int64_t Kh) {
+  __shared__ cpx<T> tile[32][33];
+  const int64_t nk = (Kh + 31) / 32;  // tiles along k (fastest), then along r
+  const int64_t k0 = ((int64_t)blockIdx.x % nk) * 32, r0 = ((int64_t)blockIdx.x / nk) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t r = r0 + j, k = k0 + tx;
+    if (r < R && k < Kh) tile[j][tx] = in[r * Kh + k];
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t k = k0 + j, r = r0 + tx;
+    if (r < R && k < Kh) out[k * R + r] = tile[tx][j];
+  }
+}
+
 template <typename T>
 size_t m2l_batched_smem(int C, int CG, int KT, int BT) {
   return sizeof(cpx<T>) * ((size_t)C * KT * BT + (size_t)C * C + (size_t)CG);
@@ -221,20 +243,46 @@ cudaError_t launch_bin_batched(const void* pos, const void* q, bool fp64, int64_
   return cudaGetLastError();
 }
 
+cudaError_t launch_transpose(bool fp64, const void* in, void* out, int64_t R, int64_t Kh, cudaStream_t s, int* nl) {
+  if (R <= 0 || Kh <= 0) return cudaSuccess;
+  const int64_t tiles = ((Kh + 31) / 32) * ((R + 31) / 32);
+  if (tiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
+  const unsigned grid = (unsigned)tiles;
+  if (fp64)
+    transpose_kernel<double><<<grid, 256, 0, s>>>((const cpx<double>*)in, (cpx<double>*)out, R, Kh);
+  else
+    transpose_kernel<float><<<grid, 256, 0, s>>>((const cpx<float>*)in, (cpx<float>*)out, R, Kh);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+namespace {
+// systems per block of the SIMT matrix product, or 0 when A~ does not fit
+int m2l_batched_bt(bool fp64, int p, int B) {
+  const int C = (p + 1) * (p + 1), CG = (2 * p + 1) * (2 * p + 1);
+  const size_t cap = 200 * 1024;
+  const size_t esz = fp64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
+  int BT = B;
+  while (BT > 4 && ((C + 3) / 4) * ((BT + 3) / 4) > 256) BT = (BT + 1) / 2;
+  while (BT > 1 && esz * ((size_t)C * BT + (size_t)C * C + CG) > cap) BT = (BT + 1) / 2;
+  if (esz * ((size_t)C * BT + (size_t)C * C + CG) > cap || BT < 4) return 0;
+  return BT;
+}
+}  // namespace
+
+bool m2l_batched_gemm(bool fp64, int p, int B) { return m2l_batched_bt(fp64, p, B) > 0; }
+
 // Chooses the wavevectors per block (KT) and systems per block (BT) that fit
-// the shared memory and the one-tile-per-thread layout (C/4 * BT/4 <= 256);
-// falls back to the per-wavevector kernel when fewer than 4 systems fit.
+// the shared memory and the one-tile-per-thread layout (C/4 * BT/4 <= 256).
+// Spectra are wavevector-major; m2l_batched_gemm() tells whether it applies.
 cudaError_t launch_m2l_batched(bool fp64, const void* Mt, const void* Gt, void* Lt, const int* tab, int p, int B,
                                int64_t Kh, cudaStream_t s, int* nl) {
   const int C = (p + 1) * (p + 1), CG = (2 * p + 1) * (2 * p + 1);
   const size_t cap = 200 * 1024;
-  int BT = B;
-  while (BT > 4 && ((C + 3) / 4) * ((BT + 3) / 4) > 256) BT = (BT + 1) / 2;
+  const int BT = m2l_batched_bt(fp64, p, B);
+  if (BT == 0) return cudaErrorInvalidConfiguration;
   const size_t esz = fp64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
   auto fits = [&](int KT, int bt) { return esz * ((size_t)C * KT * bt + (size_t)C * C + CG) <= cap; };
-  while (BT > 1 && !fits(1, BT)) BT = (BT + 1) / 2;
-  // A~ too large for shared memory: one thread per (k, l, system) instead
-  if (!fits(1, BT) || BT < 4) return launch_m2l_systems(p, fp64, Mt, Gt, Lt, Kh, B, s, nl);
   ++*nl;
   const int4* t4 = (const int4*)tab;
   if (fits(4, BT))

@@ -118,9 +118,21 @@ cudaError_t launch_bin_batched(const void* pos, const void* q, bool fp64, int64_
                                int* nlaunch);
 // Entry table of the real-matrix M2L as 4 ints per entry (i1, s1, i2, s2), C*C entries.
 std::vector<int> build_m2l_table_int4(int p);
-// L~(k) = A~(k) M~(k) for all systems at once (spectra [c][system][k]); tab on the device.
+// out[k][r] = in[r][k] for complex R x Kh (channel-major <-> wavevector-major spectra)
+cudaError_t launch_transpose(bool fp64, const void* in, void* out, int64_t R, int64_t Kh, cudaStream_t s,
+                             int* nlaunch);
+// Whether the SIMT matrix-product M2L fits (else launch_m2l_systems on channel-major spectra).
+bool m2l_batched_gemm(bool fp64, int p, int nsys);
+// L~(k) = A~(k) M~(k) for all systems at once on wavevector-major spectra
+// ([k][c][system]); tab on the device.
 cudaError_t launch_m2l_batched(bool fp64, const void* Mt, const void* Gt, void* Lt, const int* tab, int p, int nsys,
                                int64_t Kh, cudaStream_t s, int* nlaunch);
+// The same product on the tensor cores (m2l_tc.cu): FP32 wavevector-major spectra,
+// split-BF16 operands, FP32 accumulation; p <= 7.  tab: build_m2l_table_tc(p) on the device.
+bool m2l_tc_supported(int p);
+std::vector<uint32_t> build_m2l_table_tc(int p);
+cudaError_t launch_m2l_tc(const void* Mt, const void* Gt, void* Lt, const uint32_t* tab, int p, int nsys, int64_t Kh,
+                          int num_sms, int* err, cudaStream_t s, int* nlaunch);
 // corr[16 s + ...] of every system (the single-system layout of launch_corrections)
 cudaError_t launch_corrections_batched(const double* cellsum, int64_t Ktot, int64_t Ksys, int nsys, double hs,
                                        double V, double* corr, cudaStream_t s, int* nlaunch);
@@ -154,9 +166,10 @@ struct PPParams {
 int64_t pp_items_max(int64_t K, int64_t n);
 // source pairs of the FP32 near field: at most (n + K) / 2 + 1
 int64_t pp_pairs_max(int64_t K, int64_t n);
+// zero_all: zero the energy partials of every item slot (the per-target kernel accumulates into them)
 cudaError_t launch_pp_items(const int* cell_start, int64_t K, uint32_t* item_start, uint32_t* item_cell,
                             uint32_t* pair_start, uint32_t* chunks, unsigned int* counter, double* epart,
-                            int64_t max_items, cudaStream_t s, int* nlaunch);
+                            int64_t max_items, bool zero_all, cudaStream_t s, int* nlaunch);
 // pair-interleaved FP32 source records (see pp.cu), src2: 32 bytes per pair
 cudaError_t launch_pair_pack(const void* part, const uint32_t* keys, const int* cell_start, const uint32_t* pair_start,
                              int64_t n, void* src2, cudaStream_t s, int* nlaunch);
@@ -164,10 +177,13 @@ cudaError_t launch_pair_pack(const void* part, const uint32_t* keys, const int* 
 // the caller's order to phi / force; energy and force partials per work item
 // (epart[max_items][4]).  Persistent warps fetch items from *counter.  With
 // FP32, c = 1 and src2 given, the packed-FP32 kernel on the pair layout is used.
+// per_target (FP32, c = 1 only): one thread per sorted target (keys = sorted cell ids), for sparse cells.
+bool pp_per_target_applies(bool fp64, int c);
 cudaError_t launch_pp(bool fp64, const void* part, const void* src2, const uint32_t* pair_start, const uint32_t* vals,
-                      const int* cell_start, int64_t K, const uint32_t* item_start, const uint32_t* item_cell,
-                      unsigned int* counter, int num_sms, const void* far, PPParams pp, void* phi, void* force,
-                      double* epart, cudaStream_t s, int* nlaunch);
+                      const uint32_t* keys, int64_t n, bool per_target, const int* cell_start, int64_t K,
+                      const uint32_t* item_start, const uint32_t* item_cell, unsigned int* counter, int num_sms,
+                      const void* far, PPParams pp, void* phi, void* force, double* epart, cudaStream_t s,
+                      int* nlaunch);
 
 // ---------------------------------------------------------------- reduce.cu
 // Sums per-cell FP64 quantities and builds the periodic correction terms:

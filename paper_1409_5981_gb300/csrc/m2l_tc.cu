@@ -1,0 +1,339 @@
+// Batched M2L on the 5th-generation tensor cores (tcgen05), split-BF16 operands
+// with FP32 accumulation in tensor memory.
+//
+// Per wavevector k, the M2L of all systems (Sec. 2.1, real-matrix form of
+// App. A.8) is the complex product L~ = A~ M~ with A~ (C x C) assembled from the
+// kernel spectra and M~ (C x B).  Written as one real product with interleaved
+// rows,
+//   [Re L_c ; Im L_c] (row 2c, 2c+1) = [[Re A_c, -Im A_c], [Im A_c, Re A_c]] . [Re M ; Im M],
+// it is a D[128 x N] = W[128 x 128] X[128 x N] GEMM with C padded to 64 channels
+// (p <= 7).  Each FP32 operand x is split into x_hi = bf16(x) and
+// x_lo = bf16(x - x_hi); D accumulates W_hi X_hi + W_hi X_lo + W_lo X_hi (the
+// lo-lo term, below 2^-18 relative, is dropped), so every product carries a
+// relative error of at most about 3 * 2^-18.
+//
+// Spectra are wavevector-major ([k][c][system]), so each wavevector's M~ and L~
+// are one contiguous block.  One CTA of 256 threads owns a contiguous range of wavevectors and a tile of up
+// to 64 systems.  Per wavevector all threads build W and X in shared memory (two
+// buffers), one thread issues the 24 MMAs (M = 128, N = 64 or less, K = 16) into
+// one of two TMEM accumulators and commits them to an mbarrier, and while they
+// run the threads drain the previous accumulator (tcgen05.ld) to global memory.
+// Shared-memory operands use the no-swizzle K-major layout of core matrices
+// (8 rows x 16 bytes): element (r, k) at (r/8)*SBO + (k/8)*LBO + (r%8)*16 + (k%8)*2
+// with LBO = 128 B and SBO = 2048 B.  Every mbarrier wait is bounded; on a
+// timeout the kernel sets the plan's error flag, releases its tensor memory and
+// returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+#include "m2l_table.cuh"
+
+namespace pmmm {
+
+namespace {
+
+constexpr int TC_THREADS = 256;
+constexpr int TC_CH = 64;                             // channels after padding (p <= 7)
+constexpr int TC_K = 2 * TC_CH;                       // GEMM K: Re and Im parts of M
+constexpr int TC_NMAX = 64;                           // systems per tile (GEMM N)
+constexpr uint32_t TC_LBO = 128;                      // next core matrix along K
+constexpr uint32_t TC_SBO = (TC_K / 8) * 128;         // next 8-row group: 2048 B
+constexpr uint32_t TC_A_BYTES = 128 * TC_K * 2;       // one split of W: 32 KB
+constexpr uint32_t TC_B_BYTES = TC_NMAX * TC_K * 2;   // one split of X: 16 KB
+constexpr uint32_t TC_STAGE = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // 96 KB
+constexpr uint32_t TC_GK_BYTES = 2048;                // (2p+1)^2 <= 225 complex
+constexpr uint32_t TC_TAB_BYTES = TC_CH * TC_CH * 4;  // packed entry table, 16 KB
+constexpr uint32_t TC_OFF_GK = 2 * TC_STAGE;
+constexpr uint32_t TC_OFF_TAB = TC_OFF_GK + TC_GK_BYTES;
+constexpr uint32_t TC_OFF_BAR = TC_OFF_TAB + TC_TAB_BYTES;
+constexpr uint32_t TC_SMEM = TC_OFF_BAR + 64;
+constexpr uint32_t TC_TMEM_COLS = 2 * TC_NMAX;        // two accumulators
+constexpr long long TC_WAIT_LIMIT = 1ll << 26;        // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, LBO, SBO (all >> 4), version 1,
+// no swizzle.
+__device__ __forceinline__ uint64_t make_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(TC_LBO >> 4) << 16) | ((uint64_t)(TC_SBO >> 4) << 32) |
+         (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 D, BF16 A and B, both K-major, N, M = 128.
+__device__ __forceinline__ uint32_t make_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// 32 lanes x 16 columns of 32-bit accumulators: lane i of the warp reads TMEM
+// lane (taddr >> 16) + i.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// hi / lo BF16 split of 8 values, packed in K order (element j at the lower address).
+__device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const __nv_bfloat162 bh = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+    const float r0 = x[2 * j] - __low2float(bh), r1 = x[2 * j + 1] - __high2float(bh);
+    const __nv_bfloat162 bl = __floats2bfloat162_rn(r0, r1);
+    h[j] = *reinterpret_cast<const uint32_t*>(&bh);
+    l[j] = *reinterpret_cast<const uint32_t*>(&bl);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ uint4 neg_bf16(uint4 v) {
+  return make_uint4(v.x ^ 0x80008000u, v.y ^ 0x80008000u, v.z ^ 0x80008000u, v.w ^ 0x80008000u);
+}
+
+// byte offset of the 16-byte chunk (row r, K-group g) in one operand
+__device__ __forceinline__ uint32_t chunk_off(int r, int g) {
+  return (uint32_t)(r >> 3) * TC_SBO + (uint32_t)g * TC_LBO + (uint32_t)(r & 7) * 16;
+}
+
+// Entry table packing: i1 | (s1 + 1) << 10 | i2 << 12 | (s2 + 1) << 22
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    m2l_tc_kernel(const float2* __restrict__ Mt, const float2* __restrict__ Gt, float2* __restrict__ Lt,
+                  const uint32_t* __restrict__ tab_g, int C, int CG, int B, int64_t Kh, int64_t kchunk,
+                  int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float2* gk = reinterpret_cast<float2*>(smem + TC_OFF_GK);
+  uint32_t* tab = reinterpret_cast<uint32_t*>(smem + TC_OFF_TAB);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_OFF_BAR);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + TC_OFF_BAR + 16);
+  int* abort_flag = reinterpret_cast<int*>(smem + TC_OFF_BAR + 20);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b0 = blockIdx.y * TC_NMAX;
+  const int nb = min(TC_NMAX, B - b0);
+  const int nmma = (nb + 15) & ~15;  // GEMM N: systems padded to a multiple of 16
+  const int64_t kbeg = (int64_t)blockIdx.x * kchunk, kend = min(Kh, kbeg + kchunk);
+
+  for (int i = tid; i < TC_CH * TC_CH; i += TC_THREADS) tab[i] = tab_g[i];
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])));
+    *abort_flag = 0;
+    fence_proxy_async();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = make_idesc(nmma);
+  const uint32_t sbase = smem_u32(smem);
+
+  // drains accumulator `buf` (wavevector k) to Lt: warp w reads TMEM lanes 32 (w % 4) ...
+  // (rows: Re / Im of channel row / 2) and columns 32 (w / 4) ... of the tile
+  auto drain = [&](int buf, int64_t k, uint32_t parity) -> bool {
+    // warp-uniform outcome: the TMEM loads below are .sync.aligned
+    if (!__all_sync(0xffffffffu, bar_wait(smem_u32(&bars[buf]), parity))) return false;
+    fence_after();
+    const int row = 32 * (warp & 3) + lane;
+    const int col0 = 32 * (warp >> 2);
+    float v[32];
+    const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(buf * TC_NMAX + col0);
+    tmem_ld16(taddr, v);
+    tmem_ld16(taddr + 16, v + 16);
+    tmem_wait_ld();
+    const int c = row >> 1;
+    const bool odd = lane & 1;
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      const float a = v[2 * jj], b = v[2 * jj + 1];
+      const float recv = __shfl_xor_sync(0xffffffffu, odd ? a : b, 1);
+      const int n = col0 + 2 * jj + (odd ? 1 : 0);
+      if (c < C && n < nb) Lt[(k * C + c) * B + b0 + n] = odd ? make_float2(recv, b) : make_float2(a, recv);
+    }
+    fence_before();
+    return true;
+  };
+
+  int it = 0;
+  int64_t kprev = -1;
+  bool ok = true;
+  for (int64_t k = kbeg; k < kend; ++k, ++it) {
+    const int buf = it & 1;
+    unsigned char* st = smem + buf * TC_STAGE;
+    // kernel spectra of this wavevector
+    for (int s = tid; s < CG; s += TC_THREADS) gk[s] = Gt[(int64_t)s * Kh + k];
+    __syncthreads();
+    // W: unit (output channel co, K-group kg of 8 input channels) -> rows 2co, 2co+1
+    for (int u = tid; u < TC_CH * 8; u += TC_THREADS) {
+      const int kg = (u >> 2) & 7, co = (u & 3) + 4 * (u >> 5);
+      float ar[8], ai[8];
+      uint32_t tv[8];
+      *reinterpret_cast<uint4*>(tv) = *reinterpret_cast<const uint4*>(tab + co * TC_CH + kg * 8);
+      *reinterpret_cast<uint4*>(tv + 4) = *reinterpret_cast<const uint4*>(tab + co * TC_CH + kg * 8 + 4);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t t = tv[j];
+        const float s1 = (float)((int)((t >> 10) & 3u) - 1), s2 = (float)((int)((t >> 22) & 3u) - 1);
+        const float2 g1 = gk[t & 1023u], g2 = gk[(t >> 12) & 1023u];
+        ar[j] = s1 * g1.x + s2 * g2.x;
+        ai[j] = s1 * g1.y + s2 * g2.y;
+      }
+      uint4 rh, rl, ih, il;
+      split8(ar, rh, rl);
+      split8(ai, ih, il);
+      unsigned char* Ah = st;
+      unsigned char* Al = st + TC_A_BYTES;
+      *reinterpret_cast<uint4*>(Ah + chunk_off(2 * co, kg)) = rh;
+      *reinterpret_cast<uint4*>(Al + chunk_off(2 * co, kg)) = rl;
+      *reinterpret_cast<uint4*>(Ah + chunk_off(2 * co, 8 + kg)) = neg_bf16(ih);
+      *reinterpret_cast<uint4*>(Al + chunk_off(2 * co, 8 + kg)) = neg_bf16(il);
+      *reinterpret_cast<uint4*>(Ah + chunk_off(2 * co + 1, kg)) = ih;
+      *reinterpret_cast<uint4*>(Al + chunk_off(2 * co + 1, kg)) = il;
+      *reinterpret_cast<uint4*>(Ah + chunk_off(2 * co + 1, 8 + kg)) = rh;
+      *reinterpret_cast<uint4*>(Al + chunk_off(2 * co + 1, 8 + kg)) = rl;
+    }
+    // X: unit (system n, K-group cg of 8 channels) -> row n, K-groups cg (Re) and 8 + cg (Im)
+    for (int u = tid; u < TC_NMAX * 8; u += TC_THREADS) {
+      const int n = (u & 7) + 8 * (u >> 6), cg = (u >> 3) & 7;
+      float xr[8], xi[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int ci = cg * 8 + j;
+        float2 m = make_float2(0.f, 0.f);
+        if (n < nb && ci < C) m = __ldg(Mt + (k * C + ci) * B + b0 + n);
+        xr[j] = m.x;
+        xi[j] = m.y;
+      }
+      uint4 rh, rl, ih, il;
+      split8(xr, rh, rl);
+      split8(xi, ih, il);
+      unsigned char* Xh = st + 2 * TC_A_BYTES;
+      unsigned char* Xl = Xh + TC_B_BYTES;
+      *reinterpret_cast<uint4*>(Xh + chunk_off(n, cg)) = rh;
+      *reinterpret_cast<uint4*>(Xl + chunk_off(n, cg)) = rl;
+      *reinterpret_cast<uint4*>(Xh + chunk_off(n, 8 + cg)) = ih;
+      *reinterpret_cast<uint4*>(Xl + chunk_off(n, 8 + cg)) = il;
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after();
+      const uint32_t a_h = sbase + buf * TC_STAGE, a_l = a_h + TC_A_BYTES;
+      const uint32_t x_h = a_h + 2 * TC_A_BYTES, x_l = x_h + TC_B_BYTES;
+      const uint32_t d = tmem + (uint32_t)(buf * TC_NMAX);
+      const uint32_t As[3] = {a_h, a_h, a_l}, Xs[3] = {x_h, x_l, x_h};
+#pragma unroll
+      for (int sp = 0; sp < 3; ++sp)
+#pragma unroll
+        for (int j = 0; j < TC_K / 16; ++j)
+          mma_bf16(d, make_desc(As[sp] + 256 * j), make_desc(Xs[sp] + 256 * j), idesc, (sp | j) != 0);
+      mma_commit(smem_u32(&bars[buf]));
+    }
+    // the previous wavevector's accumulator, while these MMAs run
+    if (kprev >= 0) {
+      if (!drain(buf ^ 1, kprev, (uint32_t)(((it - 1) >> 1) & 1))) atomicExch(abort_flag, 1);
+    }
+    kprev = k;
+    __syncthreads();
+    if (*abort_flag) {
+      ok = false;
+      break;
+    }
+  }
+  if (ok && kprev >= 0) {
+    if (!drain((it - 1) & 1, kprev, (uint32_t)(((it - 1) >> 1) & 1))) atomicExch(abort_flag, 1);
+  }
+  __syncthreads();
+  if (*abort_flag) {
+    if (tid == 0) set_err(err, ERRBIT_TIMEOUT);
+    // give MMAs still in flight a bounded time to finish before the memory is released
+    if (it >= 1) bar_wait(smem_u32(&bars[(it - 1) & 1]), (uint32_t)(((it - 1) >> 1) & 1));
+  }
+  fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
+}  // namespace
+
+bool m2l_tc_supported(int p) { return p >= 0 && p <= 7; }
+
+// Packed entry table of the real-matrix M2L, padded to 64 x 64 channels.
+std::vector<uint32_t> build_m2l_table_tc(int p) {
+  const int C = (p + 1) * (p + 1);
+  std::vector<M2LEntry> t = build_m2l_table(p);
+  std::vector<uint32_t> out((size_t)TC_CH * TC_CH, (1u << 10) | (1u << 22));  // both signs 0
+  for (int co = 0; co < C; ++co)
+    for (int ci = 0; ci < C; ++ci) {
+      const M2LEntry& e = t[(size_t)co * C + ci];
+      out[(size_t)co * TC_CH + ci] = (uint32_t)e.i1 | ((uint32_t)(e.s1 + 1) << 10) | ((uint32_t)e.i2 << 12) |
+                                     ((uint32_t)(e.s2 + 1) << 22);
+    }
+  return out;
+}
+
+cudaError_t launch_m2l_tc(const void* Mt, const void* Gt, void* Lt, const uint32_t* tab, int p, int B, int64_t Kh,
+                          int num_sms, int* err, cudaStream_t s, int* nl) {
+  if (!m2l_tc_supported(p) || B < 1) return cudaErrorInvalidValue;
+  const int C = (p + 1) * (p + 1), CG = (2 * p + 1) * (2 * p + 1);
+  const int ntiles = (B + TC_NMAX - 1) / TC_NMAX;
+  const int per_tile = (int)std::max<int64_t>(1, std::min<int64_t>(Kh, (num_sms + ntiles - 1) / ntiles));
+  const int64_t kchunk = (Kh + per_tile - 1) / per_tile;
+  const unsigned gx = (unsigned)((Kh + kchunk - 1) / kchunk);
+  cudaError_t e = cudaFuncSetAttribute(m2l_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+  if (e != cudaSuccess) return e;
+  dim3 grid(gx, (unsigned)ntiles);
+  m2l_tc_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>((const float2*)Mt, (const float2*)Gt, (float2*)Lt, tab, C, CG, B,
+                                                  Kh, kchunk, err);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+}  // namespace pmmm

@@ -63,6 +63,8 @@ struct pmmm_plan {
   int64_t* offsets_pinned = nullptr;  // host staging of the offsets
   std::vector<int64_t> offsets_up;    // offsets of the last upload
   int* m2l_tab = nullptr;             // batched M2L entry table, 4 ints per entry
+  uint32_t* m2l_tab_tc = nullptr;     // packed entry table of the tensor-core M2L
+  bool m2l_tc = false;                // batched M2L on the tensor cores (split BF16)
   std::unordered_map<void*, size_t> sizes;
   // CUDA graph of one batched evaluation, and the arguments it was captured for
   cudaGraphExec_t gexec = nullptr;
@@ -155,6 +157,7 @@ void free_all(pmmm_plan* pl) {
   dfree(pl, pl->counter);
   dfree(pl, pl->err);
   dfree(pl, pl->m2l_tab);
+  dfree(pl, pl->m2l_tab_tc);
   dfree(pl, pl->hpos); dfree(pl, pl->hq); dfree(pl, pl->hphi); dfree(pl, pl->hforce);
   if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
   pl->gexec = nullptr;
@@ -221,6 +224,7 @@ int validate(const pmmm_config* c) {
   if (c->p < 0 || c->cutoff < 1) return PMMM_ERR_INVALID_ARG;
   if (!(c->sign == 1.0 || c->sign == -1.0)) return PMMM_ERR_INVALID_ARG;
   if (c->ewald_alpha < 0.0 || !isfinite(c->ewald_alpha) || c->ewald_nmax < 0) return PMMM_ERR_INVALID_ARG;
+  if (c->near_field < PMMM_NEAR_AUTO || c->near_field > PMMM_NEAR_PER_TARGET) return PMMM_ERR_INVALID_ARG;
   if (c->p > PMMM_PMAX || c->cutoff > 2) return PMMM_ERR_UNSUPPORTED;
   for (int a = 0; a < 3; ++a) {
     if (!pow2(c->mesh[a])) return PMMM_ERR_UNSUPPORTED;
@@ -343,6 +347,12 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
   cudaError_t e = cudaSuccess;
   const bool fp64 = pl->fp64;
   const int64_t Ks = pl->d.K, K = Ks * B;  // cells per system, cells of all systems
+  // near field: one thread per target when asked, or (automatic) when the cells
+  // hold fewer than PMMM_NEAR_AUTO_OCCUPANCY particles on average
+  const bool per_target =
+      pp_per_target_applies(fp64, pl->g.c) &&
+      (pl->cfg.near_field == PMMM_NEAR_PER_TARGET ||
+       (pl->cfg.near_field == PMMM_NEAR_AUTO && n < (int64_t)PMMM_NEAR_AUTO_OCCUPANCY * K));
 #define CK(x)                    \
   do {                           \
     e = (x);                     \
@@ -361,7 +371,7 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
     CK(launch_cell_bounds(pl->keys_sorted, n, K, pl->cs, s, &nl));
     CK(launch_gather(pl->far, fp64, pl->vals_sorted, n, pl->part, s, &nl));
     CK(launch_pp_items(pl->cs, K, pl->item_start, pl->item_cell, pl->pair_start, pl->item_chunks, pl->counter,
-                       pl->epart, pp_items_max(K, n), s, &nl));
+                       pl->epart, pp_items_max(K, n), per_target, s, &nl));
     if (!fp64) CK(launch_pair_pack(pl->part, pl->keys_sorted, pl->cs, pl->pair_start, n, pl->src2, s, &nl));
   }
   mark(pl, ST_P2M);
@@ -371,10 +381,22 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
     FftTw tw{pl->twx, pl->twy, pl->twz};
     CK(launch_fft_forward(fp64, pl->M, pl->specM, pl->d, pl->C * B, tw, s, &nl));
     mark(pl, ST_M2L);
-    if (B == 1)
+    const int64_t R = (int64_t)pl->C * B;
+    if (B == 1) {
       CK(launch_m2l(pl->p, fp64, pl->specM, pl->G, pl->specL, pl->d.Kh, s, &nl));
-    else
-      CK(launch_m2l_batched(fp64, pl->specM, pl->G, pl->specL, pl->m2l_tab, pl->p, B, pl->d.Kh, s, &nl));
+    } else if (pl->m2l_tc || m2l_batched_gemm(fp64, pl->p, B)) {
+      // matrix products per wavevector on wavevector-major spectra:
+      // specM -> specL (transposed) -> M2L -> specM -> specL (channel-major)
+      CK(launch_transpose(fp64, pl->specM, pl->specL, R, pl->d.Kh, s, &nl));
+      if (pl->m2l_tc)
+        CK(launch_m2l_tc(pl->specL, pl->G, pl->specM, pl->m2l_tab_tc, pl->p, B, pl->d.Kh, pl->num_sms, pl->err, s,
+                         &nl));
+      else
+        CK(launch_m2l_batched(fp64, pl->specL, pl->G, pl->specM, pl->m2l_tab, pl->p, B, pl->d.Kh, s, &nl));
+      CK(launch_transpose(fp64, pl->specM, pl->specL, pl->d.Kh, R, s, &nl));
+    } else {
+      CK(launch_m2l_systems(pl->p, fp64, pl->specM, pl->G, pl->specL, pl->d.Kh, B, s, &nl));
+    }
     mark(pl, ST_FFT_INV);
     CK(launch_fft_inverse(fp64, pl->specL, pl->L, pl->d, pl->C * B, tw, s, &nl));
   }
@@ -416,8 +438,9 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
     pp.ih2_32 = (float)pp.ih2f;
     pp.sign32 = (float)pp.signf;
     const int64_t mi = pp_items_max(K, n);
-    CK(launch_pp(fp64, pl->part, pl->src2, pl->pair_start, pl->vals_sorted, pl->cs, K, pl->item_start,
-                 pl->item_cell, pl->counter, pl->num_sms, pl->far, pp, phi, force, pl->epart, s, &nl));
+    CK(launch_pp(fp64, pl->part, pl->src2, pl->pair_start, pl->vals_sorted, pl->keys_sorted, n, per_target, pl->cs, K,
+                 pl->item_start, pl->item_cell, pl->counter, pl->num_sms, pl->far, pp, phi, force, pl->epart, s,
+                 &nl));
     mark(pl, ST_REDUCE);
     if (B == 1)
       CK(launch_energy(pl->epart, mi, pl->partial + 256 * 5, pl->energy, s, &nl));
@@ -454,6 +477,17 @@ int upload_offsets(pmmm_plan* pl, int B, const int64_t* off, int64_t* n) {
       return map_cuda(e);
     }
     pl->m2l_tab = (int*)v;
+  }
+  if (pl->m2l_tc && !pl->m2l_tab_tc) {
+    std::vector<uint32_t> t = build_m2l_table_tc(pl->p);
+    void* v = nullptr;
+    cudaError_t e = dalloc(pl, &v, sizeof(uint32_t) * t.size());
+    if (e == cudaSuccess) e = cudaMemcpy(v, t.data(), sizeof(uint32_t) * t.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      dfree(pl, v);
+      return map_cuda(e);
+    }
+    pl->m2l_tab_tc = (uint32_t*)v;
   }
   if (pl->offsets_up.size() == (size_t)B + 1 && memcmp(pl->offsets_up.data(), off, sizeof(int64_t) * (B + 1)) == 0)
     return PMMM_OK;
@@ -570,6 +604,7 @@ int pmmm_plan_create(const pmmm_config* cfg, void* stream, pmmm_plan** out) {
   pl->C = (cfg->p + 1) * (cfg->p + 1);
   pl->CG = (2 * cfg->p + 1) * (2 * cfg->p + 1);
   pl->fp64 = cfg->precision == PMMM_FP64;
+  pl->m2l_tc = cfg->precision == PMMM_FP32_SPLITBF16_M2L && m2l_tc_supported(cfg->p);
   pl->tsize = pl->fp64 ? sizeof(double) : sizeof(float);
   const bool per = cfg->boundary == PMMM_PERIODIC;
   Dims& d = pl->d;

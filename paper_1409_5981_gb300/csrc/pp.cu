@@ -71,10 +71,11 @@ __global__ void pair_pack_kernel(const float4* __restrict__ part, const uint32_t
 }
 
 __global__ void item_fill_kernel(const uint32_t* __restrict__ item_start, int64_t K, uint32_t* __restrict__ item_cell,
-                                 double* __restrict__ epart, int64_t max_items) {
+                                 double* __restrict__ epart, int64_t max_items, int zero_all) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // energy partials of unused item slots are zero
-  for (int64_t i = (int64_t)item_start[K] + c; i < max_items; i += (int64_t)gridDim.x * blockDim.x)
+  // energy partials of unused item slots are zero (of every slot when the
+  // near-field kernel accumulates into them)
+  for (int64_t i = (zero_all ? 0 : (int64_t)item_start[K]) + c; i < max_items; i += (int64_t)gridDim.x * blockDim.x)
     epart[4 * i] = epart[4 * i + 1] = epart[4 * i + 2] = epart[4 * i + 3] = 0.0;
   if (c >= K) return;
   for (uint32_t it = item_start[c]; it < item_start[c + 1]; ++it) item_cell[it] = (uint32_t)c;
@@ -492,6 +493,126 @@ __global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel_f32
   }
 }
 
+// FP32 near field (c = 1) with one thread per target: for sparsely filled cells,
+// where the per-item set-up of the cell-item kernels costs more than the
+// interactions.  Thread i takes sorted target i; it walks the 9 neighbour rows
+// (dy, dz) and in each row the pairs of the cells x-1, x, x+1 of the pair layout
+// (sources of neighbouring targets coincide, so loads are served by L1).  Energy
+// and net-force terms are reduced per work item: a segmented warp scan over
+// lanes of equal item, one store per item that lies inside the warp, and two
+// double atomics (commutative, so deterministic) on a zeroed slot for an item
+// split between two warps.
+constexpr int PPS_THREADS = 256;
+
+__global__ void __launch_bounds__(PPS_THREADS, 4) pp_target_kernel(
+    const float4* __restrict__ P, const ulonglong2* __restrict__ S2, const uint32_t* __restrict__ pair_start,
+    const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, const int* __restrict__ cs,
+    const uint32_t* __restrict__ item_start, int64_t n, const float4* __restrict__ far, PPParams pp,
+    float* __restrict__ phi, float* __restrict__ force, double* __restrict__ epart) {
+  const int64_t i = (int64_t)blockIdx.x * PPS_THREADS + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t wbase = i - lane;
+  float e_t = 0.f, f_t0 = 0.f, f_t1 = 0.f, f_t2 = 0.f;
+  uint32_t item = 0xffffffffu;
+  int64_t tb = 0, te = 0;
+  if (i < n) {
+    const float4 xi = P[i];
+    const int cell = (int)keys[i];
+    const int c0 = cs[cell], c1 = cs[cell + 1];
+    const int chunk = (int)((i - c0) / CHUNK);
+    item = item_start[cell] + (uint32_t)chunk;
+    tb = c0 + (int64_t)chunk * CHUNK;
+    te = min(tb + CHUNK, (int64_t)c1);
+    const int nx = pp.n[0], ny = pp.n[1], nz = pp.n[2];
+    const int sbase = cell - cell % pp.ksys, lc = cell - sbase;
+    const int ix = lc % nx, iy = (lc / nx) % ny, iz = lc / (nx * ny);
+    const float csx = pp.cs32[0], csy = pp.cs32[1], csz = pp.cs32[2];
+    f2 pot = pk2(0.f, 0.f), gx = pot, gy = pot, gz = pot;
+    for (int dz = -1; dz <= 1; ++dz) {
+      int jz = iz + dz;
+      if (jz < 0 || jz >= nz) {
+        if (!pp.periodic) continue;
+        jz += (jz < 0) ? nz : -nz;
+      }
+      const float tzs = xi.z - (float)dz * csz;
+      const f2 tz = pk2(tzs, tzs);
+      for (int dy = -1; dy <= 1; ++dy) {
+        int jy = iy + dy;
+        if (jy < 0 || jy >= ny) {
+          if (!pp.periodic) continue;
+          jy += (jy < 0) ? ny : -ny;
+        }
+        const float tys = xi.y - (float)dy * csy;
+        const f2 ty = pk2(tys, tys);
+        const int row = sbase + nx * (jy + ny * jz);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          int jx = ix + d - 1;
+          if (jx < 0 || jx >= nx) {
+            if (!pp.periodic) continue;
+            jx += (jx < 0) ? nx : -nx;
+          }
+          const int pb = (int)__ldg(pair_start + row + jx), pe = (int)__ldg(pair_start + row + jx + 1);
+          const float txs = xi.x - (float)(d - 1) * csx;
+          const f2 tx = pk2(txs, txs);
+#pragma unroll 1
+          for (int pr = pb; pr < pe; ++pr) pp_pair2<true>(S2[2 * pr], S2[2 * pr + 1], tx, ty, tz, pot, gx, gy, gz);
+        }
+      }
+    }
+    float pa, pbv, xa, xb, ya, yb, za, zb;
+    up2(pot, pa, pbv);
+    up2(gx, xa, xb);
+    up2(gy, ya, yb);
+    up2(gz, za, zb);
+    const float ps = pa + pbv, gxs = -(xa + xb), gys = -(ya + yb), gzs = -(za + zb);
+    const float4 fr = far[i];
+    const float ih = pp.ih32, ih2 = pp.ih2_32, sg = pp.sign32;
+    const float pt = sg * (fr.x + ps * ih);
+    const float g0 = sg * (fr.y + gxs * ih2), g1 = sg * (fr.z + gys * ih2), g2 = sg * (fr.w + gzs * ih2);
+    const uint32_t o = vals[i];
+    const float q = xi.w;
+    if (phi) phi[o] = pt;
+    if (force) {
+      force[3 * (int64_t)o + 0] = -q * g0;
+      force[3 * (int64_t)o + 1] = -q * g1;
+      force[3 * (int64_t)o + 2] = -q * g2;
+    }
+    e_t = 0.5f * q * pt;
+    f_t0 = -q * g0;
+    f_t1 = -q * g1;
+    f_t2 = -q * g2;
+  }
+  // segmented inclusive scan over runs of lanes with the same item
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float ue = __shfl_up_sync(0xffffffffu, e_t, o), u0 = __shfl_up_sync(0xffffffffu, f_t0, o);
+    const float u1 = __shfl_up_sync(0xffffffffu, f_t1, o), u2 = __shfl_up_sync(0xffffffffu, f_t2, o);
+    const uint32_t uit = __shfl_up_sync(0xffffffffu, item, o);
+    if (lane >= o && uit == item) {
+      e_t += ue;
+      f_t0 += u0;
+      f_t1 += u1;
+      f_t2 += u2;
+    }
+  }
+  const uint32_t next = __shfl_down_sync(0xffffffffu, item, 1);
+  if (i < n && (lane == 31 || next != item)) {
+    double* ep = epart + 4 * (int64_t)item;
+    if (tb >= wbase && te <= wbase + 32) {
+      ep[0] = (double)e_t;
+      ep[1] = (double)f_t0;
+      ep[2] = (double)f_t1;
+      ep[3] = (double)f_t2;
+    } else {
+      atomicAdd(ep + 0, (double)e_t);
+      atomicAdd(ep + 1, (double)f_t0);
+      atomicAdd(ep + 2, (double)f_t1);
+      atomicAdd(ep + 3, (double)f_t2);
+    }
+  }
+}
+
 }  // namespace
 
 int64_t pp_items_max(int64_t K, int64_t n) { return K + (n + CHUNK - 1) / CHUNK + 1; }
@@ -500,13 +621,14 @@ int64_t pp_pairs_max(int64_t K, int64_t n) { return (n + K) / 2 + 1; }
 
 cudaError_t launch_pp_items(const int* cell_start, int64_t K, uint32_t* item_start, uint32_t* item_cell,
                             uint32_t* pair_start, uint32_t* chunks, unsigned int* counter, double* epart,
-                            int64_t max_items, cudaStream_t s, int* nl) {
+                            int64_t max_items, bool zero_all, cudaStream_t s, int* nl) {
   item_count_kernel<<<(unsigned)((K + 1 + 255) / 256), 256, 0, s>>>(cell_start, K, item_start, pair_start, counter);
   ++*nl;
   cudaError_t e = launch_exclusive_scan(item_start, K + 1, chunks, s, nl);
   if (e == cudaSuccess && pair_start) e = launch_exclusive_scan(pair_start, K + 1, chunks, s, nl);
   if (e != cudaSuccess) return e;
-  item_fill_kernel<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(item_start, K, item_cell, epart, max_items);
+  item_fill_kernel<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(item_start, K, item_cell, epart, max_items,
+                                                               zero_all ? 1 : 0);
   ++*nl;
   return cudaGetLastError();
 }
@@ -520,13 +642,22 @@ cudaError_t launch_pair_pack(const void* part, const uint32_t* keys, const int* 
   return cudaGetLastError();
 }
 
+bool pp_per_target_applies(bool fp64, int c) { return !fp64 && c <= 1; }
+
 cudaError_t launch_pp(bool fp64, const void* part, const void* src2, const uint32_t* pair_start, const uint32_t* vals,
-                      const int* cell_start, int64_t K, const uint32_t* item_start, const uint32_t* item_cell,
-                      unsigned int* counter, int num_sms, const void* far, PPParams pp, void* phi, void* force,
-                      double* epart, cudaStream_t s, int* nl) {
+                      const uint32_t* keys, int64_t n, bool per_target, const int* cell_start, int64_t K,
+                      const uint32_t* item_start, const uint32_t* item_cell, unsigned int* counter, int num_sms,
+                      const void* far, PPParams pp, void* phi, void* force, double* epart, cudaStream_t s, int* nl) {
   // persistent launch: PP_BLOCKS_PER_SM resident blocks of PP_WARPS warps per SM
   const unsigned blocks = (unsigned)(PP_BLOCKS_PER_SM * (num_sms > 0 ? num_sms : 1));
-  if (!fp64 && pp.c <= 1 && src2 != nullptr) {
+  if (per_target && pp_per_target_applies(fp64, pp.c) && src2 != nullptr) {
+    if (n > 0)
+      pp_target_kernel<<<(unsigned)((n + PPS_THREADS - 1) / PPS_THREADS), PPS_THREADS, 0, s>>>(
+          (const float4*)part, (const ulonglong2*)src2, pair_start, keys, vals, cell_start, item_start, n,
+          (const float4*)far, pp, (float*)phi, (float*)force, epart);
+    else
+      return cudaSuccess;
+  } else if (!fp64 && pp.c <= 1 && src2 != nullptr) {
     pp_kernel_f32x2<<<blocks, PP_WARPS * 32, 0, s>>>((const float*)part, (const float*)src2, pair_start, vals,
                                                      cell_start, K, item_start, item_cell, counter, (const float*)far,
                                                      pp, (float*)phi, (float*)force, epart);

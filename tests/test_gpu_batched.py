@@ -280,3 +280,37 @@ def test_batched_graph_replay(pk):
     ref.close()
     assert np.array_equal(phi.double().cpu().numpy(), rphi3) and np.array_equal(e3, re3)
     plan.close()
+
+
+# relative RMS force / potential error bound of the split-BF16 tensor-core M2L against
+# the FP32 path: each M2L product carries <= 3 * 2^-18 relative error (hi + lo
+# representation of both operands, lo * lo dropped), i.e. ~1.1e-5 per term; the
+# far field is a fraction of each force, so the force error stays below 2e-5
+SPLITBF16_TOL = 2e-5
+
+
+@pytest.mark.parametrize("p", [2, 5, 7])
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_batched_splitbf16_tensor_core_m2l(pk, p, boundary):
+    """The batched M2L on the tensor cores (precision FP32_SPLITBF16_M2L, p <= 7):
+    locals of every system against the FP32 batched path, and forces against the
+    FP64 path, over two system tiles (70 systems: 64 + a ragged 6)."""
+    import torch
+    sizes = list(synth.batched_sizes(70, synth.seed(4, 8 + boundary), lo_exp=7, hi_exp=10))
+    sizes[3] = 0
+    res = {}
+    for prec in (pk.FP32_SPLITBF16_M2L, pk.FP32, pk.FP64):
+        cfg = pk.Config(mesh=(8, 8, 8), p=p, boundary=boundary, precision=prec, ewald_nmax=4)
+        pos, q, off = _systems(pk, cfg if prec != pk.FP64 else pk.Config(precision=pk.FP32), sizes, 54 + boundary)
+        plan, phi, force, e = _batched(pk, cfg, pos, q, off)
+        res[prec] = (phi, force, e, plan.export(pk.EXPORT_LOCAL))
+        plan.close()
+    L_tc, L_32 = res[pk.FP32_SPLITBF16_M2L][3], res[pk.FP32][3]
+    eL = float(np.abs(L_tc - L_32).max() / np.abs(L_32).max())
+    ef = _rel(res[pk.FP32_SPLITBF16_M2L][1], res[pk.FP64][1])
+    ef32 = _rel(res[pk.FP32][1], res[pk.FP64][1])
+    ep = _rel(res[pk.FP32_SPLITBF16_M2L][0], res[pk.FP64][0])
+    print(f"split-BF16 M2L p={p} bnd={boundary}: locals vs FP32 {eL:.2e}; force vs FP64 {ef:.2e} "
+          f"(FP32 path {ef32:.2e}), phi {ep:.2e}")
+    assert eL < 1e-4
+    assert ef < SPLITBF16_TOL and ep < SPLITBF16_TOL
