@@ -6,6 +6,7 @@
 //   L~(k)[C x B] = A~(k)[C x C] M~(k)[C x B]
 // (Sec. 2.1 convolution theorem with the real-matrix form of App. A.8), with
 // A~(k) assembled once per k from the (2p+1)^2 kernel spectra.
+#include <algorithm>
 #include <vector>
 
 #include "binning.cuh"
@@ -121,26 +122,48 @@ __global__ void __launch_bounds__(256) m2l_batched_kernel(const cpx<T>* __restri
   }
 }
 
-// Per-system periodic corrections (App. B.3): block s reduces the five per-cell
-// FP64 sums of its cells; corr[16 s + ...] as in the single-system kernel.
-__global__ void __launch_bounds__(256) corrections_batched_kernel(const double* __restrict__ cellsum, int64_t Ktot,
-                                                                  int64_t Ksys, double hs, double V,
-                                                                  double* __restrict__ corr) {
-  __shared__ double sh[5][256];
-  const int s = blockIdx.x;
-  double acc[5] = {0, 0, 0, 0, 0};
-  for (int64_t c = (int64_t)s * Ksys + threadIdx.x; c < (int64_t)(s + 1) * Ksys; c += blockDim.x)
+// Per-system periodic corrections (App. B.3) in two fixed-order levels: block
+// (chunk, s) sums the five per-cell FP64 quantities of RB_CHUNK cells of system
+// s; one block per system then sums its chunks and writes corr[16 s + ...] as in
+// the single-system kernel.
+constexpr int RB_CHUNK = 4096;
+
+template <int NQ>
+__device__ __forceinline__ void block_sum(double (&acc)[NQ], double (*sh)[256]) {
 #pragma unroll
-    for (int qn = 0; qn < 5; ++qn) acc[qn] += cellsum[qn * Ktot + c];
-#pragma unroll
-  for (int qn = 0; qn < 5; ++qn) sh[qn][threadIdx.x] = acc[qn];
+  for (int qn = 0; qn < NQ; ++qn) sh[qn][threadIdx.x] = acc[qn];
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w)
 #pragma unroll
-      for (int qn = 0; qn < 5; ++qn) sh[qn][threadIdx.x] += sh[qn][threadIdx.x + w];
+      for (int qn = 0; qn < NQ; ++qn) sh[qn][threadIdx.x] += sh[qn][threadIdx.x + w];
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(256) cellsum_partial_kernel(const double* __restrict__ cellsum, int64_t Ktot,
+                                                              int64_t Ksys, int nchunk, double* __restrict__ part) {
+  __shared__ double sh[5][256];
+  const int s = blockIdx.y, ch = blockIdx.x;
+  const int64_t lo = (int64_t)s * Ksys + (int64_t)ch * RB_CHUNK;
+  const int64_t hi = min(lo + RB_CHUNK, (int64_t)(s + 1) * Ksys);
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int64_t c = lo + threadIdx.x; c < hi; c += blockDim.x)
+#pragma unroll
+    for (int qn = 0; qn < 5; ++qn) acc[qn] += cellsum[qn * Ktot + c];
+  block_sum<5>(acc, sh);
+  if (threadIdx.x < 5) part[((int64_t)s * nchunk + ch) * 5 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(256) corrections_batched_kernel(const double* __restrict__ part, int nchunk,
+                                                                  double hs, double V, double* __restrict__ corr) {
+  __shared__ double sh[5][256];
+  const int s = blockIdx.x;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int ch = threadIdx.x; ch < nchunk; ch += blockDim.x)
+#pragma unroll
+    for (int qn = 0; qn < 5; ++qn) acc[qn] += part[((int64_t)s * nchunk + ch) * 5 + qn];
+  block_sum<5>(acc, sh);
   if (threadIdx.x == 0) {
     const double f = 2.0 * kPi / (3.0 * V);
     double* c = corr + 16 * s;
@@ -153,32 +176,37 @@ __global__ void __launch_bounds__(256) corrections_batched_kernel(const double* 
   }
 }
 
-// Per-system energy and net force: block s sums the near-field work items of
-// its cells (items are numbered in cell order).
-__global__ void __launch_bounds__(256) energy_batched_kernel(const double* __restrict__ epart,
+// Per-system energy and net force from the near-field work items (numbered in
+// cell order): block (chunk, s) sums RB_CHUNK items of system s, then one block
+// per system sums its chunks.  The item range of system s is
+// item_start[s Ksys] ... item_start[(s+1) Ksys].
+__global__ void __launch_bounds__(256) energy_partial_kernel(const double* __restrict__ epart,
                                                              const uint32_t* __restrict__ item_start, int64_t Ksys,
-                                                             double* __restrict__ energies) {
+                                                             int nchunk, double* __restrict__ part) {
   __shared__ double sh[4][256];
-  const int s = blockIdx.x;
-  const int64_t lo = item_start[(int64_t)s * Ksys], hi = item_start[(int64_t)(s + 1) * Ksys];
+  const int s = blockIdx.y, ch = blockIdx.x;
+  const int64_t b = item_start[(int64_t)s * Ksys], e = item_start[(int64_t)(s + 1) * Ksys];
   double acc[4] = {0, 0, 0, 0};
+  const int64_t lo = b + (int64_t)ch * RB_CHUNK, hi = min(lo + RB_CHUNK, e);
   for (int64_t it = lo + threadIdx.x; it < hi; it += blockDim.x)
 #pragma unroll
     for (int qn = 0; qn < 4; ++qn) acc[qn] += epart[4 * it + qn];
+  block_sum<4>(acc, sh);
+  if (threadIdx.x < 4) part[((int64_t)s * nchunk + ch) * 4 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(256) energy_batched_kernel(const double* __restrict__ part, int nchunk,
+                                                             double* __restrict__ energies) {
+  __shared__ double sh[4][256];
+  const int s = blockIdx.x;
+  double acc[4] = {0, 0, 0, 0};
+  for (int ch = threadIdx.x; ch < nchunk; ch += blockDim.x)
 #pragma unroll
-  for (int qn = 0; qn < 4; ++qn) sh[qn][threadIdx.x] = acc[qn];
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-#pragma unroll
-      for (int qn = 0; qn < 4; ++qn) sh[qn][threadIdx.x] += sh[qn][threadIdx.x + w];
-    __syncthreads();
-  }
+    for (int qn = 0; qn < 4; ++qn) acc[qn] += part[((int64_t)s * nchunk + ch) * 4 + qn];
+  block_sum<4>(acc, sh);
   if (threadIdx.x < 4) energies[4 * s + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// out[k][r] = in[r][k] for an R x Kh matrix of complex values; 32 x 32 tiles
-// through shared memory so that both the reads and the writes are coalesced.
 template <typename T>
 __global__ void __launch_bounds__(256) transpose_kernel(const cpx<T>* __restrict__ in, cpx<T>* __restrict__ out,
                                                         int64_t R, int64_t Kh) {
@@ -295,17 +323,26 @@ cudaError_t launch_m2l_batched(bool fp64, const void* Mt, const void* Gt, void* 
               : m2l_batched_run<float, 1>(Mt, Gt, Lt, t4, C, CG, B, BT, Kh, s);
 }
 
+int reduce_batched_chunks(int64_t Ksys, int64_t max_items_per_sys) {
+  const int64_t m = std::max<int64_t>(Ksys, max_items_per_sys);
+  return (int)std::max<int64_t>(1, (m + RB_CHUNK - 1) / RB_CHUNK);
+}
+
 cudaError_t launch_corrections_batched(const double* cellsum, int64_t Ktot, int64_t Ksys, int nsys, double hs, double V,
-                                       double* corr, cudaStream_t s, int* nl) {
-  corrections_batched_kernel<<<nsys, 256, 0, s>>>(cellsum, Ktot, Ksys, hs, V, corr);
-  ++*nl;
+                                       double* partial, double* corr, cudaStream_t s, int* nl) {
+  const int nchunk = (int)((Ksys + RB_CHUNK - 1) / RB_CHUNK);
+  cellsum_partial_kernel<<<dim3((unsigned)nchunk, (unsigned)nsys), 256, 0, s>>>(cellsum, Ktot, Ksys, nchunk, partial);
+  corrections_batched_kernel<<<nsys, 256, 0, s>>>(partial, nchunk, hs, V, corr);
+  *nl += 2;
   return cudaGetLastError();
 }
 
-cudaError_t launch_energy_batched(const double* epart, const uint32_t* item_start, int64_t Ksys, int nsys,
-                                  double* energies, cudaStream_t s, int* nl) {
-  energy_batched_kernel<<<nsys, 256, 0, s>>>(epart, item_start, Ksys, energies);
-  ++*nl;
+cudaError_t launch_energy_batched(const double* epart, const uint32_t* item_start, int64_t Ksys, int nsys, int nchunk,
+                                  double* partial, double* energies, cudaStream_t s, int* nl) {
+  energy_partial_kernel<<<dim3((unsigned)nchunk, (unsigned)nsys), 256, 0, s>>>(epart, item_start, Ksys, nchunk,
+                                                                               partial);
+  energy_batched_kernel<<<nsys, 256, 0, s>>>(partial, nchunk, energies);
+  *nl += 2;
   return cudaGetLastError();
 }
 

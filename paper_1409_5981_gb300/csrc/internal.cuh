@@ -74,8 +74,9 @@ int64_t scan_chunk_count(int64_t n);
 cudaError_t launch_exclusive_scan(uint32_t* data, int64_t n, uint32_t* chunks, cudaStream_t s, int* nlaunch);
 
 // ---------------------------------------------------------------- p2m_l2p.cu
+// sparse (FP32, p <= 8): one thread per cell, crowded cells taken by the whole warp
 cudaError_t launch_p2m(int p, bool fp64, const void* part, const int* cell_start, int64_t K, void* M,
-                       double* cellq, double* celld, cudaStream_t s, int* nlaunch);
+                       double* cellq, double* celld, bool sparse, cudaStream_t s, int* nlaunch);
 struct CorrParams {
   double hs, alpha, V;
   double ih, ih2;      // 1 / hs, 1 / hs^2
@@ -101,6 +102,13 @@ cudaError_t launch_fft_forward(bool fp64, const void* in, void* spec, const Dims
 cudaError_t launch_fft_inverse(bool fp64, void* spec, void* out, const Dims& d, int C, const FftTw& tw,
                                cudaStream_t s, int* nlaunch);
 cudaError_t launch_twiddles(bool fp64, int L, void* tw, cudaStream_t s);
+// One CTA per channel, whole 3-D transform in shared memory (fft_fused.cu): FP32,
+// transform lengths <= 32, the physical planes' half spectrum <= 200 KB.
+bool fft_fused_applies(bool fp64, const Dims& d);
+cudaError_t launch_fft_fused_forward(const void* in, void* spec, const Dims& d, int C, const FftTw& tw, cudaStream_t s,
+                                     int* nlaunch);
+cudaError_t launch_fft_fused_inverse(const void* spec, void* out, const Dims& d, int C, const FftTw& tw, cudaStream_t s,
+                                     int* nlaunch);
 
 // ---------------------------------------------------------------- m2l.cu
 cudaError_t launch_m2l(int p, bool fp64, const void* Mt, const void* Gt, void* Lt, int64_t Kh, cudaStream_t s,
@@ -133,12 +141,15 @@ bool m2l_tc_supported(int p);
 std::vector<uint32_t> build_m2l_table_tc(int p);
 cudaError_t launch_m2l_tc(const void* Mt, const void* Gt, void* Lt, const uint32_t* tab, int p, int nsys, int64_t Kh,
                           int num_sms, int* err, cudaStream_t s, int* nlaunch);
+// Chunks per system of the two-level batched reductions (partial: 5 * nsys * chunks doubles).
+int reduce_batched_chunks(int64_t Ksys, int64_t max_items_per_sys);
 // corr[16 s + ...] of every system (the single-system layout of launch_corrections)
 cudaError_t launch_corrections_batched(const double* cellsum, int64_t Ktot, int64_t Ksys, int nsys, double hs,
-                                       double V, double* corr, cudaStream_t s, int* nlaunch);
-// energies[4 s + ...] = energy and net force of system s from the near-field partials
-cudaError_t launch_energy_batched(const double* epart, const uint32_t* item_start, int64_t Ksys, int nsys,
-                                  double* energies, cudaStream_t s, int* nlaunch);
+                                       double V, double* partial, double* corr, cudaStream_t s, int* nlaunch);
+// energies[4 s + ...] = energy and net force of system s from the near-field partials;
+// nchunk >= ceil(items of any system / 4096)
+cudaError_t launch_energy_batched(const double* epart, const uint32_t* item_start, int64_t Ksys, int nsys, int nchunk,
+                                  double* partial, double* energies, cudaStream_t s, int* nlaunch);
 
 // ---------------------------------------------------------------- green.cu
 // Builds the real-space Green components G[s][Kt] (FP64, units of hs), s < (2p+1)^2.

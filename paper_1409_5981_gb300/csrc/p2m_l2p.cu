@@ -79,6 +79,84 @@ __global__ void __launch_bounds__(256) p2m_kernel(const T* __restrict__ part, co
   }
 }
 
+// Sparsely filled cells (FP32, p <= 8): one thread per cell accumulates its particles
+// and writes its channels with coalesced stores (consecutive threads hold
+// consecutive cells).  Cells with more than P2M_BIG particles are taken by the
+// whole warp instead (lanes over particles, xor-butterfly sum), so that a
+// crowded cell does not hold up the 31 other lanes.
+constexpr int P2M_BIG = 16;
+
+template <int P, typename T>
+__global__ void __launch_bounds__(256) p2m_cell_kernel(const T* __restrict__ part, const int* __restrict__ cs,
+                                                       int64_t K, T* __restrict__ M, double* __restrict__ cellsum) {
+  constexpr int C = (P + 1) * (P + 1);
+  const int lane = threadIdx.x & 31;
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int beg = 0, end = 0;
+  if (cell < K) {
+    beg = cs[cell];
+    end = cs[cell + 1];
+  }
+  const bool big = end - beg > P2M_BIG;
+  T acc[C];
+  T sq = 0, sx = 0, sy = 0, sz = 0, sr = 0;
+  auto accumulate = [&](int i) {
+    const typename V4<T>::type r = reinterpret_cast<const typename V4<T>::type*>(part)[i];
+    T R[C];
+    regular_real<P, T>(-r.x, -r.y, -r.z, R);
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = fma(r.w, R[c], acc[c]);
+    sq += r.w;
+    sx = fma(r.w, r.x, sx);
+    sy = fma(r.w, r.y, sy);
+    sz = fma(r.w, r.z, sz);
+    sr = fma(r.w, r.x * r.x + r.y * r.y + r.z * r.z, sr);
+  };
+#pragma unroll
+  for (int c = 0; c < C; ++c) acc[c] = T(0);
+  if (cell < K && !big) {
+    for (int i = beg; i < end; ++i) accumulate(i);
+#pragma unroll
+    for (int c = 0; c < C; ++c) M[(int64_t)c * K + cell] = acc[c];
+    cellsum[cell] = (double)sq;
+    cellsum[K + cell] = (double)sx;
+    cellsum[2 * K + cell] = (double)sy;
+    cellsum[3 * K + cell] = (double)sz;
+    cellsum[4 * K + cell] = (double)sr;
+  }
+  unsigned todo = __ballot_sync(0xffffffffu, cell < K && big);
+  while (todo) {
+    const int src = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const int64_t bc = __shfl_sync(0xffffffffu, cell, src);
+    const int bb = __shfl_sync(0xffffffffu, beg, src), be = __shfl_sync(0xffffffffu, end, src);
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = T(0);
+    sq = sx = sy = sz = sr = T(0);
+    for (int i = bb + lane; i < be; i += 32) accumulate(i);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+      sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      sz += __shfl_xor_sync(0xffffffffu, sz, o);
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+      if ((c & 31) == lane) M[(int64_t)c * K + bc] = acc[c];
+    if (lane == 0) {
+      cellsum[bc] = (double)sq;
+      cellsum[K + bc] = (double)sx;
+      cellsum[2 * K + bc] = (double)sy;
+      cellsum[3 * K + bc] = (double)sz;
+      cellsum[4 * K + bc] = (double)sr;
+    }
+  }
+}
+
 // One thread per sorted particle.  Far-field potential and gradient in
 // physical units, with the periodic corrections of App. B.3:
 //   phi  += c0 + c1 . r_rel + qfac (|r_rel|^2 - 3/(2 alpha^2)) - 2 alpha/sqrt(pi) Q_cell
@@ -127,8 +205,16 @@ __global__ void __launch_bounds__(128) l2p_kernel(const T* __restrict__ part, co
 }
 
 template <int P, typename T>
-cudaError_t p2m_run(const void* part, const int* cs, int64_t K, void* M, double* cq, double* cd, cudaStream_t s) {
+cudaError_t p2m_run(const void* part, const int* cs, int64_t K, void* M, double* cq, double* cd, bool sparse,
+                    cudaStream_t s) {
   (void)cd;  // the per-cell sums are laid out [5][K] starting at cq
+  // one thread per cell keeps its (p+1)^2 sums in registers: FP32 and p <= 8 only
+  if constexpr (sizeof(T) == 4 && P <= 8) {
+    if (sparse) {
+      p2m_cell_kernel<P, T><<<(unsigned)((K + 255) / 256), 256, 0, s>>>((const T*)part, cs, K, (T*)M, cq);
+      return cudaGetLastError();
+    }
+  }
   const int blocks = (int)((K + P2M_CPB - 1) / P2M_CPB);
   p2m_kernel<P, T><<<blocks, 256, 0, s>>>((const T*)part, cs, K, (T*)M, cq);
   return cudaGetLastError();
@@ -145,10 +231,11 @@ cudaError_t l2p_run(const void* part, const uint32_t* keys, int64_t n, const voi
 
 template <int P>
 cudaError_t p2m_dispatch(int p, bool fp64, const void* part, const int* cs, int64_t K, void* M, double* cq,
-                         double* cd, cudaStream_t s) {
+                         double* cd, bool sparse, cudaStream_t s) {
   if (p == P)
-    return fp64 ? p2m_run<P, double>(part, cs, K, M, cq, cd, s) : p2m_run<P, float>(part, cs, K, M, cq, cd, s);
-  if constexpr (P < PMMM_PMAX) return p2m_dispatch<P + 1>(p, fp64, part, cs, K, M, cq, cd, s);
+    return fp64 ? p2m_run<P, double>(part, cs, K, M, cq, cd, sparse, s)
+                : p2m_run<P, float>(part, cs, K, M, cq, cd, sparse, s);
+  if constexpr (P < PMMM_PMAX) return p2m_dispatch<P + 1>(p, fp64, part, cs, K, M, cq, cd, sparse, s);
   return cudaErrorInvalidValue;
 }
 
@@ -165,9 +252,9 @@ cudaError_t l2p_dispatch(int p, bool fp64, const void* part, const uint32_t* key
 }  // namespace
 
 cudaError_t launch_p2m(int p, bool fp64, const void* part, const int* cell_start, int64_t K, void* M, double* cellq,
-                       double* celld, cudaStream_t s, int* nl) {
+                       double* celld, bool sparse, cudaStream_t s, int* nl) {
   ++*nl;
-  return p2m_dispatch<0>(p, fp64, part, cell_start, K, M, cellq, celld, s);
+  return p2m_dispatch<0>(p, fp64, part, cell_start, K, M, cellq, celld, sparse, s);
 }
 
 cudaError_t launch_l2p(int p, bool fp64, const void* part, const uint32_t* keys, int64_t n, const void* L, int64_t K,

@@ -44,7 +44,9 @@ struct pmmm_plan {
   double* cellsum = nullptr;  // [5][K]: sum q, sum q u_x, sum q u_y, sum q u_z, sum q |u|^2
   int* cs = nullptr;          // [K+1]
   double* corr = nullptr;     // [16]
-  double* partial = nullptr;  // [256 * 8]
+  double* partial = nullptr;  // [256 * 16]
+  double* bpartial = nullptr;  // per-system reduction chunks: [5][bcap][bchunks]
+  int bchunks = 0;
   double* epart = nullptr;    // [max items][4]
   uint32_t* item_start = nullptr;  // [K+1] near-field work items per cell (scanned)
   uint32_t* item_chunks = nullptr; // scan scratch
@@ -126,6 +128,8 @@ void free_particles(pmmm_plan* pl) {
   dfree(pl, pl->item_cell);
   dfree(pl, pl->src2);
   dfree(pl, pl->epart);
+  dfree(pl, pl->bpartial);
+  pl->bchunks = 0;
   pl->max_items = 0;
   pl->cap = 0;
 }
@@ -271,6 +275,13 @@ int ensure_particles(pmmm_plan* pl, int64_t n) {
   if (e == cudaSuccess) e = dalloc(pl, &v, sizeof(double) * 4 * (size_t)mi);
   if (e == cudaSuccess) pl->epart = (double*)v;
   if (e == cudaSuccess && !pl->fp64) e = dalloc(pl, &pl->src2, 32 * (size_t)pp_pairs_max(Kb, cap));
+  // items of one system: at most its cells + cap / 32 + 1
+  const int bch = reduce_batched_chunks(pl->d.K, pp_items_max(pl->d.K, cap));
+  if (e == cudaSuccess) e = dalloc(pl, &v, sizeof(double) * 5 * (size_t)pl->bcap * bch);
+  if (e == cudaSuccess) {
+    pl->bpartial = (double*)v;
+    pl->bchunks = bch;
+  }
   if (e != cudaSuccess) {
     free_particles(pl);
     return map_cuda(e);
@@ -349,10 +360,10 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
   const int64_t Ks = pl->d.K, K = Ks * B;  // cells per system, cells of all systems
   // near field: one thread per target when asked, or (automatic) when the cells
   // hold fewer than PMMM_NEAR_AUTO_OCCUPANCY particles on average
-  const bool per_target =
-      pp_per_target_applies(fp64, pl->g.c) &&
-      (pl->cfg.near_field == PMMM_NEAR_PER_TARGET ||
-       (pl->cfg.near_field == PMMM_NEAR_AUTO && n < (int64_t)PMMM_NEAR_AUTO_OCCUPANCY * K));
+  const bool sparse = n < (int64_t)PMMM_NEAR_AUTO_OCCUPANCY * K;
+  const bool per_target = pp_per_target_applies(fp64, pl->g.c) &&
+                          (pl->cfg.near_field == PMMM_NEAR_PER_TARGET ||
+                           (pl->cfg.near_field == PMMM_NEAR_AUTO && sparse));
 #define CK(x)                    \
   do {                           \
     e = (x);                     \
@@ -375,11 +386,15 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
     if (!fp64) CK(launch_pair_pack(pl->part, pl->keys_sorted, pl->cs, pl->pair_start, n, pl->src2, s, &nl));
   }
   mark(pl, ST_P2M);
-  CK(launch_p2m(pl->p, fp64, pl->part, pl->cs, K, pl->M, pl->cellsum, pl->cellsum + K, s, &nl));
+  CK(launch_p2m(pl->p, fp64, pl->part, pl->cs, K, pl->M, pl->cellsum, pl->cellsum + K, sparse, s, &nl));
   mark(pl, ST_FFT_FWD);
   {
     FftTw tw{pl->twx, pl->twy, pl->twz};
-    CK(launch_fft_forward(fp64, pl->M, pl->specM, pl->d, pl->C * B, tw, s, &nl));
+    const bool fused = fft_fused_applies(fp64, pl->d);
+    if (fused)
+      CK(launch_fft_fused_forward(pl->M, pl->specM, pl->d, pl->C * B, tw, s, &nl));
+    else
+      CK(launch_fft_forward(fp64, pl->M, pl->specM, pl->d, pl->C * B, tw, s, &nl));
     mark(pl, ST_M2L);
     const int64_t R = (int64_t)pl->C * B;
     if (B == 1) {
@@ -398,14 +413,17 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
       CK(launch_m2l_systems(pl->p, fp64, pl->specM, pl->G, pl->specL, pl->d.Kh, B, s, &nl));
     }
     mark(pl, ST_FFT_INV);
-    CK(launch_fft_inverse(fp64, pl->specL, pl->L, pl->d, pl->C * B, tw, s, &nl));
+    if (fused)
+      CK(launch_fft_fused_inverse(pl->specL, pl->L, pl->d, pl->C * B, tw, s, &nl));
+    else
+      CK(launch_fft_inverse(fp64, pl->specL, pl->L, pl->d, pl->C * B, tw, s, &nl));
   }
   mark(pl, ST_L2P);
   if (pl->g.periodic) {
     if (B == 1)
       CK(launch_corrections(pl->cellsum, pl->cellsum + K, K, pl->g.hs, pl->g.V, pl->partial, pl->corr, s, &nl));
     else
-      CK(launch_corrections_batched(pl->cellsum, K, Ks, B, pl->g.hs, pl->g.V, pl->corr, s, &nl));
+      CK(launch_corrections_batched(pl->cellsum, K, Ks, B, pl->g.hs, pl->g.V, pl->bpartial, pl->corr, s, &nl));
   }
   {
     CorrParams cp;
@@ -445,7 +463,7 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
     if (B == 1)
       CK(launch_energy(pl->epart, mi, pl->partial + 256 * 5, pl->energy, s, &nl));
     else
-      CK(launch_energy_batched(pl->epart, pl->item_start, Ks, B, pl->energy, s, &nl));
+      CK(launch_energy_batched(pl->epart, pl->item_start, Ks, B, pl->bchunks, pl->bpartial, pl->energy, s, &nl));
   }
   mark(pl, ST_COUNT);
 #undef CK

@@ -362,3 +362,26 @@ def test_near_field_kernels_agree(pk, case):
     for nf in (pk.NEAR_CELL_ITEMS, pk.NEAR_PER_TARGET):
         e_f = _rel(out[nf][1][sel], rf)
         assert e_f < FP32_TOL[c.p], (nf, e_f)
+
+
+def test_sparse_p2m_fp32_vs_oracle(pk):
+    """FP32 P2M on sparsely filled cells (one thread per cell) with crowded cells (more
+    than 16 particles, taken by the whole warp): multipoles of every cell against the
+    oracle's, and the sums of the periodic corrections."""
+    pos, q = synth.plummer(20000, synth.seed(1, 35))
+    pos = pos.astype(np.float32).astype(np.float64)
+    cfg = pk.Config(box_lo=(-1, -1, -1), box_len=(2, 2, 2), mesh=(16, 16, 16), p=6, boundary=pk.PERIODIC,
+                    precision=pk.FP32)
+    plan, *_ = _run(pk, cfg, pos, q)
+    counts = np.diff(plan.export(pk.EXPORT_CELL_START))
+    assert counts.max() > 16 and (counts[counts > 0] <= 16).any()
+    ref = _oracle(cfg, pk, pos, q, want_ml=True)
+    M = plan.export(pk.EXPORT_MULTIPOLE)
+    Mr = oracle.to_real_storage(ref["M"]).T
+    for l in range(cfg.p + 1):
+        sl = slice(l * l, (l + 1) ** 2)
+        err = np.abs(M[sl] - Mr[sl]).max() / np.abs(Mr[sl]).max()
+        assert err < 2e-6 * (l + 1), (l, err)
+    corr = plan.export(pk.EXPORT_CORR)
+    assert np.allclose(corr[:5], ref["corr"][:5], rtol=1e-5, atol=1e-5)
+    plan.close()
