@@ -259,6 +259,79 @@ const char* pmmm_stage_name(int i);
 int pmmm_bin_sort_static(const pmmm_config* cfg, int64_t n, const void* pos, int32_t* perm, int32_t* cell_start,
                          void* cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned local-expansion correction.  The paper has no counterpart; this is an
+ * added form of the method.  A multilayer perceptron 432 -> 256 -> 256 -> 121
+ * (GELU; BF16 operands, FP32 accumulation on the tensor cores; FP32 master
+ * parameters) maps, for every cell, the order-3 multipoles (16 real storage
+ * channels, App. A.7) of its 27 nearest cells to the difference between the
+ * cell's order-p_high local expansion and its order-3 one.  An evaluation then
+ * runs the order-3 pipeline up to the cell convolution (Sec. 2.1), adds the
+ * network's correction to the order-3 locals, and runs L2P (Eqs. L2P, phigrad)
+ * at order p_high plus the usual near field.  The plain order-p_high
+ * evaluation produces the training targets, and pmmm_surrogate_set_fallback
+ * routes evaluations to it (used when the held-out error exceeds its bound).
+ *
+ * Units: features are M'_l = M_l / h^l times in_scale[channel]; targets and
+ * outputs are (L'_l(p_high) - L'_l(3)) times out_scale[channel], L'_l = h^(l+1) L_l,
+ * with h the cell size.  Parameter vector (FP32, PMMM_SUR_NPARAM values):
+ * W1 [256 x 432], b1 [256], W2 [256 x 256], b2 [256], W3 [128 x 256], b3 [128]
+ * (rows >= (p_high+1)^2 of W3 and b3 are padding).  Feature rows are ordered
+ * neighbour-major ((dz, dy, dx) in {-1,0,1}^3, dx fastest) then channel.
+ * Row counts passed to the calls below are multiples of 128.
+ * ------------------------------------------------------------------------- */
+typedef struct pmmm_surrogate pmmm_surrogate;
+#define PMMM_SUR_IN 432
+#define PMMM_SUR_OUT_ROWS 128
+#define PMMM_SUR_NPARAM 209536
+enum { PMMM_SUR_PARAMS = 1, PMMM_SUR_ADAM_M = 2, PMMM_SUR_ADAM_V = 3, PMMM_SUR_IN_SCALE = 4, PMMM_SUR_OUT_SCALE = 5 };
+enum {
+  PMMM_SUR_INFO_STEP = 1,     /* Adam steps taken */
+  PMMM_SUR_INFO_FALLBACK = 2, /* 1 when evaluations run the plain order-p_high method */
+  PMMM_SUR_INFO_CLOW = 3,     /* 16 */
+  PMMM_SUR_INFO_CHIGH = 4,    /* (p_high + 1)^2 */
+  PMMM_SUR_INFO_ROWS = 5      /* feature rows of one system: cells rounded up to 128 */
+};
+
+/* cfg: the order-3 configuration (p = 3, cutoff 1, PMMM_FP32); p_high in 4..10.
+ * Creates both the order-3 and the order-p_high plans on the stream; parameters
+ * and Adam state start at zero, scales at one. */
+int pmmm_surrogate_create(const pmmm_config* cfg, int32_t p_high, void* cuda_stream, pmmm_surrogate** out);
+int pmmm_surrogate_destroy(pmmm_surrogate* s);
+
+/* Host copies of the parameters, Adam moments (PMMM_SUR_NPARAM each) and the
+ * input (16) and output ((p_high+1)^2) scales; count must match.  Synchronous. */
+int pmmm_surrogate_get(pmmm_surrogate* s, int what, float* host, int64_t count);
+int pmmm_surrogate_set(pmmm_surrogate* s, int what, const float* host, int64_t count);
+int pmmm_surrogate_info(pmmm_surrogate* s, int what, int64_t* value);
+int pmmm_surrogate_set_step(pmmm_surrogate* s, int64_t step);
+int pmmm_surrogate_set_fallback(pmmm_surrogate* s, int on);
+
+/* One training example set from one system (device pos / q as in pmmm_compute):
+ * runs the plain order-3 and order-p_high evaluations and writes the features
+ * X (device, BF16 [rows][432]) and targets T (device, FP32 [rows][128]) of its
+ * cells, rows = PMMM_SUR_INFO_ROWS (zero past the last cell).  stats: host
+ * double[16 + (p_high+1)^2] or NULL; adds the sums over cells of the squared
+ * raw multipole channels and raw target channels (for choosing the scales).
+ * Synchronous. */
+int pmmm_surrogate_training_pair(pmmm_surrogate* s, int64_t n, const void* pos, const void* q, void* X, float* T,
+                                 double* stats);
+
+/* Network output for rows of features: out (device, FP32 [rows][128]).  Synchronous. */
+int pmmm_surrogate_forward(pmmm_surrogate* s, const void* X, int64_t rows, float* out);
+/* Loss (mean over rows and the (p_high+1)^2 outputs of the squared error) and its
+ * gradient with respect to the parameters (host, PMMM_SUR_NPARAM, may be NULL);
+ * no update.  Synchronous. */
+int pmmm_surrogate_gradients(pmmm_surrogate* s, const void* X, const float* T, int64_t rows, float* grad_host,
+                             double* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on a batch; loss (host) may be
+ * NULL, in which case the call is asynchronous. */
+int pmmm_surrogate_train_step(pmmm_surrogate* s, const void* X, const float* T, int64_t rows, float lr, double* loss);
+/* Potential and force with the corrected locals (or the plain order-p_high
+ * method in fallback); arguments as pmmm_compute. */
+int pmmm_surrogate_compute(pmmm_surrogate* s, int64_t n, const void* pos, const void* q, void* phi, void* force,
+                           double* energy);
+
 /* Human-readable name of a status code (static string). */
 const char* pmmm_strerror(int status);
 

@@ -28,6 +28,9 @@ EXPORT_MULTIPOLE, EXPORT_LOCAL, EXPORT_CORR, EXPORT_FAR = 4, 5, 6, 7
 INFO_K, INFO_C, INFO_CG, INFO_KH, INFO_N, INFO_WORKSPACE_BYTES, INFO_LAUNCHES = 1, 2, 3, 4, 5, 6, 7
 INFO_SYSTEMS = 8
 MAX_SYSTEMS = 65535
+SUR_PARAMS, SUR_ADAM_M, SUR_ADAM_V, SUR_IN_SCALE, SUR_OUT_SCALE = 1, 2, 3, 4, 5
+SUR_INFO_STEP, SUR_INFO_FALLBACK, SUR_INFO_CLOW, SUR_INFO_CHIGH, SUR_INFO_ROWS = 1, 2, 3, 4, 5
+SUR_IN, SUR_OUT_ROWS, SUR_NPARAM = 432, 128, 209536
 
 
 class PmmmError(RuntimeError):
@@ -85,6 +88,23 @@ _SIGS = {
     "pmmm_bin_sort_static": (ctypes.c_int, [ctypes.POINTER(_Config), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p]),
     "pmmm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pmmm_surrogate_create": (ctypes.c_int, [ctypes.POINTER(_Config), ctypes.c_int32, ctypes.c_void_p,
+                                             ctypes.POINTER(ctypes.c_void_p)]),
+    "pmmm_surrogate_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pmmm_surrogate_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]),
+    "pmmm_surrogate_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]),
+    "pmmm_surrogate_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+    "pmmm_surrogate_set_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "pmmm_surrogate_set_fallback": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "pmmm_surrogate_training_pair": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pmmm_surrogate_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "pmmm_surrogate_gradients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "pmmm_surrogate_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                 ctypes.c_float, ctypes.POINTER(ctypes.c_double)]),
+    "pmmm_surrogate_compute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -371,3 +391,119 @@ class Plan:
         if k < 0:
             raise PmmmError(k, "pmmm_plan_stage_times")
         return {names[i]: float(buf[i]) for i in range(k)}
+
+
+class Surrogate:
+    """Learned local-expansion correction (pmmm_surrogate_* of include/pmmm.h): an
+    order-3 plan whose locals are corrected toward order p_high by a multilayer
+    perceptron before L2P, with the plain order-p_high plan as training target and
+    fallback.  cfg must have p = 3, cutoff 1 and FP32 precision."""
+
+    def __init__(self, cfg: Config, p_high: int = 10, stream=None):
+        import torch
+        self.cfg = cfg
+        self.p_high = int(p_high)
+        c = cfg.to_c()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(_lib().pmmm_surrogate_create(ctypes.byref(c), self.p_high, ctypes.c_void_p(stream.cuda_stream),
+                                            ctypes.byref(h)), "pmmm_surrogate_create")
+        self._h = h
+        self.rows = self.info(SUR_INFO_ROWS)
+        self.c_high = self.info(SUR_INFO_CHIGH)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().pmmm_surrogate_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self, what: int) -> int:
+        v = ctypes.c_int64(0)
+        _check(_lib().pmmm_surrogate_info(self._h, int(what), ctypes.byref(v)), "pmmm_surrogate_info")
+        return int(v.value)
+
+    def _count(self, what):
+        return {SUR_PARAMS: SUR_NPARAM, SUR_ADAM_M: SUR_NPARAM, SUR_ADAM_V: SUR_NPARAM, SUR_IN_SCALE: 16,
+                SUR_OUT_SCALE: self.c_high}[what]
+
+    def get(self, what: int) -> np.ndarray:
+        out = np.zeros(self._count(what), dtype=np.float32)
+        _check(_lib().pmmm_surrogate_get(self._h, int(what), ctypes.c_void_p(out.ctypes.data), out.size),
+               "pmmm_surrogate_get")
+        return out
+
+    def set(self, what: int, values):
+        a = np.ascontiguousarray(values, dtype=np.float32).reshape(-1)
+        _check(_lib().pmmm_surrogate_set(self._h, int(what), ctypes.c_void_p(a.ctypes.data), a.size),
+               "pmmm_surrogate_set")
+
+    @property
+    def step(self) -> int:
+        return self.info(SUR_INFO_STEP)
+
+    @step.setter
+    def step(self, v: int):
+        _check(_lib().pmmm_surrogate_set_step(self._h, int(v)), "pmmm_surrogate_set_step")
+
+    @property
+    def fallback(self) -> bool:
+        return bool(self.info(SUR_INFO_FALLBACK))
+
+    @fallback.setter
+    def fallback(self, on: bool):
+        _check(_lib().pmmm_surrogate_set_fallback(self._h, int(bool(on))), "pmmm_surrogate_set_fallback")
+
+    def training_pair(self, pos, q, X, T, stats: np.ndarray = None):
+        """Features X (CUDA bfloat16 [rows, 432] view) and targets T (CUDA float32 [rows, 128])."""
+        st = _lib().pmmm_surrogate_training_pair(
+            self._h, int(q.shape[0]), ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(q.data_ptr()),
+            ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+            ctypes.c_void_p(stats.ctypes.data) if stats is not None else None)
+        _check(st, "pmmm_surrogate_training_pair")
+
+    def forward(self, X, out):
+        rows = int(X.shape[0])
+        _check(_lib().pmmm_surrogate_forward(self._h, ctypes.c_void_p(X.data_ptr()), rows,
+                                             ctypes.c_void_p(out.data_ptr())), "pmmm_surrogate_forward")
+        return out
+
+    def gradients(self, X, T):
+        g = np.zeros(SUR_NPARAM, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(_lib().pmmm_surrogate_gradients(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                               int(X.shape[0]), ctypes.c_void_p(g.ctypes.data), ctypes.byref(loss)),
+               "pmmm_surrogate_gradients")
+        return float(loss.value), g
+
+    def train_step_raw(self, x_ptr: int, t_ptr: int, rows: int, lr: float, want_loss: bool = False):
+        loss = ctypes.c_double(0.0)
+        st = _lib().pmmm_surrogate_train_step(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr), int(rows),
+                                              float(lr), ctypes.byref(loss) if want_loss else None)
+        _check(st, "pmmm_surrogate_train_step")
+        return float(loss.value) if want_loss else None
+
+    def compute(self, pos, q, phi=None, force=None, energy: bool = False):
+        import torch
+        n = int(q.shape[0])
+        if phi is None:
+            phi = torch.empty(n, dtype=torch.float32, device=q.device)
+        if force is None:
+            force = torch.empty((n, 3), dtype=torch.float32, device=q.device)
+        e = ctypes.c_double(0.0)
+        st = _lib().pmmm_surrogate_compute(self._h, n, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(q.data_ptr()),
+                                           ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(force.data_ptr()),
+                                           ctypes.byref(e) if energy else None)
+        _check(st, "pmmm_surrogate_compute")
+        return phi, force, (e.value if energy else None)
+
+    def compute_raw(self, n: int, pos_ptr: int, q_ptr: int, phi_ptr: int, force_ptr: int) -> int:
+        return _lib().pmmm_surrogate_compute(self._h, int(n), ctypes.c_void_p(pos_ptr), ctypes.c_void_p(q_ptr),
+                                             ctypes.c_void_p(phi_ptr), ctypes.c_void_p(force_ptr), None)

@@ -1,6 +1,7 @@
 // Internal declarations of the PMMM GPU library: plan state, geometry and the
 // launchers of every kernel.  Not part of the C ABI.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -150,6 +151,51 @@ cudaError_t launch_corrections_batched(const double* cellsum, int64_t Ktot, int6
 // nchunk >= ceil(items of any system / 4096)
 cudaError_t launch_energy_batched(const double* epart, const uint32_t* item_start, int64_t Ksys, int nsys, int nchunk,
                                   double* partial, double* energies, cudaStream_t s, int* nlaunch);
+
+// ---------------------------------------------------------------- mlp.cu
+// D[M x N] = A[M x K] . B[N x K]^T on the tensor cores (BF16 in, FP32 accumulate);
+// M % 128 == 0, N % 16 == 0, K % 16 == 0, row strides multiples of 8 elements.
+enum GemmEpi {
+  GEMM_EPI_LINEAR = 0,  // v = acc (+ bias): D32 and/or D16
+  GEMM_EPI_GELU = 1,    // v = acc + bias: D32 = v (pre-activation), D16 = gelu(v)
+  GEMM_EPI_DGELU = 2    // v = acc * gelu'(Zin): D32 and/or D16
+};
+struct GemmArgs {
+  const __nv_bfloat16* A = nullptr;
+  int64_t lda = 0;
+  const __nv_bfloat16* B = nullptr;
+  int64_t ldb = 0;
+  int M = 0, N = 0, K = 0;
+  const float* bias = nullptr;
+  float* D32 = nullptr;
+  int64_t ldd = 0;
+  __nv_bfloat16* D16 = nullptr;
+  int64_t ldd16 = 0;
+  const float* Zin = nullptr;
+  int64_t ldz = 0;
+  int epi = GEMM_EPI_LINEAR;
+  int* err = nullptr;
+};
+cudaError_t launch_gemm_tc(const GemmArgs& a, cudaStream_t s, int* nlaunch);
+cudaError_t launch_transpose_bf16(const void* in, int64_t ld_in, void* out, int64_t ld_out, int R, int C,
+                                  cudaStream_t s, int* nlaunch);
+cudaError_t launch_colsum(const float* in, int64_t ld, int R, int C, float* out, cudaStream_t s, int* nlaunch);
+// dO = 2 (O - T) / (rows nout) on columns < nout; *loss = mean square (device, FP64); part: nparts doubles
+cudaError_t launch_mse_grad(const float* O, const float* T, int64_t rows, int ld, int nout, float* dO, void* dO16,
+                            double* part, int nparts, double* loss, cudaStream_t s, int* nlaunch);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, int64_t step,
+                        cudaStream_t s, int* nlaunch);
+cudaError_t launch_to_bf16(const float* in, void* out, int64_t n, cudaStream_t s, int* nlaunch);
+// X[cell][27 * 16]: the 16 multipole channels of the 27 neighbour cells, times in_scale
+cudaError_t launch_gather_features(const float* M, int64_t K, const int n[3], int periodic, const float* in_scale,
+                                   void* X, int64_t ldx, cudaStream_t s, int* nlaunch);
+cudaError_t launch_build_targets(const float* Lhi, const float* Llo, int64_t K, int chi, int clow,
+                                 const float* out_scale, float* T, int ldt, cudaStream_t s, int* nlaunch);
+cudaError_t launch_combine_locals(const float* Llo, const float* O, int ldo, int64_t K, int chi, int clow,
+                                  const float* out_scale, float* L, cudaStream_t s, int* nlaunch);
+cudaError_t launch_channel_sumsq(const float* X, int C, int64_t K, double* out, cudaStream_t s, int* nlaunch);
+cudaError_t launch_diff_sumsq(const float* Lhi, const float* Llo, int C, int clow, int64_t K, double* out,
+                              cudaStream_t s, int* nlaunch);
 
 // ---------------------------------------------------------------- green.cu
 // Builds the real-space Green components G[s][Kt] (FP64, units of hs), s < (2p+1)^2.

@@ -30,6 +30,7 @@
 
 #include "internal.cuh"
 #include "m2l_table.cuh"
+#include "tcgen05.cuh"
 
 namespace pmmm {
 
@@ -53,68 +54,20 @@ constexpr uint32_t TC_SMEM = TC_OFF_BAR + 64;
 constexpr uint32_t TC_TMEM_COLS = 2 * TC_NMAX;        // two accumulators
 constexpr long long TC_WAIT_LIMIT = 1ll << 26;        // mbarrier polls before giving up
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
+using tc::smem_u32;
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t addr) { return tc::desc(addr, TC_LBO, TC_SBO); }
+__device__ __forceinline__ uint32_t make_idesc(int n) { return tc::idesc_bf16_m128(n); }
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+  tc::mma_bf16(d, a, b, idesc, acc);
 }
-
-// Shared-memory matrix descriptor: start address, LBO, SBO (all >> 4), version 1,
-// no swizzle.
-__device__ __forceinline__ uint64_t make_desc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(TC_LBO >> 4) << 16) | ((uint64_t)(TC_SBO >> 4) << 32) |
-         (1ull << 46);
-}
-
-// Instruction descriptor of kind::f16: FP32 D, BF16 A and B, both K-major, N, M = 128.
-__device__ __forceinline__ uint32_t make_idesc(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-// 32 lanes x 16 columns of 32-bit accumulators: lane i of the warp reads TMEM
-// lane (taddr >> 16) + i.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void mma_commit(uint32_t bar) { tc::commit(bar); }
+__device__ __forceinline__ void fence_after() { tc::fence_after(); }
+__device__ __forceinline__ void fence_before() { tc::fence_before(); }
+__device__ __forceinline__ void fence_proxy_async() { tc::fence_proxy_async(); }
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) { return tc::bar_wait(bar, parity, TC_WAIT_LIMIT); }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) { tc::ld16(taddr, v); }
+__device__ __forceinline__ void tmem_wait_ld() { tc::wait_ld(); }
 
 // hi / lo BF16 split of 8 values, packed in K order (element j at the lower address).
 __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
@@ -159,16 +112,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   for (int i = tid; i < TC_CH * TC_CH; i += TC_THREADS) tab[i] = tab_g[i];
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])));
+    tc::bar_init(smem_u32(&bars[0]), 1);
+    tc::bar_init(smem_u32(&bars[1]), 1);
     *abort_flag = 0;
     fence_proxy_async();
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TC_TMEM_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, TC_TMEM_COLS);
   fence_before();
   __syncthreads();
   fence_after();
@@ -298,7 +247,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (it >= 1) bar_wait(smem_u32(&bars[(it - 1) & 1]), (uint32_t)(((it - 1) >> 1) & 1));
   }
   fence_after();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+  if (warp == 0) tc::tmem_free(tmem, TC_TMEM_COLS);
 }
 
 }  // namespace

@@ -1,0 +1,93 @@
+// Private state of a PMMM plan (the opaque pmmm_plan of the C ABI), shared by
+// the translation units that drive an evaluation (pmmm.cu, surrogate.cu).
+#pragma once
+#include <functional>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+
+enum Stage { ST_SORT = 0, ST_P2M, ST_FFT_FWD, ST_M2L, ST_FFT_INV, ST_L2P, ST_PP, ST_REDUCE, ST_COUNT };
+
+namespace pmmm {
+// Called after the cell convolution (locals L ready, before L2P): may replace
+// the locals that L2P reads by an array of order p_l2p ([(p_l2p+1)^2][K], same
+// device units and type as the plan's L).
+struct FarHook {
+  std::function<cudaError_t(cudaStream_t, int*)> fn;
+  int p_l2p = -1;
+  const void* L = nullptr;
+};
+}  // namespace pmmm
+
+struct pmmm_plan {
+  using Dims = pmmm::Dims;
+  using Geo = pmmm::Geo;
+  using SortWork = pmmm::SortWork;
+  pmmm_config cfg;
+  cudaStream_t stream = nullptr;
+  int p = 0, C = 0, CG = 0;
+  bool fp64 = true;
+  Dims d{};
+  Geo g{};
+  int nmax = 5;
+  size_t tsize = 8;  // sizeof(T)
+  // mesh workspace
+  void *M = nullptr, *L = nullptr, *specM = nullptr, *specL = nullptr, *G = nullptr;
+  void *twx = nullptr, *twy = nullptr, *twz = nullptr;
+  double* cellsum = nullptr;  // [5][K]: sum q, sum q u_x, sum q u_y, sum q u_z, sum q |u|^2
+  int* cs = nullptr;          // [K+1]
+  double* corr = nullptr;     // [16]
+  double* partial = nullptr;  // [256 * 16]
+  double* bpartial = nullptr;  // per-system reduction chunks: [5][bcap][bchunks]
+  int bchunks = 0;
+  double* epart = nullptr;    // [max items][4]
+  uint32_t* item_start = nullptr;  // [K+1] near-field work items per cell (scanned)
+  uint32_t* item_chunks = nullptr; // scan scratch
+  uint32_t* item_cell = nullptr;   // [max items]
+  int64_t max_items = 0;
+  unsigned int* counter = nullptr; // near-field work counter
+  uint32_t* pair_start = nullptr;  // [K+1] FP32 near-field source pairs per cell (scanned)
+  void* src2 = nullptr;            // pair-interleaved FP32 sources
+  int num_sms = 0;
+  double* energy = nullptr;   // [4 * bcap]: energy and net force per system
+  int* err = nullptr;
+  // systems: the mesh workspace above holds bcap systems side by side
+  int bcap = 0;
+  int nsys_last = 1;
+  int64_t* offsets_d = nullptr;       // [bcap + 1] particle offsets of the systems
+  int64_t* offsets_pinned = nullptr;  // host staging of the offsets
+  std::vector<int64_t> offsets_up;    // offsets of the last upload
+  int* m2l_tab = nullptr;             // batched M2L entry table, 4 ints per entry
+  uint32_t* m2l_tab_tc = nullptr;     // packed entry table of the tensor-core M2L
+  bool m2l_tc = false;                // batched M2L on the tensor cores (split BF16)
+  std::unordered_map<void*, size_t> sizes;
+  // CUDA graph of one batched evaluation, and the arguments it was captured for
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<int64_t> gkey_off;
+  const void* gkey_ptr[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool capturing = false;
+  const pmmm::FarHook* hook = nullptr;  // set by the surrogate for one evaluation
+  // particle workspace
+  int64_t cap = 0;
+  SortWork sw{};
+  void *part = nullptr, *far = nullptr;
+  // staging for pmmm_compute_host
+  int64_t hcap = 0;
+  void *hpos = nullptr, *hq = nullptr, *hphi = nullptr, *hforce = nullptr;
+  // last evaluation
+  int64_t n_last = 0;
+  uint32_t *keys_sorted = nullptr, *vals_sorted = nullptr;
+  int launches = 0;
+  size_t ws_bytes = 0;
+  bool timing = false, timed = false;
+  cudaEvent_t ev[ST_COUNT + 1] = {};
+};
+
+
+namespace pmmm {
+// One evaluation of B systems (pmmm.cu); B > 1 needs the offsets uploaded.
+int plan_run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* phi, void* force);
+int plan_read_energies(pmmm_plan* pl, int B, double* out);
+int plan_map_cuda(cudaError_t e);
+}  // namespace pmmm

@@ -6,16 +6,14 @@
 #include <string.h>
 
 #include <new>
-#include <unordered_map>
 #include <vector>
 
-#include "internal.cuh"
+#include "plan.cuh"
 
 using namespace pmmm;
 
 namespace {
 
-enum Stage { ST_SORT = 0, ST_P2M, ST_FFT_FWD, ST_M2L, ST_FFT_INV, ST_L2P, ST_PP, ST_REDUCE, ST_COUNT };
 const char* kStageNames[ST_COUNT] = {"bin_sort", "p2m", "fft_forward", "m2l", "fft_inverse", "l2p", "near_field",
                                      "reduce"};
 
@@ -28,66 +26,6 @@ int map_cuda(cudaError_t e) {
 }
 
 }  // namespace
-
-struct pmmm_plan {
-  pmmm_config cfg;
-  cudaStream_t stream = nullptr;
-  int p = 0, C = 0, CG = 0;
-  bool fp64 = true;
-  Dims d{};
-  Geo g{};
-  int nmax = 5;
-  size_t tsize = 8;  // sizeof(T)
-  // mesh workspace
-  void *M = nullptr, *L = nullptr, *specM = nullptr, *specL = nullptr, *G = nullptr;
-  void *twx = nullptr, *twy = nullptr, *twz = nullptr;
-  double* cellsum = nullptr;  // [5][K]: sum q, sum q u_x, sum q u_y, sum q u_z, sum q |u|^2
-  int* cs = nullptr;          // [K+1]
-  double* corr = nullptr;     // [16]
-  double* partial = nullptr;  // [256 * 16]
-  double* bpartial = nullptr;  // per-system reduction chunks: [5][bcap][bchunks]
-  int bchunks = 0;
-  double* epart = nullptr;    // [max items][4]
-  uint32_t* item_start = nullptr;  // [K+1] near-field work items per cell (scanned)
-  uint32_t* item_chunks = nullptr; // scan scratch
-  uint32_t* item_cell = nullptr;   // [max items]
-  int64_t max_items = 0;
-  unsigned int* counter = nullptr; // near-field work counter
-  uint32_t* pair_start = nullptr;  // [K+1] FP32 near-field source pairs per cell (scanned)
-  void* src2 = nullptr;            // pair-interleaved FP32 sources
-  int num_sms = 0;
-  double* energy = nullptr;   // [4 * bcap]: energy and net force per system
-  int* err = nullptr;
-  // systems: the mesh workspace above holds bcap systems side by side
-  int bcap = 0;
-  int nsys_last = 1;
-  int64_t* offsets_d = nullptr;       // [bcap + 1] particle offsets of the systems
-  int64_t* offsets_pinned = nullptr;  // host staging of the offsets
-  std::vector<int64_t> offsets_up;    // offsets of the last upload
-  int* m2l_tab = nullptr;             // batched M2L entry table, 4 ints per entry
-  uint32_t* m2l_tab_tc = nullptr;     // packed entry table of the tensor-core M2L
-  bool m2l_tc = false;                // batched M2L on the tensor cores (split BF16)
-  std::unordered_map<void*, size_t> sizes;
-  // CUDA graph of one batched evaluation, and the arguments it was captured for
-  cudaGraphExec_t gexec = nullptr;
-  std::vector<int64_t> gkey_off;
-  const void* gkey_ptr[4] = {nullptr, nullptr, nullptr, nullptr};
-  bool capturing = false;
-  // particle workspace
-  int64_t cap = 0;
-  SortWork sw{};
-  void *part = nullptr, *far = nullptr;
-  // staging for pmmm_compute_host
-  int64_t hcap = 0;
-  void *hpos = nullptr, *hq = nullptr, *hphi = nullptr, *hforce = nullptr;
-  // last evaluation
-  int64_t n_last = 0;
-  uint32_t *keys_sorted = nullptr, *vals_sorted = nullptr;
-  int launches = 0;
-  size_t ws_bytes = 0;
-  bool timing = false, timed = false;
-  cudaEvent_t ev[ST_COUNT + 1] = {};
-};
 
 namespace {
 
@@ -436,7 +374,14 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
     cp.c_self = 2.0 * pl->g.alpha * 0.56418958354775628695;  // 2 alpha / sqrt(pi)
     cp.periodic = pl->g.periodic;
     cp.ksys = Ks;
-    CK(launch_l2p(pl->p, fp64, pl->part, pl->keys_sorted, n, pl->L, K, pl->corr, pl->cellsum, cp, pl->far, s, &nl));
+    const void* Luse = pl->L;
+    int puse = pl->p;
+    if (pl->hook) {
+      CK(pl->hook->fn(s, &nl));
+      Luse = pl->hook->L;
+      puse = pl->hook->p_l2p;
+    }
+    CK(launch_l2p(puse, fp64, pl->part, pl->keys_sorted, n, Luse, K, pl->corr, pl->cellsum, cp, pl->far, s, &nl));
   }
   mark(pl, ST_PP);
   {
@@ -571,6 +516,14 @@ int run_host(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, vo
 }
 
 }  // namespace
+
+namespace pmmm {
+int plan_run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* phi, void* force) {
+  return run(pl, B, n, pos, q, phi, force);
+}
+int plan_read_energies(pmmm_plan* pl, int B, double* out) { return read_energies(pl, B, out); }
+int plan_map_cuda(cudaError_t e) { return map_cuda(e); }
+}  // namespace pmmm
 
 extern "C" {
 

@@ -1,0 +1,160 @@
+"""Training and evaluation driver of the learned local-expansion correction.
+
+Everything numerical runs in the library's kernels through the C ABI
+(pmmm_surrogate_*): data generation (order-3 and order-p_high evaluations,
+feature gather, targets), the forward and backward passes, Adam, and the
+corrected evaluation.  This module only allocates device buffers, chooses
+minibatch offsets, and keeps checkpoints (``.npz`` with parameters, Adam
+moments, step, scales and the fallback flag).
+
+Held-out judgement: the relative RMS force error of the corrected evaluation
+against the plain order-p_high evaluation on systems not used for training;
+above ``bound`` (1e-4 by default) the surrogate is switched to its fallback,
+the plain order-p_high method.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import (SUR_ADAM_M, SUR_ADAM_V, SUR_IN_SCALE, SUR_NPARAM, SUR_OUT_SCALE, SUR_PARAMS, FP32, Config, Plan,
+               Surrogate)
+
+I, H, OP = 432, 256, 128
+
+
+def init_params(c_high: int, seed: int) -> np.ndarray:
+    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases, zero padding rows of W3."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    W1 = g.uniform(-1, 1, (H, I)) / math.sqrt(I)
+    W2 = g.uniform(-1, 1, (H, H)) / math.sqrt(H)
+    W3 = g.uniform(-1, 1, (OP, H)) / math.sqrt(H)
+    W3[c_high:] = 0.0
+    parts = [W1, np.zeros(H), W2, np.zeros(H), W3, np.zeros(OP)]
+    theta = np.concatenate([p.reshape(-1) for p in parts]).astype(np.float32)
+    assert theta.size == SUR_NPARAM
+    return theta
+
+
+def _dev(a, dtype):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+class Trainer:
+    def __init__(self, sur: Surrogate):
+        self.sur = sur
+        self.rows = sur.rows
+
+    # ------------------------------------------------------------------ data
+    def calibrate(self, systems):
+        """Input and output scales from the mean squares of the raw multipole and
+        target channels over the cells of `systems` ((pos, q) numpy pairs)."""
+        import torch
+        stats = np.zeros(16 + self.sur.c_high)
+        X = torch.empty((self.rows, I), dtype=torch.bfloat16, device="cuda")
+        T = torch.empty((self.rows, OP), dtype=torch.float32, device="cuda")
+        self.sur.set(SUR_IN_SCALE, np.ones(16))
+        self.sur.set(SUR_OUT_SCALE, np.ones(self.sur.c_high))
+        cells = 0
+        for pos, q in systems:
+            self.sur.training_pair(_dev(pos, torch.float32), _dev(q, torch.float32), X, T, stats)
+            cells += int(np.prod(self.sur.cfg.mesh))
+        ms = np.maximum(stats / cells, 1e-30)
+        self.in_scale = (1.0 / np.sqrt(ms[:16])).astype(np.float32)
+        self.out_scale = (1.0 / np.sqrt(ms[16:])).astype(np.float32)
+        self.sur.set(SUR_IN_SCALE, self.in_scale)
+        self.sur.set(SUR_OUT_SCALE, self.out_scale)
+        return self.in_scale, self.out_scale
+
+    def dataset(self, systems):
+        """Device features [S * rows, 432] (bfloat16) and targets [S * rows, 128] (float32)."""
+        import torch
+        S = len(systems)
+        X = torch.empty((S * self.rows, I), dtype=torch.bfloat16, device="cuda")
+        T = torch.empty((S * self.rows, OP), dtype=torch.float32, device="cuda")
+        for s, (pos, q) in enumerate(systems):
+            self.sur.training_pair(_dev(pos, torch.float32), _dev(q, torch.float32), X[s * self.rows:(s + 1) * self.rows],
+                                   T[s * self.rows:(s + 1) * self.rows])
+        return X, T
+
+    # ------------------------------------------------------------------ training
+    def fit(self, X, T, epochs: int, batch: int, lr: float, seed: int, log_every: int = 0):
+        """Adam on minibatches of `batch` consecutive rows, taken in a new random order
+        every epoch; returns the loss of the last batch of every epoch."""
+        assert batch % 128 == 0 and X.shape[0] % batch == 0
+        g = np.random.Generator(np.random.PCG64(seed))
+        nb = X.shape[0] // batch
+        xs, ts = X.element_size() * I, T.element_size() * OP
+        history = []
+        for ep in range(epochs):
+            order = g.permutation(nb)
+            for j, b in enumerate(order):
+                last = j == nb - 1
+                loss = self.sur.train_step_raw(X.data_ptr() + int(b) * batch * xs, T.data_ptr() + int(b) * batch * ts,
+                                               batch, lr, want_loss=last)
+            history.append(loss)
+            if log_every and (ep + 1) % log_every == 0:
+                print(f"epoch {ep + 1}: loss {loss:.4e}")
+        return history
+
+    def loss(self, X, T, batch: int = 8192):
+        """Mean loss over a dataset (no update)."""
+        tot, n = 0.0, 0
+        for b in range(X.shape[0] // batch):
+            l, _ = self.sur.gradients(X[b * batch:(b + 1) * batch], T[b * batch:(b + 1) * batch])
+            tot += l
+            n += 1
+        return tot / max(n, 1)
+
+    # ------------------------------------------------------------------ judgement
+    def evaluate(self, systems, bound: float = 1e-4):
+        """Relative RMS force error, against the plain order-p_high evaluation, of the
+        corrected evaluation and of the plain order-3 one, per held-out system; sets
+        the fallback when the largest corrected error exceeds `bound`."""
+        import torch
+        cfg = self.sur.cfg
+        lo = Plan(Config(box_lo=cfg.box_lo, box_len=cfg.box_len, mesh=cfg.mesh, p=3, boundary=cfg.boundary,
+                         precision=FP32, sign=cfg.sign, ewald_alpha=cfg.ewald_alpha, ewald_nmax=cfg.ewald_nmax),
+                  self.sur.stream)
+        hi = Plan(Config(box_lo=cfg.box_lo, box_len=cfg.box_len, mesh=cfg.mesh, p=self.sur.p_high,
+                         boundary=cfg.boundary, precision=FP32, sign=cfg.sign, ewald_alpha=cfg.ewald_alpha,
+                         ewald_nmax=cfg.ewald_nmax), self.sur.stream)
+        fallback = self.sur.fallback
+        self.sur.fallback = False
+        rows = []
+        for pos, q in systems:
+            tp, tq = _dev(pos, torch.float32), _dev(q, torch.float32)
+            _, f_hi, _ = hi.compute(tp, tq, energy=True)
+            _, f_lo, _ = lo.compute(tp, tq, energy=True)
+            _, f_s, _ = self.sur.compute(tp, tq, energy=True)
+            ref = f_hi.double().cpu().numpy()
+            norm = math.sqrt((ref ** 2).sum())
+            e_lo = math.sqrt(((f_lo.double().cpu().numpy() - ref) ** 2).sum()) / norm
+            e_s = math.sqrt(((f_s.double().cpu().numpy() - ref) ** 2).sum()) / norm
+            rows.append((e_lo, e_s))
+        lo.close()
+        hi.close()
+        errs = np.array(rows)
+        self.sur.fallback = bool(errs[:, 1].max() > bound) or fallback
+        return errs
+
+    # ------------------------------------------------------------------ checkpoints
+    def save(self, path: str):
+        np.savez(path, params=self.sur.get(SUR_PARAMS), adam_m=self.sur.get(SUR_ADAM_M),
+                 adam_v=self.sur.get(SUR_ADAM_V), step=np.int64(self.sur.step),
+                 in_scale=self.sur.get(SUR_IN_SCALE), out_scale=self.sur.get(SUR_OUT_SCALE),
+                 fallback=np.int64(self.sur.fallback), p_high=np.int64(self.sur.p_high))
+
+    def load(self, path: str):
+        d = np.load(path)
+        if int(d["p_high"]) != self.sur.p_high:
+            raise ValueError("checkpoint is for another p_high")
+        self.sur.set(SUR_PARAMS, d["params"])
+        self.sur.set(SUR_ADAM_M, d["adam_m"])
+        self.sur.set(SUR_ADAM_V, d["adam_v"])
+        self.sur.set(SUR_IN_SCALE, d["in_scale"])
+        self.sur.set(SUR_OUT_SCALE, d["out_scale"])
+        self.sur.step = int(d["step"])
+        self.sur.fallback = bool(int(d["fallback"]))
