@@ -223,9 +223,23 @@ enum {
   PMMM_INFO_N = 5,
   PMMM_INFO_WORKSPACE_BYTES = 6,
   PMMM_INFO_LAUNCHES = 7,
-  PMMM_INFO_SYSTEMS = 8
+  PMMM_INFO_SYSTEMS = 8,
+  PMMM_INFO_TUNED_NEAR = 9, /* near-field kernel chosen by pmmm_plan_autotune (0: none, from the config) */
+  PMMM_INFO_M2L_TILE = 10   /* systems per CTA of the tensor-core batched M2L (32 or 64; default 64) */
 };
 int pmmm_plan_info(pmmm_plan* plan, int what, int64_t* value);
+
+/* Autotuner: evaluates the given input (nsys systems; offsets as in
+ * pmmm_compute_batched, or {0, n} for one system) once per candidate of each
+ * tunable choice, timed over `reps` evaluations with CUDA events after one
+ * warm-up, and keeps the fastest: the near-field kernel (cell items or per
+ * target, where both apply) and, for batched PMMM_FP32_SPLITBF16_M2L plans, the
+ * systems per CTA of the tensor-core M2L (64 or 32).  The choice overrides the
+ * config's near_field; results differ between choices only by the order of
+ * floating-point sums.  Synchronous; reads back with PMMM_INFO_TUNED_NEAR and
+ * PMMM_INFO_M2L_TILE. */
+int pmmm_plan_autotune(pmmm_plan* plan, int32_t nsys, const int64_t* offsets, const void* pos, const void* q,
+                       int32_t reps);
 
 /* Per-stage timing with CUDA events on the plan's stream (off by default).
  * pmmm_plan_stage_times synchronises and writes up to max_stages values in

@@ -27,6 +27,7 @@ EXPORT_PERM, EXPORT_SORTED_CELL, EXPORT_CELL_START = 1, 2, 3
 EXPORT_MULTIPOLE, EXPORT_LOCAL, EXPORT_CORR, EXPORT_FAR = 4, 5, 6, 7
 INFO_K, INFO_C, INFO_CG, INFO_KH, INFO_N, INFO_WORKSPACE_BYTES, INFO_LAUNCHES = 1, 2, 3, 4, 5, 6, 7
 INFO_SYSTEMS = 8
+INFO_TUNED_NEAR, INFO_M2L_TILE = 9, 10
 MAX_SYSTEMS = 65535
 SUR_PARAMS, SUR_ADAM_M, SUR_ADAM_V, SUR_IN_SCALE, SUR_OUT_SCALE = 1, 2, 3, 4, 5
 SUR_INFO_STEP, SUR_INFO_FALLBACK, SUR_INFO_CLOW, SUR_INFO_CHIGH, SUR_INFO_ROWS = 1, 2, 3, 4, 5
@@ -79,6 +80,8 @@ _SIGS = {
                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                   ctypes.c_void_p]),
     "pmmm_plan_reserve_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
+    "pmmm_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int32]),
     "pmmm_plan_status": (ctypes.c_int, [ctypes.c_void_p]),
     "pmmm_plan_export": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
     "pmmm_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
@@ -353,6 +356,15 @@ class Plan:
                                               ctypes.c_void_p(e.ctypes.data))
         _check(st, "pmmm_compute_batched_host")
         return phi, force, e
+
+    def autotune(self, counts, pos, q, reps: int = 3):
+        """pmmm_plan_autotune on these inputs (counts: particles per system); returns the
+        (near-field kernel, tensor-core M2L tile) chosen."""
+        off = self._offsets(counts)
+        _check(_lib().pmmm_plan_autotune(self._h, len(counts), ctypes.c_void_p(off.ctypes.data),
+                                         ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(q.data_ptr()), int(reps)),
+               "pmmm_plan_autotune")
+        return self.info(INFO_TUNED_NEAR), self.info(INFO_M2L_TILE)
 
     def status(self) -> int:
         return int(_lib().pmmm_plan_status(self._h))

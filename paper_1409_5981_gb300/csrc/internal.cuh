@@ -140,8 +140,9 @@ cudaError_t launch_m2l_batched(bool fp64, const void* Mt, const void* Gt, void* 
 // split-BF16 operands, FP32 accumulation; p <= 7.  tab: build_m2l_table_tc(p) on the device.
 bool m2l_tc_supported(int p);
 std::vector<uint32_t> build_m2l_table_tc(int p);
+// tile: systems per CTA (32 or 64)
 cudaError_t launch_m2l_tc(const void* Mt, const void* Gt, void* Lt, const uint32_t* tab, int p, int nsys, int64_t Kh,
-                          int num_sms, int* err, cudaStream_t s, int* nlaunch);
+                          int num_sms, int tile, int* err, cudaStream_t s, int* nlaunch);
 // Chunks per system of the two-level batched reductions (partial: 5 * nsys * chunks doubles).
 int reduce_batched_chunks(int64_t Ksys, int64_t max_items_per_sys);
 // corr[16 s + ...] of every system (the single-system layout of launch_corrections)

@@ -36,22 +36,26 @@ namespace pmmm {
 
 namespace {
 
-constexpr int TC_THREADS = 256;
+constexpr int TC_THREADS = 512;  // 16 warps: the operand assembly is latency bound
 constexpr int TC_CH = 64;                             // channels after padding (p <= 7)
 constexpr int TC_K = 2 * TC_CH;                       // GEMM K: Re and Im parts of M
-constexpr int TC_NMAX = 64;                           // systems per tile (GEMM N)
+constexpr int TC_NMAX = 64;                           // largest system tile (GEMM N)
 constexpr uint32_t TC_LBO = 128;                      // next core matrix along K
 constexpr uint32_t TC_SBO = (TC_K / 8) * 128;         // next 8-row group: 2048 B
 constexpr uint32_t TC_A_BYTES = 128 * TC_K * 2;       // one split of W: 32 KB
-constexpr uint32_t TC_B_BYTES = TC_NMAX * TC_K * 2;   // one split of X: 16 KB
-constexpr uint32_t TC_STAGE = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // 96 KB
 constexpr uint32_t TC_GK_BYTES = 2048;                // (2p+1)^2 <= 225 complex
 constexpr uint32_t TC_TAB_BYTES = TC_CH * TC_CH * 4;  // packed entry table, 16 KB
-constexpr uint32_t TC_OFF_GK = 2 * TC_STAGE;
-constexpr uint32_t TC_OFF_TAB = TC_OFF_GK + TC_GK_BYTES;
-constexpr uint32_t TC_OFF_BAR = TC_OFF_TAB + TC_TAB_BYTES;
-constexpr uint32_t TC_SMEM = TC_OFF_BAR + 64;
-constexpr uint32_t TC_TMEM_COLS = 2 * TC_NMAX;        // two accumulators
+// per system tile NT (32 or 64): X splits, stage, shared-memory offsets, TMEM columns
+template <int NT>
+struct TcTile {
+  static constexpr uint32_t B_BYTES = NT * TC_K * 2;                   // one split of X
+  static constexpr uint32_t STAGE = 2 * TC_A_BYTES + 2 * B_BYTES;
+  static constexpr uint32_t OFF_GK = 2 * STAGE;
+  static constexpr uint32_t OFF_TAB = OFF_GK + TC_GK_BYTES;
+  static constexpr uint32_t OFF_BAR = OFF_TAB + TC_TAB_BYTES;
+  static constexpr uint32_t SMEM = OFF_BAR + 64;
+  static constexpr uint32_t TMEM_COLS = 2 * NT;                         // two accumulators
+};
 constexpr long long TC_WAIT_LIMIT = 1ll << 26;        // mbarrier polls before giving up
 
 using tc::smem_u32;
@@ -94,19 +98,21 @@ __device__ __forceinline__ uint32_t chunk_off(int r, int g) {
 }
 
 // Entry table packing: i1 | (s1 + 1) << 10 | i2 << 12 | (s2 + 1) << 22
+template <int NT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     m2l_tc_kernel(const float2* __restrict__ Mt, const float2* __restrict__ Gt, float2* __restrict__ Lt,
                   const uint32_t* __restrict__ tab_g, int C, int CG, int B, int64_t Kh, int64_t kchunk,
                   int* __restrict__ err) {
+  using Tl = TcTile<NT>;
   extern __shared__ __align__(1024) unsigned char smem[];
-  float2* gk = reinterpret_cast<float2*>(smem + TC_OFF_GK);
-  uint32_t* tab = reinterpret_cast<uint32_t*>(smem + TC_OFF_TAB);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_OFF_BAR);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + TC_OFF_BAR + 16);
-  int* abort_flag = reinterpret_cast<int*>(smem + TC_OFF_BAR + 20);
+  float2* gk = reinterpret_cast<float2*>(smem + Tl::OFF_GK);
+  uint32_t* tab = reinterpret_cast<uint32_t*>(smem + Tl::OFF_TAB);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Tl::OFF_BAR);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Tl::OFF_BAR + 16);
+  int* abort_flag = reinterpret_cast<int*>(smem + Tl::OFF_BAR + 20);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int b0 = blockIdx.y * TC_NMAX;
-  const int nb = min(TC_NMAX, B - b0);
+  const int b0 = blockIdx.y * NT;
+  const int nb = min(NT, B - b0);
   const int nmma = (nb + 15) & ~15;  // GEMM N: systems padded to a multiple of 16
   const int64_t kbeg = (int64_t)blockIdx.x * kchunk, kend = min(Kh, kbeg + kchunk);
 
@@ -117,7 +123,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     *abort_flag = 0;
     fence_proxy_async();
   }
-  if (warp == 0) tc::tmem_alloc(tmem_slot, TC_TMEM_COLS);
+  if (warp == 0) tc::tmem_alloc(tmem_slot, Tl::TMEM_COLS);
   fence_before();
   __syncthreads();
   fence_after();
@@ -131,17 +137,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // warp-uniform outcome: the TMEM loads below are .sync.aligned
     if (!__all_sync(0xffffffffu, bar_wait(smem_u32(&bars[buf]), parity))) return false;
     fence_after();
+    // warp w reads TMEM lanes 32 (w % 4) ... and the 16 columns 16 (w / 4) ... (NT / 16 groups)
+    const int cg = warp >> 2;
+    if (cg >= NT / 16) {
+      fence_before();
+      return true;
+    }
     const int row = 32 * (warp & 3) + lane;
-    const int col0 = 32 * (warp >> 2);
-    float v[32];
-    const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(buf * TC_NMAX + col0);
+    const int col0 = 16 * cg;
+    float v[16];
+    const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(buf * NT + col0);
     tmem_ld16(taddr, v);
-    tmem_ld16(taddr + 16, v + 16);
     tmem_wait_ld();
     const int c = row >> 1;
     const bool odd = lane & 1;
 #pragma unroll
-    for (int jj = 0; jj < 16; ++jj) {
+    for (int jj = 0; jj < 8; ++jj) {
       const float a = v[2 * jj], b = v[2 * jj + 1];
       const float recv = __shfl_xor_sync(0xffffffffu, odd ? a : b, 1);
       const int n = col0 + 2 * jj + (odd ? 1 : 0);
@@ -156,7 +167,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   bool ok = true;
   for (int64_t k = kbeg; k < kend; ++k, ++it) {
     const int buf = it & 1;
-    unsigned char* st = smem + buf * TC_STAGE;
+    unsigned char* st = smem + buf * Tl::STAGE;
     // kernel spectra of this wavevector
     for (int s = tid; s < CG; s += TC_THREADS) gk[s] = Gt[(int64_t)s * Kh + k];
     __syncthreads();
@@ -190,7 +201,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       *reinterpret_cast<uint4*>(Al + chunk_off(2 * co + 1, 8 + kg)) = rl;
     }
     // X: unit (system n, K-group cg of 8 channels) -> row n, K-groups cg (Re) and 8 + cg (Im)
-    for (int u = tid; u < TC_NMAX * 8; u += TC_THREADS) {
+    for (int u = tid; u < NT * 8; u += TC_THREADS) {
       const int n = (u & 7) + 8 * (u >> 6), cg = (u >> 3) & 7;
       float xr[8], xi[8];
 #pragma unroll
@@ -205,7 +216,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       split8(xr, rh, rl);
       split8(xi, ih, il);
       unsigned char* Xh = st + 2 * TC_A_BYTES;
-      unsigned char* Xl = Xh + TC_B_BYTES;
+      unsigned char* Xl = Xh + Tl::B_BYTES;
       *reinterpret_cast<uint4*>(Xh + chunk_off(n, cg)) = rh;
       *reinterpret_cast<uint4*>(Xl + chunk_off(n, cg)) = rl;
       *reinterpret_cast<uint4*>(Xh + chunk_off(n, 8 + cg)) = ih;
@@ -215,9 +226,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     if (tid == 0) {
       fence_after();
-      const uint32_t a_h = sbase + buf * TC_STAGE, a_l = a_h + TC_A_BYTES;
-      const uint32_t x_h = a_h + 2 * TC_A_BYTES, x_l = x_h + TC_B_BYTES;
-      const uint32_t d = tmem + (uint32_t)(buf * TC_NMAX);
+      const uint32_t a_h = sbase + buf * Tl::STAGE, a_l = a_h + TC_A_BYTES;
+      const uint32_t x_h = a_h + 2 * TC_A_BYTES, x_l = x_h + Tl::B_BYTES;
+      const uint32_t d = tmem + (uint32_t)(buf * NT);
       const uint32_t As[3] = {a_h, a_h, a_l}, Xs[3] = {x_h, x_l, x_h};
 #pragma unroll
       for (int sp = 0; sp < 3; ++sp)
@@ -247,7 +258,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (it >= 1) bar_wait(smem_u32(&bars[(it - 1) & 1]), (uint32_t)(((it - 1) >> 1) & 1));
   }
   fence_after();
-  if (warp == 0) tc::tmem_free(tmem, TC_TMEM_COLS);
+  if (warp == 0) tc::tmem_free(tmem, Tl::TMEM_COLS);
 }
 
 }  // namespace
@@ -268,21 +279,31 @@ std::vector<uint32_t> build_m2l_table_tc(int p) {
   return out;
 }
 
-cudaError_t launch_m2l_tc(const void* Mt, const void* Gt, void* Lt, const uint32_t* tab, int p, int B, int64_t Kh,
-                          int num_sms, int* err, cudaStream_t s, int* nl) {
-  if (!m2l_tc_supported(p) || B < 1) return cudaErrorInvalidValue;
+namespace {
+template <int NT>
+cudaError_t m2l_tc_run(const void* Mt, const void* Gt, void* Lt, const uint32_t* tab, int p, int B, int64_t Kh,
+                       int num_sms, int* err, cudaStream_t s) {
   const int C = (p + 1) * (p + 1), CG = (2 * p + 1) * (2 * p + 1);
-  const int ntiles = (B + TC_NMAX - 1) / TC_NMAX;
+  const int ntiles = (B + NT - 1) / NT;
   const int per_tile = (int)std::max<int64_t>(1, std::min<int64_t>(Kh, (num_sms + ntiles - 1) / ntiles));
   const int64_t kchunk = (Kh + per_tile - 1) / per_tile;
   const unsigned gx = (unsigned)((Kh + kchunk - 1) / kchunk);
-  cudaError_t e = cudaFuncSetAttribute(m2l_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+  const uint32_t smem = TcTile<NT>::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(m2l_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(gx, (unsigned)ntiles);
-  m2l_tc_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>((const float2*)Mt, (const float2*)Gt, (float2*)Lt, tab, C, CG, B,
-                                                  Kh, kchunk, err);
-  ++*nl;
+  m2l_tc_kernel<NT><<<grid, TC_THREADS, smem, s>>>((const float2*)Mt, (const float2*)Gt, (float2*)Lt, tab, C, CG, B,
+                                                   Kh, kchunk, err);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_m2l_tc(const void* Mt, const void* Gt, void* Lt, const uint32_t* tab, int p, int B, int64_t Kh,
+                          int num_sms, int tile, int* err, cudaStream_t s, int* nl) {
+  if (!m2l_tc_supported(p) || B < 1) return cudaErrorInvalidValue;
+  ++*nl;
+  if (tile == 32) return m2l_tc_run<32>(Mt, Gt, Lt, tab, p, B, Kh, num_sms, err, s);
+  return m2l_tc_run<64>(Mt, Gt, Lt, tab, p, B, Kh, num_sms, err, s);
 }
 
 }  // namespace pmmm

@@ -68,6 +68,9 @@ struct pmmm_plan {
   const void* gkey_ptr[4] = {nullptr, nullptr, nullptr, nullptr};
   bool capturing = false;
   const pmmm::FarHook* hook = nullptr;  // set by the surrogate for one evaluation
+  // choices of pmmm_plan_autotune: near-field kernel (0: from the config), tensor-core M2L system tile
+  int tuned_near = 0;
+  int m2l_tile = 64;
   // particle workspace
   int64_t cap = 0;
   SortWork sw{};

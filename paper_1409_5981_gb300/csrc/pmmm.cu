@@ -299,9 +299,9 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
   // near field: one thread per target when asked, or (automatic) when the cells
   // hold fewer than PMMM_NEAR_AUTO_OCCUPANCY particles on average
   const bool sparse = n < (int64_t)PMMM_NEAR_AUTO_OCCUPANCY * K;
+  const int near = pl->tuned_near ? pl->tuned_near : pl->cfg.near_field;
   const bool per_target = pp_per_target_applies(fp64, pl->g.c) &&
-                          (pl->cfg.near_field == PMMM_NEAR_PER_TARGET ||
-                           (pl->cfg.near_field == PMMM_NEAR_AUTO && sparse));
+                          (near == PMMM_NEAR_PER_TARGET || (near == PMMM_NEAR_AUTO && sparse));
 #define CK(x)                    \
   do {                           \
     e = (x);                     \
@@ -342,8 +342,8 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
       // specM -> specL (transposed) -> M2L -> specM -> specL (channel-major)
       CK(launch_transpose(fp64, pl->specM, pl->specL, R, pl->d.Kh, s, &nl));
       if (pl->m2l_tc)
-        CK(launch_m2l_tc(pl->specL, pl->G, pl->specM, pl->m2l_tab_tc, pl->p, B, pl->d.Kh, pl->num_sms, pl->err, s,
-                         &nl));
+        CK(launch_m2l_tc(pl->specL, pl->G, pl->specM, pl->m2l_tab_tc, pl->p, B, pl->d.Kh, pl->num_sms, pl->m2l_tile,
+                         pl->err, s, &nl));
       else
         CK(launch_m2l_batched(fp64, pl->specL, pl->G, pl->specM, pl->m2l_tab, pl->p, B, pl->d.Kh, s, &nl));
       CK(launch_transpose(fp64, pl->specM, pl->specL, pl->d.Kh, R, s, &nl));
@@ -768,6 +768,64 @@ int pmmm_compute_batched_graph(pmmm_plan* pl, int32_t nsys, const int64_t* offse
   return energies ? read_energies(pl, nsys, energies) : PMMM_OK;
 }
 
+int pmmm_plan_autotune(pmmm_plan* pl, int32_t nsys, const int64_t* offsets, const void* pos, const void* q,
+                       int32_t reps) {
+  if (!pl || nsys < 1 || nsys > PMMM_MAX_SYSTEMS || reps < 1 || reps > 100) return PMMM_ERR_INVALID_ARG;
+  int64_t n = 0;
+  int rc = PMMM_OK;
+  if (nsys > 1) {
+    if (pl->d.K * nsys > ((int64_t)1 << 30)) return PMMM_ERR_UNSUPPORTED;
+    rc = upload_offsets(pl, nsys, offsets, &n);
+  } else {
+    if (!offsets) return PMMM_ERR_INVALID_ARG;
+    n = offsets[1] - offsets[0];
+    if (offsets[0] != 0 || n < 0 || n > INT32_MAX) return PMMM_ERR_INVALID_ARG;
+  }
+  if (rc != PMMM_OK) return rc;
+  if (n > 0 && (!pos || !q)) return PMMM_ERR_INVALID_ARG;
+  std::vector<int> nears = {pl->tuned_near};
+  if (pp_per_target_applies(pl->fp64, pl->g.c)) nears = {PMMM_NEAR_CELL_ITEMS, PMMM_NEAR_PER_TARGET};
+  std::vector<int> tiles = {pl->m2l_tile};
+  if (pl->m2l_tc && nsys > 1) tiles = {64, 32};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return PMMM_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return PMMM_ERR_CUDA;
+  }
+  const bool timing = pl->timing;
+  pl->timing = false;
+  float best = 1e30f;
+  int best_near = pl->tuned_near, best_tile = pl->m2l_tile;
+  for (int nr : nears)
+    for (int tl : tiles) {
+      pl->tuned_near = nr;
+      pl->m2l_tile = tl;
+      rc = run(pl, nsys, n, pos, q, nullptr, nullptr);  // warm-up (allocates if needed)
+      cudaError_t ce = cudaSuccess;
+      if (rc == PMMM_OK) ce = cudaEventRecord(e0, pl->stream);
+      for (int r = 0; r < reps && rc == PMMM_OK && ce == cudaSuccess; ++r) rc = run(pl, nsys, n, pos, q, nullptr, nullptr);
+      if (rc == PMMM_OK && ce == cudaSuccess) ce = cudaEventRecord(e1, pl->stream);
+      if (rc == PMMM_OK && ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (rc == PMMM_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (rc == PMMM_OK && ce != cudaSuccess) rc = map_cuda(ce);
+      if (rc != PMMM_OK) break;
+      if (ms < best) {
+        best = ms;
+        best_near = nr;
+        best_tile = tl;
+      }
+    }
+  pl->tuned_near = best_near;
+  pl->m2l_tile = best_tile;
+  pl->timing = timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != PMMM_OK) return rc;
+  return read_device_status(pl);
+}
+
 int pmmm_plan_status(pmmm_plan* pl) {
   if (!pl) return PMMM_ERR_INVALID_ARG;
   cudaError_t e = cudaGetLastError();
@@ -856,6 +914,8 @@ int pmmm_plan_info(pmmm_plan* pl, int what, int64_t* value) {
     case PMMM_INFO_WORKSPACE_BYTES: *value = (int64_t)pl->ws_bytes; break;
     case PMMM_INFO_LAUNCHES: *value = pl->launches; break;
     case PMMM_INFO_SYSTEMS: *value = pl->nsys_last; break;
+    case PMMM_INFO_TUNED_NEAR: *value = pl->tuned_near; break;
+    case PMMM_INFO_M2L_TILE: *value = pl->m2l_tile; break;
     default: return PMMM_ERR_INVALID_ARG;
   }
   return PMMM_OK;

@@ -48,9 +48,13 @@ class Trainer:
         self.rows = sur.rows
 
     # ------------------------------------------------------------------ data
-    def calibrate(self, systems):
+    def calibrate(self, systems, common_output_scale: bool = False):
         """Input and output scales from the mean squares of the raw multipole and
-        target channels over the cells of `systems` ((pos, q) numpy pairs)."""
+        target channels over the cells of `systems` ((pos, q) numpy pairs).  With
+        common_output_scale every target channel gets the same scale: in the
+        device units L'_l = h^(l+1) L_l each order contributes to the field inside
+        a cell with comparable weight, so the loss then follows the force error
+        instead of weighting every order equally."""
         import torch
         stats = np.zeros(16 + self.sur.c_high)
         X = torch.empty((self.rows, I), dtype=torch.bfloat16, device="cuda")
@@ -63,7 +67,10 @@ class Trainer:
             cells += int(np.prod(self.sur.cfg.mesh))
         ms = np.maximum(stats / cells, 1e-30)
         self.in_scale = (1.0 / np.sqrt(ms[:16])).astype(np.float32)
-        self.out_scale = (1.0 / np.sqrt(ms[16:])).astype(np.float32)
+        if common_output_scale:
+            self.out_scale = np.full(ms.size - 16, 1.0 / math.sqrt(ms[16:].mean()), dtype=np.float32)
+        else:
+            self.out_scale = (1.0 / np.sqrt(ms[16:])).astype(np.float32)
         self.sur.set(SUR_IN_SCALE, self.in_scale)
         self.sur.set(SUR_OUT_SCALE, self.out_scale)
         return self.in_scale, self.out_scale

@@ -314,3 +314,27 @@ def test_batched_splitbf16_tensor_core_m2l(pk, p, boundary):
           f"(FP32 path {ef32:.2e}), phi {ep:.2e}")
     assert eL < 1e-4
     assert ef < SPLITBF16_TOL and ep < SPLITBF16_TOL
+
+
+def test_autotune_choices_are_equivalent(pk):
+    """pmmm_plan_autotune picks a near-field kernel and a tensor-core M2L tile by timing;
+    whatever it picks, the results agree with the untuned plan to rounding, and the
+    chosen configuration reproduces itself bit for bit."""
+    import torch
+    cfg = pk.Config(mesh=(8, 8, 8), p=5, boundary=pk.PERIODIC, precision=pk.FP32_SPLITBF16_M2L)
+    pos, q, off = _systems(pk, cfg, [1500, 700, 2600, 40, 900], 56)
+    counts = np.diff(off)
+    tp, tq = _t(pos, torch.float32), _t(q, torch.float32)
+    base = pk.Plan(cfg)
+    phi0, f0, e0 = base.compute_batched(counts, tp, tq, energies=True)
+    plan = pk.Plan(cfg)
+    near, tile = plan.autotune(counts, tp, tq, reps=2)
+    assert near in (pk.NEAR_CELL_ITEMS, pk.NEAR_PER_TARGET) and tile in (32, 64)
+    phi1, f1, e1 = plan.compute_batched(counts, tp, tq, energies=True)
+    phi2, f2, e2 = plan.compute_batched(counts, tp, tq, energies=True)
+    assert torch.equal(phi1, phi2) and torch.equal(f1, f2) and np.array_equal(e1, e2)
+    a, b = f1.double().cpu().numpy(), f0.double().cpu().numpy()
+    assert _rel(a, b) < 2e-6
+    print(f"autotune: near-field kernel {near}, M2L tile {tile}")
+    base.close()
+    plan.close()
