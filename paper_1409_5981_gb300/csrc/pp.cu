@@ -329,6 +329,47 @@ __device__ __forceinline__ void pp_pair2(const ulonglong2& A, const ulonglong2& 
   gz = fma2(qr3, dz, gz);
 }
 
+// The same two-source step with the arithmetic after the rsqrt in scalar FP32
+// (faster in the per-target kernel, whose lanes follow different neighbour
+// lists; the cell-item kernel is faster with the packed form above).
+template <bool SELF>
+__device__ __forceinline__ void pp_pair2_mixed(const ulonglong2& A, const ulonglong2& B, f2 tx, f2 ty, f2 tz, f2& pot,
+                                               f2& gx, f2& gy, f2& gz) {
+  const f2 dx = sub2(tx, A.x), dy = sub2(ty, A.y), dz = sub2(tz, B.x);
+  const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+  float a, b;
+  up2(r2, a, b);
+  float ra = rsqrtf(a), rb = rsqrtf(b);
+  if (SELF) {
+    ra = a > 0.f ? ra : 0.f;
+    rb = b > 0.f ? rb : 0.f;
+  }
+  float qa, qb, dxa, dxb, dya, dyb, dza, dzb;
+  up2(B.y, qa, qb);
+  up2(dx, dxa, dxb);
+  up2(dy, dya, dyb);
+  up2(dz, dza, dzb);
+  const float qra = qa * ra, qrb = qb * rb;
+  float p0, p1, x0, x1, y0, y1, z0, z1;
+  up2(pot, p0, p1);
+  up2(gx, x0, x1);
+  up2(gy, y0, y1);
+  up2(gz, z0, z1);
+  p0 += qra;
+  p1 += qrb;
+  const float ca = qra * (ra * ra), cb = qrb * (rb * rb);
+  x0 = fmaf(ca, dxa, x0);
+  y0 = fmaf(ca, dya, y0);
+  z0 = fmaf(ca, dza, z0);
+  x1 = fmaf(cb, dxb, x1);
+  y1 = fmaf(cb, dyb, y1);
+  z1 = fmaf(cb, dzb, z1);
+  pot = pk2(p0, p1);
+  gx = pk2(x0, x1);
+  gy = pk2(y0, y1);
+  gz = pk2(z0, z1);
+}
+
 template <bool SELF>
 __device__ __forceinline__ void pp_sum2(const ulonglong2* __restrict__ src, int npair, int ph, int SP, f2 tx, f2 ty,
                                         f2 tz, f2& pot, f2& gx, f2& gy, f2& gz) {
@@ -556,7 +597,8 @@ __global__ void __launch_bounds__(PPS_THREADS, 4) pp_target_kernel(
           const float txs = xi.x - (float)(d - 1) * csx;
           const f2 tx = pk2(txs, txs);
 #pragma unroll 1
-          for (int pr = pb; pr < pe; ++pr) pp_pair2<true>(S2[2 * pr], S2[2 * pr + 1], tx, ty, tz, pot, gx, gy, gz);
+          for (int pr = pb; pr < pe; ++pr)
+            pp_pair2_mixed<true>(S2[2 * pr], S2[2 * pr + 1], tx, ty, tz, pot, gx, gy, gz);
         }
       }
     }
