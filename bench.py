@@ -69,6 +69,8 @@ BATCHED = {
 # The specified set is 256 training and 32 held-out systems; the bench trains on a bounded sample.
 SURROGATE = {
     "periodic_surrogate_p3to10_n1048576_mesh32_fp32": (1 << 20, 32, 3, 10, 24, 8, 6),
+    # the specified training scale: 256 training and 32 held-out systems
+    "periodic_surrogate_full_p3to10_n1048576_mesh32_fp32": (1 << 20, 32, 3, 10, 256, 32, 4),
 }
 DEFAULT_WORKLOAD = "periodic_uniform_n1048576_mesh32_p7_fp32"
 METRIC = "particles/s per full force eval at fixed RMS force error; mesh-stage HBM % peak"
@@ -189,6 +191,21 @@ def _gpu_id(torch, dev):
     if vis:
         return vis.split(",")[dev].strip()
     return str(dev)
+
+
+def _max_over_ranks(values, world: int, device):
+    """Element-wise maximum of per-rank values (times) over all ranks; identity for one rank."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def _job_rate(world: int, units_per_rank: float, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank * steps / (total_ms * 1e-3)
 
 
 def _pairs(cs: np.ndarray, mesh: int, periodic: bool, c: int = 1) -> int:
@@ -420,14 +437,9 @@ def run_ours(args, rank, world, local_rank):
     sha = _src_sha(["paper_1409_5981_gb300/csrc/pp.cu"])
 
     # reduce over ranks: max time
-    tmax = total_ms
-    e2e_tot = sum(e2e_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms, e2e_tot], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        tmax, e2e_tot = float(tt[0]), float(tt[1])
-    value = world * n * args.steps / (tmax * 1e-3)
-    e2e_value = world * n * args.steps / (e2e_tot * 1e-3)
+    tmax, e2e_tot = _max_over_ranks([total_ms, sum(e2e_ms)], world, dev)
+    value = _job_rate(world, n, args.steps, tmax)
+    e2e_value = _job_rate(world, n, args.steps, e2e_tot)
     if rank != 0:
         return 0
 
@@ -609,12 +621,8 @@ def run_ours_batched(args, rank, world, local_rank):
     mesh_bytes = esz * nsys * (2 * C * K + 4 * 2 * C * Kh) + esz * 2 * CG * Kh
     m2l_bytes = esz * 2 * (2 * C * Kh * nsys + CG * Kh)
 
-    tmax, e2e_tot = total_ms, sum(e2e_ms) / len(e2e_ms) * args.steps
-    if world > 1:
-        tt = torch.tensor([total_ms, e2e_tot], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        tmax, e2e_tot = float(tt[0]), float(tt[1])
-    value = world * n * args.steps / (tmax * 1e-3)
+    tmax, e2e_tot = _max_over_ranks([total_ms, sum(e2e_ms) / len(e2e_ms) * args.steps], world, dev)
+    value = _job_rate(world, n, args.steps, tmax)
     if rank != 0:
         plan.close()
         return 0
@@ -656,7 +664,7 @@ def run_ours_batched(args, rank, world, local_rank):
                           "unit": "GB/s", "frac": mesh_bytes / (mesh_ms * 1e-3) / 1e9 / hbm,
                           "stages": "fft_forward + m2l + fft_inverse", "peak_kind": peak_kind,
                           "m2l_ms": stage.get("m2l"), "m2l_GBps": m2l_bytes / (stage.get("m2l", 1.0) * 1e-3) / 1e9},
-        "e2e": {"value": world * n / (statistics.median(e2e_ms) * 1e-3), "unit": UNIT,
+        "e2e": {"value": _job_rate(world, n, args.steps, e2e_tot), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * esz * n, "d2h_bytes_per_step": 4 * esz * n + 8 * nsys},
         "gpu_launches": launches * args.steps,
         "clocks": clocks,
@@ -748,10 +756,7 @@ def run_ours_surrogate(args, rank, world, local_rank):
                                                    force.data_ptr())), args.steps)
     t1w = time.time()
     sampler.stop()
-    if world > 1:
-        tt = torch.tensor([ms_user], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_user = float(tt[0])
+    ms_user = _max_over_ranks([ms_user], world, dev)[0]
     if rank != 0:
         return 0
     # end to end through the host-buffer ABI call of the method the user gets
@@ -770,14 +775,15 @@ def run_ours_surrogate(args, rank, world, local_rank):
         torch.cuda.synchronize()
         e2e.append(1e3 * (time.perf_counter() - t))
     line = {
-        "metric": METRIC, "value": world * n / (ms_user * 1e-3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": _job_rate(world, n, 1, ms_user), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_user, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16 mlp", "data": "synthetic",
         "config": {"workload": name, "n_particles": n, "boundary": "periodic", "mesh": [mesh] * 3, "p_low": p_lo,
                    "p_high": p_hi, "train_systems": ntrain, "held_out_systems": nheld, "epochs": epochs,
                    "batch": 8192, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas{world}",
-                   "sample": f"{ntrain} of the 256 specified training systems, {nheld} of the 32 held-out"},
+                   "sample": f"{ntrain} of the 256 specified training systems, {nheld} of the 32 held-out"
+                             if ntrain < 256 else "the specified 256 training and 32 held-out systems"},
         "fallback": bool(fallback),
         "held_out_rel_rms_force_err_vs_plain_p10": {"plain_p3": float(errs[:, 0].mean()),
                                                     "corrected": float(errs[:, 1].mean()),
