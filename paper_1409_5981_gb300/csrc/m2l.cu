@@ -11,7 +11,7 @@ namespace pmmm {
 namespace {
 
 template <int P, typename T>
-__global__ void __launch_bounds__(128) m2l_kernel(const cpx<T>* __restrict__ Mt, const cpx<T>* __restrict__ Gt,
+__global__ void __launch_bounds__(128, (P <= 7 ? 4 : 1)) m2l_kernel(const cpx<T>* __restrict__ Mt, const cpx<T>* __restrict__ Gt,
                                                   cpx<T>* __restrict__ Lt, int64_t Kh, int nsys, int p) {
   const int l = blockIdx.y;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

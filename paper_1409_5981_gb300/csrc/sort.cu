@@ -123,19 +123,26 @@ __global__ void scan_top_kernel(uint32_t* __restrict__ sums, int nchunks) {
 
 // Stable scatter of one radix pass.  Warp w of a tile owns keys
 // [w*256, (w+1)*256) of the tile, visited in 8 rounds of 32 in index order, so
-// that ranks among equal digits follow the input order.
+// that ranks among equal digits follow the input order.  The tile is first
+// grouped by digit in shared memory (stable), then written out position by
+// position, so that keys of one digit leave as one contiguous run.
 __global__ void radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                      uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
                                      int nbits, const uint32_t* __restrict__ hist, const uint32_t* __restrict__ chunks,
                                      int ntiles) {
   __shared__ uint32_t whist[RS_WARPS][256];
   __shared__ uint32_t gbase[256];
+  __shared__ uint32_t tdo[256];  // first tile position of each digit
+  __shared__ uint32_t wtot[RS_WARPS];
+  __shared__ uint32_t sk[RS_TILE], sv[RS_TILE];
   const int radix = 1 << nbits;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < RS_WARPS * 256; t += RS_THREADS) (&whist[0][0])[t] = 0;
   __syncthreads();
   const uint32_t lt = (1u << lane) - 1u;
-  const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (32 * RS_ITEMS);
+  const int64_t tbase = (int64_t)blockIdx.x * RS_TILE;
+  const int64_t wbase = tbase + (int64_t)warp * (32 * RS_ITEMS);
+  const int tcount = (int)min((int64_t)RS_TILE, n - tbase);
   uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
   int dig[RS_ITEMS];
 #pragma unroll
@@ -156,26 +163,48 @@ __global__ void radix_scatter_kernel(const uint32_t* __restrict__ kin, const uin
     dig[r] = d;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < radix; t += RS_THREADS) {
-    uint32_t run = 0;
+  // per digit: exclusive offsets of the warps, the tile total, the global base
+  const int t = threadIdx.x;  // RS_THREADS == 256 >= radix: one digit per thread
+  uint32_t total = 0;
+  if (t < radix) {
 #pragma unroll
     for (int w = 0; w < RS_WARPS; ++w) {
       const uint32_t c = whist[w][t];
-      whist[w][t] = run;
-      run += c;
+      whist[w][t] = total;
+      total += c;
     }
     const int64_t idx = (int64_t)t * ntiles + blockIdx.x;
     gbase[t] = hist[idx] + chunks[idx / SCAN_CH];
   }
+  // exclusive scan of the digit totals over the block -> tdo
+  uint32_t incl = total;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wtot[warp] = incl;
+  __syncthreads();
+  uint32_t woff = 0;
+  for (int w = 0; w < warp; ++w) woff += wtot[w];
+  tdo[t] = woff + incl - total;
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < RS_ITEMS; ++r) {
     const int d = dig[r];
     if (d < radix) {
-      const uint32_t dst = gbase[d] + whist[warp][d] + rank[r];
-      kout[dst] = key[r];
-      vout[dst] = val[r];
+      const uint32_t lp = tdo[d] + whist[warp][d] + rank[r];
+      sk[lp] = key[r];
+      sv[lp] = val[r];
     }
+  }
+  __syncthreads();
+  for (int j = t; j < tcount; j += RS_THREADS) {
+    const uint32_t k = sk[j];
+    const int d = (int)((k >> shift) & (uint32_t)(radix - 1));
+    const uint32_t dst = gbase[d] + ((uint32_t)j - tdo[d]);
+    kout[dst] = k;
+    vout[dst] = sv[j];
   }
 }
 
