@@ -43,8 +43,9 @@ constexpr int TC_NMAX = 64;                           // largest system tile (GE
 constexpr uint32_t TC_LBO = 128;                      // next core matrix along K
 constexpr uint32_t TC_SBO = (TC_K / 8) * 128;         // next 8-row group: 2048 B
 constexpr uint32_t TC_A_BYTES = 128 * TC_K * 2;       // one split of W: 32 KB
-constexpr uint32_t TC_GK_BYTES = 2048;                // (2p+1)^2 <= 225 complex
-constexpr uint32_t TC_TAB_BYTES = TC_CH * TC_CH * 4;  // packed entry table, 16 KB
+constexpr uint32_t TC_GK_BYTES = 2 * 2048;            // (2p+1)^2 <= 225 complex, two wavevectors
+constexpr int TC_TAB_ROW = TC_CH + 4;                 // table row stride (words): 17 chunks of 16 B
+constexpr uint32_t TC_TAB_BYTES = TC_CH * TC_TAB_ROW * 4;  // packed entry table, 17 KB
 // per system tile NT (32 or 64): X splits, stage, shared-memory offsets, TMEM columns
 template <int NT>
 struct TcTile {
@@ -97,6 +98,10 @@ __device__ __forceinline__ uint32_t chunk_off(int r, int g) {
   return (uint32_t)(r >> 3) * TC_SBO + (uint32_t)g * TC_LBO + (uint32_t)(r & 7) * 16;
 }
 
+__device__ __forceinline__ void cp8(uint32_t saddr, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(saddr), "l"(g) : "memory");
+}
+
 // Entry table packing: i1 | (s1 + 1) << 10 | i2 << 12 | (s2 + 1) << 22
 template <int NT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                   int* __restrict__ err) {
   using Tl = TcTile<NT>;
   extern __shared__ __align__(1024) unsigned char smem[];
-  float2* gk = reinterpret_cast<float2*>(smem + Tl::OFF_GK);
+  float2* gkb = reinterpret_cast<float2*>(smem + Tl::OFF_GK);  // [2][256]: kernel spectra of k and k + 1
   uint32_t* tab = reinterpret_cast<uint32_t*>(smem + Tl::OFF_TAB);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Tl::OFF_BAR);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Tl::OFF_BAR + 16);
@@ -116,7 +121,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int nmma = (nb + 15) & ~15;  // GEMM N: systems padded to a multiple of 16
   const int64_t kbeg = (int64_t)blockIdx.x * kchunk, kend = min(Kh, kbeg + kchunk);
 
-  for (int i = tid; i < TC_CH * TC_CH; i += TC_THREADS) tab[i] = tab_g[i];
+  for (int i = tid; i < TC_CH * TC_CH; i += TC_THREADS) tab[(i / TC_CH) * TC_TAB_ROW + i % TC_CH] = tab_g[i];
+  // kernel spectra of the first wavevector (asynchronous copies, 8 bytes each)
+  auto fetch_gk = [&](int64_t kk, int slot) {
+    if (kk < kend)
+      for (int s = tid; s < CG; s += TC_THREADS) cp8(smem_u32(gkb + 256 * slot + s), Gt + (int64_t)s * Kh + kk);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  fetch_gk(kbeg, 0);
   if (tid == 0) {
     tc::bar_init(smem_u32(&bars[0]), 1);
     tc::bar_init(smem_u32(&bars[1]), 1);
@@ -168,16 +180,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   for (int64_t k = kbeg; k < kend; ++k, ++it) {
     const int buf = it & 1;
     unsigned char* st = smem + buf * Tl::STAGE;
-    // kernel spectra of this wavevector
-    for (int s = tid; s < CG; s += TC_THREADS) gk[s] = Gt[(int64_t)s * Kh + k];
+    // this wavevector's kernel spectra were fetched one iteration ahead; start the next fetch
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-    // W: unit (output channel co, K-group kg of 8 input channels) -> rows 2co, 2co+1
+    const float2* gk = gkb + 256 * (it & 1);
+    fetch_gk(k + 1, (it + 1) & 1);
+    // X loads first (their latency is covered by the W assembly below)
+    float2 xm[(NT * 8 + TC_THREADS - 1) / TC_THREADS][8];
+#pragma unroll
+    for (int q = 0; q < (NT * 8 + TC_THREADS - 1) / TC_THREADS; ++q) {
+      const int u = tid + q * TC_THREADS;
+      const int n = (u & 7) + 8 * (u >> 6), cg = (u >> 3) & 7;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int ci = cg * 8 + j;
+        xm[q][j] = make_float2(0.f, 0.f);
+        if (u < NT * 8 && n < nb && ci < C) xm[q][j] = __ldg(Mt + (k * C + ci) * B + b0 + n);
+      }
+    }
+    // W: unit (output channel co, K-group kg of 8 input channels) -> rows 2co, 2co+1; eight
+    // consecutive threads take eight consecutive channels, whose padded table rows start on
+    // different banks
     for (int u = tid; u < TC_CH * 8; u += TC_THREADS) {
-      const int kg = (u >> 2) & 7, co = (u & 3) + 4 * (u >> 5);
+      const int co = (u & 7) + 8 * (u >> 6), kg = (u >> 3) & 7;
       float ar[8], ai[8];
       uint32_t tv[8];
-      *reinterpret_cast<uint4*>(tv) = *reinterpret_cast<const uint4*>(tab + co * TC_CH + kg * 8);
-      *reinterpret_cast<uint4*>(tv + 4) = *reinterpret_cast<const uint4*>(tab + co * TC_CH + kg * 8 + 4);
+      *reinterpret_cast<uint4*>(tv) = *reinterpret_cast<const uint4*>(tab + co * TC_TAB_ROW + kg * 8);
+      *reinterpret_cast<uint4*>(tv + 4) = *reinterpret_cast<const uint4*>(tab + co * TC_TAB_ROW + kg * 8 + 4);
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const uint32_t t = tv[j];
@@ -201,16 +230,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       *reinterpret_cast<uint4*>(Al + chunk_off(2 * co + 1, 8 + kg)) = rl;
     }
     // X: unit (system n, K-group cg of 8 channels) -> row n, K-groups cg (Re) and 8 + cg (Im)
-    for (int u = tid; u < NT * 8; u += TC_THREADS) {
+#pragma unroll
+    for (int q = 0; q < (NT * 8 + TC_THREADS - 1) / TC_THREADS; ++q) {
+      const int u = tid + q * TC_THREADS;
+      if (u >= NT * 8) break;
       const int n = (u & 7) + 8 * (u >> 6), cg = (u >> 3) & 7;
       float xr[8], xi[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const int ci = cg * 8 + j;
-        float2 m = make_float2(0.f, 0.f);
-        if (n < nb && ci < C) m = __ldg(Mt + (k * C + ci) * B + b0 + n);
-        xr[j] = m.x;
-        xi[j] = m.y;
+        xr[j] = xm[q][j].x;
+        xi[j] = xm[q][j].y;
       }
       uint4 rh, rl, ih, il;
       split8(xr, rh, rl);
@@ -251,6 +280,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (ok && kprev >= 0) {
     if (!drain((it - 1) & 1, kprev, (uint32_t)(((it - 1) >> 1) & 1))) atomicExch(abort_flag, 1);
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   if (*abort_flag) {
     if (tid == 0) set_err(err, ERRBIT_TIMEOUT);
