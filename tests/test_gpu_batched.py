@@ -338,3 +338,20 @@ def test_autotune_choices_are_equivalent(pk):
     print(f"autotune: near-field kernel {near}, M2L tile {tile}")
     base.close()
     plan.close()
+
+
+def test_batched_degenerate_batches(pk):
+    """A batch of one system equals pmmm_compute bit for bit; a batch of empty systems
+    gives zero energies and no particles."""
+    import torch
+    cfg = pk.Config(mesh=(8, 8, 8), p=4, boundary=pk.PERIODIC, precision=pk.FP32)
+    pos, q, off = _systems(pk, cfg, [2345], 57)
+    plan = pk.Plan(cfg)
+    phi_b, f_b, e_b = plan.compute_batched([2345], _t(pos, torch.float32), _t(q, torch.float32), energies=True)
+    phi_s, f_s, e_s = plan.compute(_t(pos, torch.float32), _t(q, torch.float32), energy=True)
+    assert torch.equal(phi_b, phi_s) and torch.equal(f_b, f_s) and e_b[0] == e_s
+    empty = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    phi0, f0, e0 = plan.compute_batched([0, 0, 0], empty, torch.zeros(0, dtype=torch.float32, device="cuda"),
+                                        energies=True)
+    assert phi0.numel() == 0 and np.array_equal(e0, np.zeros(3))
+    plan.close()
