@@ -346,6 +346,14 @@ int pmmm_surrogate_train_step(pmmm_surrogate* s, const void* X, const float* T, 
 int pmmm_surrogate_compute(pmmm_surrogate* s, int64_t n, const void* pos, const void* q, void* phi, void* force,
                            double* energy);
 
+/* Diagnostic of the failure detection (the paper has no counterpart): launches
+ * one kernel that waits, with the same bounded mbarrier wait as the
+ * tensor-core kernels (here at most `polls` polls, 1..2^24), on a barrier that
+ * nothing arrives at.  The wait gives up, the kernel raises the device error
+ * flag and returns, and the call returns PMMM_ERR_TIMEOUT with the CUDA context
+ * still usable.  Synchronises the stream. */
+int pmmm_selftest_wait_timeout(void* cuda_stream, int64_t polls);
+
 /* Human-readable name of a status code (static string). */
 const char* pmmm_strerror(int status);
 

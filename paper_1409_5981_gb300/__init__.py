@@ -91,6 +91,7 @@ _SIGS = {
     "pmmm_bin_sort_static": (ctypes.c_int, [ctypes.POINTER(_Config), ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p]),
     "pmmm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pmmm_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "pmmm_surrogate_create": (ctypes.c_int, [ctypes.POINTER(_Config), ctypes.c_int32, ctypes.c_void_p,
                                              ctypes.POINTER(ctypes.c_void_p)]),
     "pmmm_surrogate_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -152,6 +153,14 @@ def bin_sort_static(cfg: Config, pos, perm, cell_start, stream=None) -> int:
     return int(_lib().pmmm_bin_sort_static(ctypes.byref(c), n, ctypes.c_void_p(pos.data_ptr()),
                                            ctypes.c_void_p(perm.data_ptr()), ctypes.c_void_p(cell_start.data_ptr()),
                                            ctypes.c_void_p(stream.cuda_stream)))
+
+
+def selftest_wait_timeout(polls: int = 1 << 16, stream=None) -> int:
+    """pmmm_selftest_wait_timeout: a bounded device-side wait that runs out; returns the status."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(_lib().pmmm_selftest_wait_timeout(ctypes.c_void_p(stream.cuda_stream), int(polls)))
 
 
 def stage_names():

@@ -337,3 +337,35 @@ cudaError_t launch_m2l_tc(const void* Mt, const void* Gt, void* Lt, const uint32
 }
 
 }  // namespace pmmm
+
+namespace pmmm {
+namespace {
+// One thread waits on an mbarrier that expects an arrival nobody makes, with the
+// bounded wait of the tensor-core kernels; the timeout raises the error flag.
+__global__ void wait_timeout_kernel(long long polls, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  tc::bar_init(tc::smem_u32(&bar), 1);
+  if (!tc::bar_wait(tc::smem_u32(&bar), 0, polls)) set_err(err, ERRBIT_TIMEOUT);
+}
+}  // namespace
+}  // namespace pmmm
+
+extern "C" int pmmm_selftest_wait_timeout(void* cuda_stream, int64_t polls) {
+  using namespace pmmm;
+  if (polls < 1 || polls > (int64_t)1 << 24) return PMMM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int* err = nullptr;
+  cudaError_t e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    wait_timeout_kernel<<<1, 32, 0, s>>>(polls, err);
+    e = cudaGetLastError();
+  }
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (err) cudaFree(err);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? PMMM_ERR_OOM : PMMM_ERR_CUDA;
+  return (h & ERRBIT_TIMEOUT) ? PMMM_ERR_TIMEOUT : PMMM_OK;
+}

@@ -49,15 +49,17 @@ __device__ __forceinline__ void bar_init(uint32_t bar, int count) {
 }
 
 // Bounded wait for the phase of the given parity; false after `limit` polls.
+// Each poll suspends the thread for at most 1 us (it resumes as soon as the
+// phase completes), so `limit` polls bound the wait to about limit microseconds.
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, long long limit) {
   for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(1000)
         : "memory");
     if (done) return true;
   }

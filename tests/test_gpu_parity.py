@@ -385,3 +385,18 @@ def test_sparse_p2m_fp32_vs_oracle(pk):
     corr = plan.export(pk.EXPORT_CORR)
     assert np.allclose(corr[:5], ref["corr"][:5], rtol=1e-5, atol=1e-5)
     plan.close()
+
+
+def test_bounded_wait_times_out_and_context_survives(pk):
+    """Failure detection without a GPU fault: a device-side wait on a barrier that
+    nothing arrives at gives up after its poll limit, the call reports
+    PMMM_ERR_TIMEOUT, and the same CUDA context still evaluates correctly."""
+    import torch
+    assert pk.selftest_wait_timeout(1 << 14) == pk.ERR_TIMEOUT
+    pos, q = synth.uniform_pm1(2000, synth.seed(1, 36))
+    cfg = pk.Config(mesh=(8, 8, 8), p=3, boundary=pk.OPEN, precision=pk.FP64)
+    plan, phi, force, energy = _run(pk, cfg, pos, q)
+    ref = _oracle(cfg, pk, pos, q)
+    assert _rel(force, -(q[:, None] * ref["grad"])) < FP64_TOL
+    assert plan.status() == pk.OK
+    plan.close()
