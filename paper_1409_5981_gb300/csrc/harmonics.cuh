@@ -55,6 +55,42 @@ PMMM_HD void regular_real(T x, T y, T z, T* X) {
   }
 }
 
+// The same regular harmonics streamed column by column (m = 0..P, then
+// l = m..P) to a callback f(l, m, Re R_l^m, Im R_l^m), keeping only the two
+// previous rows of the current column: O(P) registers.
+template <int P, typename T, class F>
+PMMM_HD void regular_stream(T x, T y, T z, F&& f) {
+  const T r2 = x * x + y * y + z * z;
+  T mmr = T(1), mmi = T(0);
+#pragma unroll
+  for (int m = 0; m <= P; ++m) {
+    if (m > 0) {
+      const T s = T(-1) / T(2 * m);
+      const T nr = s * (x * mmr - y * mmi);
+      const T ni = s * (x * mmi + y * mmr);
+      mmr = nr;
+      mmi = ni;
+    }
+    f(m, m, mmr, mmi);
+    T ar = mmr, ai = mmi, br = T(0), bi = T(0);
+    if (m + 1 <= P) {
+      br = z * mmr;
+      bi = z * mmi;
+      f(m + 1, m, br, bi);
+    }
+#pragma unroll
+    for (int l = m + 2; l <= P; ++l) {
+      const T c1 = T(2 * l - 1) / T((l - m) * (l + m));
+      const T c2 = T(1) / T((l - m) * (l + m));
+      const T cr = c1 * z * br - c2 * r2 * ar;
+      const T ci = c1 * z * bi - c2 * r2 * ai;
+      f(l, m, cr, ci);
+      ar = br; ai = bi;
+      br = cr; bi = ci;
+    }
+  }
+}
+
 // Singular harmonics S_l^m for one m >= 0 and l = m .. J, handed to a callback
 // f(l, Re S_l^m, Im S_l^m).  Runtime orders (used by the Green function set-up).
 template <typename T, typename F>

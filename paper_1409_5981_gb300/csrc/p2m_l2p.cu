@@ -16,6 +16,24 @@ template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; };
 template <> struct V4<double> { using type = double4; };
 
+// acc += q R(-u): the harmonics streamed column by column up to order 8 (fewer
+// registers); above, the (p+1)^2 array form (measured faster there).
+template <int P, typename T>
+__device__ __forceinline__ void p2m_accumulate(T ux, T uy, T uz, T q, T* acc) {
+  constexpr int C = (P + 1) * (P + 1);
+  if constexpr (P <= 8) {
+    regular_stream<P, T>(-ux, -uy, -uz, [&](int l, int m, T re, T im) {
+      acc[sidx(l, m)] = fma(q, re, acc[sidx(l, m)]);
+      if (m > 0) acc[sidx(l, -m)] = fma(q, im, acc[sidx(l, -m)]);
+    });
+  } else {
+    T R[C];
+    regular_real<P, T>(-ux, -uy, -uz, R);
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = fma(q, R[c], acc[c]);
+  }
+}
+
 // Eight lanes per cell: each lane accumulates q R(r_M - r_i) = q R(-u) of every
 // eighth particle of its cell into (p+1)^2 registers, a 3-step butterfly sums the
 // eight lanes, and a shared-memory transpose writes the channel-major M of 32
@@ -40,10 +58,7 @@ __global__ void __launch_bounds__(256) p2m_kernel(const T* __restrict__ part, co
     const int beg = cs[cell], end = cs[cell + 1];
     for (int i = beg + sub; i < end; i += P2M_LPC) {
       const typename V4<T>::type r = reinterpret_cast<const typename V4<T>::type*>(part)[i];
-      T R[C];
-      regular_real<P, T>(-r.x, -r.y, -r.z, R);
-#pragma unroll
-      for (int c = 0; c < C; ++c) acc[c] = fma(r.w, R[c], acc[c]);
+      p2m_accumulate<P, T>(r.x, r.y, r.z, r.w, acc);
       sq += r.w;
       sx = fma(r.w, r.x, sx);
       sy = fma(r.w, r.y, sy);
@@ -102,10 +117,7 @@ __global__ void __launch_bounds__(256) p2m_cell_kernel(const T* __restrict__ par
   T sq = 0, sx = 0, sy = 0, sz = 0, sr = 0;
   auto accumulate = [&](int i) {
     const typename V4<T>::type r = reinterpret_cast<const typename V4<T>::type*>(part)[i];
-    T R[C];
-    regular_real<P, T>(-r.x, -r.y, -r.z, R);
-#pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = fma(r.w, R[c], acc[c]);
+    p2m_accumulate<P, T>(r.x, r.y, r.z, r.w, acc);
     sq += r.w;
     sx = fma(r.w, r.x, sx);
     sy = fma(r.w, r.y, sy);
@@ -174,10 +186,15 @@ __global__ void __launch_bounds__(128) l2p_kernel(const T* __restrict__ part, co
   const typename V4<T>::type r = reinterpret_cast<const typename V4<T>::type*>(part)[i];
   const int64_t cell = keys[i];
   const double* corr = corr_all + 16 * (cell / cp.ksys);  // this particle's system
-  T R[C];
-  regular_real<P, T>(r.x, r.y, r.z, R);
   T f, gx, gy, gz;
-  l2p_real<P, T>([&](int c) { return __ldg(L + (int64_t)c * K + cell); }, R, f, gx, gy, gz);
+  if constexpr (P >= 9) {
+    // high orders: harmonics streamed column by column (no (p+1)^2 array)
+    l2p_stream<P, T>([&](int c) { return __ldg(L + (int64_t)c * K + cell); }, r.x, r.y, r.z, f, gx, gy, gz);
+  } else {
+    T R[C];
+    regular_real<P, T>(r.x, r.y, r.z, R);
+    l2p_real<P, T>([&](int c) { return __ldg(L + (int64_t)c * K + cell); }, R, f, gx, gy, gz);
+  }
   const T ih = (T)cp.ih, ih2 = (T)cp.ih2;
   T phi = f * ih;
   T g[3] = {gx * ih2, gy * ih2, gz * ih2};

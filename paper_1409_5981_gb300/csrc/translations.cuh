@@ -172,4 +172,79 @@ PMMM_HD void l2p_real(LL&& Lc, const T* R, T& phi, T& gx, T& gy, T& gz) {
   gz = l10;
 }
 
+// L2P and its gradient (same sums as l2p_real) with the regular harmonics of
+// r - r_L computed on the fly column by column (recurrences of App. A.6): only
+// the current column R_l^m and the previous one R_l^{m-1} are kept, so the
+// register count grows as O(P) instead of O(P^2).  At column m, row l:
+//   potential      L_l^m R_l^m
+//   L'_1^0 term    L_l^m R_{l-1}^m                        (m <= l-1)
+//   L'_1^1 terms   L_l^m R_{l-1}^{m-1}                    (m >= 1)
+//                  -conj(L_l^{m-1} R_{l-1}^m)             (m >= 1, l >= m+1)
+template <int P, typename T, class LL>
+PMMM_HD void l2p_stream(LL&& Lc, T x, T y, T z, T& phi, T& gx, T& gy, T& gz) {
+  const T r2 = x * x + y * y + z * z;
+  T pr[P + 1], pi[P + 1], cr[P + 1], ci[P + 1];
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    pr[l] = pi[l] = cr[l] = ci[l] = T(0);
+  }
+  T f = T(0), l10 = T(0), l11r = T(0), l11i = T(0);
+  T mmr = T(1), mmi = T(0);
+#pragma unroll
+  for (int m = 0; m <= P; ++m) {
+    if (m > 0) {
+      const T s = T(-1) / T(2 * m);
+      const T nr = s * (x * mmr - y * mmi);
+      const T ni = s * (x * mmi + y * mmr);
+      mmr = nr;
+      mmi = ni;
+    }
+#pragma unroll
+    for (int l = m; l <= P; ++l) {
+      T rr, ri;
+      if (l == m) {
+        rr = mmr;
+        ri = mmi;
+      } else if (l == m + 1) {
+        rr = z * cr[l - 1];
+        ri = z * ci[l - 1];
+      } else {
+        const T c1 = T(2 * l - 1) / T((l - m) * (l + m));
+        const T c2 = T(1) / T((l - m) * (l + m));
+        rr = c1 * z * cr[l - 1] - c2 * r2 * cr[l - 2];
+        ri = c1 * z * ci[l - 1] - c2 * r2 * ci[l - 2];
+      }
+      const T Lr = Lc(sidx(l, m)), Li = (m > 0) ? Lc(sidx(l, -m)) : T(0);
+      if (m == 0) {
+        f += Lr * rr;
+        if (l >= 1) l10 += Lr * cr[l - 1];
+      } else {
+        f += T(2) * (Lr * rr - Li * ri);
+        if (l >= m + 1) l10 += T(2) * (Lr * cr[l - 1] - Li * ci[l - 1]);
+        // L_l^m R_{l-1}^{m-1}
+        const T qr = pr[l - 1], qi = (m > 1) ? pi[l - 1] : T(0);
+        l11r += Lr * qr - Li * qi;
+        l11i += Lr * qi + Li * qr;
+        if (l >= m + 1) {
+          // -conj(L_l^{m-1} R_{l-1}^m)
+          const T Mr = Lc(sidx(l, m - 1)), Mi = (m > 1) ? Lc(sidx(l, -(m - 1))) : T(0);
+          l11r -= Mr * cr[l - 1] - Mi * ci[l - 1];
+          l11i += Mr * ci[l - 1] + Mi * cr[l - 1];
+        }
+      }
+      cr[l] = rr;
+      ci[l] = ri;
+    }
+#pragma unroll
+    for (int l = m; l <= P; ++l) {
+      pr[l] = cr[l];
+      pi[l] = ci[l];
+    }
+  }
+  phi = f;
+  gx = -l11r;
+  gy = l11i;
+  gz = l10;
+}
+
 }  // namespace pmmm

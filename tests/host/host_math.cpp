@@ -46,6 +46,29 @@ static void l2p_dispatch(int p, const double* L, const double* u, double* out) {
   if constexpr (P < PMMM_PMAX) l2p_dispatch<P + 1>(p, L, u, out);
 }
 
+template <int P>
+static void l2p_stream_dispatch(int p, const double* L, const double* u, double* out) {
+  if (p == P) {
+    double f, gx, gy, gz;
+    l2p_stream<P, double>([&](int c) { return L[c]; }, u[0], u[1], u[2], f, gx, gy, gz);
+    out[0] = f; out[1] = gx; out[2] = gy; out[3] = gz;
+    return;
+  }
+  if constexpr (P < PMMM_PMAX) l2p_stream_dispatch<P + 1>(p, L, u, out);
+}
+
+template <int P>
+static void reg_stream_dispatch(int p, double x, double y, double z, double* out) {
+  if (p == P) {
+    regular_stream<P, double>(x, y, z, [&](int l, int m, double re, double im) {
+      out[sidx(l, m)] = re;
+      if (m > 0) out[sidx(l, -m)] = im;
+    });
+    return;
+  }
+  if constexpr (P < PMMM_PMAX) reg_stream_dispatch<P + 1>(p, x, y, z, out);
+}
+
 template <typename T>
 static void fft_run(int L, int inverse, double* data) {
   FftPlan1D pl = make_fft_plan(L);
@@ -85,6 +108,8 @@ void h_fft(int L, int inverse, int single, double* data) {
 }
 void h_m2l_k(int p, const double* M, const double* G, double* L) { m2l_dispatch<0>(p, M, G, L); }
 void h_l2p(int p, const double* L, const double* u, double* out) { l2p_dispatch<0>(p, L, u, out); }
+void h_l2p_stream(int p, const double* L, const double* u, double* out) { l2p_stream_dispatch<0>(p, L, u, out); }
+void h_regular_stream(int p, double x, double y, double z, double* out) { reg_stream_dispatch<0>(p, x, y, z, out); }
 // L = A M with A built from the entry table (complex k-space values)
 void h_m2l_table(int p, const double* M, const double* G, double* L) {
   const int C = (p + 1) * (p + 1);

@@ -36,6 +36,8 @@ def lib():
     L.h_m2l_k.argtypes = [i, vp, vp, vp]
     L.h_l2p.argtypes = [i, vp, vp, vp]
     L.h_m2l_table.argtypes = [i, vp, vp, vp]
+    L.h_l2p_stream.argtypes = [i, vp, vp, vp]
+    L.h_regular_stream.argtypes = [i, d, d, d, vp]
     return L
 
 
@@ -159,6 +161,27 @@ def test_l2p_real_form_vs_oracle(lib):
         assert abs(out[0] - phi) < 1e-12 * max(1, abs(phi))
         if p >= 1:
             assert np.abs(out[1:] - grad).max() < 1e-12 * max(1, np.abs(grad).max())
+
+
+def test_streamed_harmonics_and_l2p_vs_oracle(lib):
+    """Column-by-column harmonics equal the oracle's R_l^m; the streamed L2P (harmonics
+    on the fly, two columns kept) equals the oracle's L2P and gradient."""
+    g = synth.rng(108)
+    for p in (0, 1, 2, 3, 7, 11, 12):
+        for _ in range(3):
+            r = g.standard_normal(3) * 0.6
+            out = np.zeros((p + 1) ** 2)
+            lib.h_regular_stream(p, *r, P(out))
+            ref = oracle.to_real_storage(oracle.solid_R(p, r))
+            assert np.abs(out - ref).max() <= 1e-14 * max(1.0, np.abs(ref).max()), p
+            Lc, Lr = _hermitian_real_storage(p, g)
+            u = g.random(3) - 0.5
+            res = np.zeros(4)
+            lib.h_l2p_stream(p, P(np.ascontiguousarray(Lr)), P(np.ascontiguousarray(u)), P(res))
+            phi, grad = oracle.l2p(p, Lc, u)
+            assert abs(res[0] - phi) < 1e-12 * max(1, abs(phi)), p
+            if p >= 1:
+                assert np.abs(res[1:] - grad).max() < 1e-12 * max(1, np.abs(grad).max()), p
 
 
 def test_m2l_entry_table_matches_per_k_m2l(lib):
