@@ -52,6 +52,9 @@ WORKLOADS = {
     "periodic_uniform_n16777216_mesh64_p7_fp64": (1 << 24, "periodic", 64, 7, "fp64", (0, 0, 0), (1, 1, 1),
                                                    "uniform_pm1", 1.0),
     "open_uniform_n4096_mesh8_p4_fp64": (4096, "open", 8, 4, "fp64", (0, 0, 0), (1, 1, 1), "uniform_pm1", 1.0),
+    # c = 2 (125 near cells, the paper's recommended cutoff): lower p for the same accuracy
+    "periodic_uniform_n1048576_mesh32_p5_c2_fp32": (1 << 20, "periodic", 32, 5, "fp32", (0, 0, 0), (1, 1, 1),
+                                                    "uniform_pm1", 1.0, 2),
     # same particle density as the default (32 per cell), 8x smaller: the ncu profiling case
     "periodic_uniform_n131072_mesh16_p7_fp32": (1 << 17, "periodic", 16, 7, "fp32", (0, 0, 0), (1, 1, 1),
                                                  "uniform_pm1", 1.0),
@@ -83,8 +86,14 @@ NUM_SMS = 152
 L2_FLUSH_BYTES = 256 << 20
 
 
+def _wl(name: str):
+    """(n, boundary, mesh, p, precision, box lo, box length, generator, sign, cutoff) of a workload."""
+    w = WORKLOADS[name]
+    return tuple(w) + ((1,) if len(w) == 9 else ())
+
+
 def _inputs(name: str, rank: int):
-    n, boundary, mesh, p, prec, lo, ln, gen, sign = WORKLOADS[name]
+    n, boundary, mesh, p, prec, lo, ln, gen, sign, cut = _wl(name)
     s = synth.seed(2, 100 * rank)
     if gen == "uniform_pm1":
         pos, q = synth.uniform_pm1(n, s, lo, ln)
@@ -232,7 +241,7 @@ def _cpu_baseline(name: str, pos, q, g, budget_s: float = 20.0):
     workload: its Green-function table g (set-up, untimed like the GPU plan), then one
     evaluation restricted to a seeded sample of target cells, timed."""
     import oracle
-    n, boundary, mesh, p, prec, lo, ln, gen, sign = WORKLOADS[name]
+    n, boundary, mesh, p, prec, lo, ln, gen, sign, cut = _wl(name)
     per = boundary == "periodic"
     ncell = 8
     t_one = None
@@ -240,7 +249,7 @@ def _cpu_baseline(name: str, pos, q, g, budget_s: float = 20.0):
     while True:
         cells = rng.choice(mesh ** 3, size=ncell, replace=False)
         t0 = time.perf_counter()
-        r = oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, 1, per, target_cells=cells, green=g)
+        r = oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, cut, per, target_cells=cells, green=g)
         dt = time.perf_counter() - t0
         done = int((~np.isnan(r["phi"])).sum())
         if dt >= 0.5 * budget_s or ncell >= mesh ** 3:
@@ -272,21 +281,21 @@ def run_reference(args, rank, world):
         nsys, lo_e, hi_e, mesh, p, prec = BATCHED[name]
         posb, qb, off = _batched_inputs(name, 0)
         n, boundary, lo, ln = int(off[-1]), "periodic", (0, 0, 0), (1, 1, 1)
-        per = True
+        per, cut = True, 1
         systems = [(posb[off[s]:off[s + 1]], qb[off[s]:off[s + 1]]) for s in range(nsys)]
     else:
-        n, boundary, mesh, p, prec, lo, ln, gen, sign = WORKLOADS[name]
+        n, boundary, mesh, p, prec, lo, ln, gen, sign, cut = _wl(name)
         per = boundary == "periodic"
         systems = [_inputs(name, 0)]
     pos, q = systems[0]
-    g = oracle.green_table(lo, ln, (mesh,) * 3, p, 1, per)
+    g = oracle.green_table(lo, ln, (mesh,) * 3, p, cut, per)
     rng = synth.rng(777)
     # size one step to ~3 s so that warmup + steps end within a few minutes
     ncell = 8
     while True:
         cells = rng.choice(mesh ** 3, size=ncell, replace=False)
         t0 = time.perf_counter()
-        oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, 1, per, target_cells=cells, green=g)
+        oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, cut, per, target_cells=cells, green=g)
         dt = time.perf_counter() - t0
         if dt > 1.5 or ncell >= mesh ** 3:
             break
@@ -296,7 +305,7 @@ def run_reference(args, rank, world):
         cells = rng.choice(mesh ** 3, size=ncell, replace=False)
         pos, q = systems[it % len(systems)]
         t0 = time.perf_counter()
-        r = oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, 1, per, target_cells=cells, green=g)
+        r = oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, cut, per, target_cells=cells, green=g)
         dt = time.perf_counter() - t0
         if it >= args.warmup:
             times.append(dt)
@@ -326,9 +335,9 @@ def _config(name, world, near="auto"):
                 "mesh": [mesh] * 3, "fft_grid": [mesh] * 3, "p": p, "cutoff_cells": 27, "distribution": "uniform_pm1",
                 "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
                 "launch": "CUDA graph of the whole batched evaluation", "near_field_kernel": near}
-    n, boundary, mesh, p, prec, lo, ln, gen, sign = WORKLOADS[name]
+    n, boundary, mesh, p, prec, lo, ln, gen, sign, cut = _wl(name)
     return {"workload": name, "n_particles": n, "boundary": boundary, "mesh": [mesh] * 3,
-            "fft_grid": [mesh if boundary == "periodic" else 2 * mesh] * 3, "p": p, "cutoff_cells": 27,
+            "fft_grid": [mesh if boundary == "periodic" else 2 * mesh] * 3, "p": p, "cutoff_cells": (2 * cut + 1) ** 3,
             "distribution": gen, "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
             "near_field_kernel": near}
 
@@ -342,13 +351,13 @@ def run_ours(args, rank, world, local_rank):
     import paper_1409_5981_gb300 as pk
 
     name = args.workload
-    n, boundary, mesh, p, prec, lo, ln, gen, sign = WORKLOADS[name]
+    n, boundary, mesh, p, prec, lo, ln, gen, sign, cut = _wl(name)
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     pk._lib()  # fails loudly when the library is missing
     fp64 = prec == "fp64"
     dt = torch.float64 if fp64 else torch.float32
-    cfg = pk.Config(box_lo=lo, box_len=ln, mesh=(mesh,) * 3, p=p, cutoff=1,
+    cfg = pk.Config(box_lo=lo, box_len=ln, mesh=(mesh,) * 3, p=p, cutoff=cut,
                     boundary=pk.PERIODIC if boundary == "periodic" else pk.OPEN,
                     precision=pk.FP64 if fp64 else pk.FP32, sign=sign, near_field=_near(pk, args))
     stream = torch.cuda.current_stream()
@@ -425,7 +434,7 @@ def run_ours(args, rank, world, local_rank):
 
     # near-field pair count and mesh byte model
     cs = plan.export(pk.EXPORT_CELL_START)
-    pairs = _pairs(cs, mesh, boundary == "periodic")
+    pairs = _pairs(cs, mesh, boundary == "periodic", cut)
     C, CG, Kh, K = plan.info(pk.INFO_C), plan.info(pk.INFO_CG), plan.info(pk.INFO_KH), plan.info(pk.INFO_K)
     pp_ms = statistics.median(stage_acc.get("near_field", [float("nan")]))
     mesh_ms = sum(statistics.median(stage_acc.get(s, [0.0])) for s in ("fft_forward", "m2l", "fft_inverse"))
@@ -449,11 +458,11 @@ def run_ours(args, rank, world, local_rank):
     pos64, q64 = pos_np.astype(npdt).astype(np.float64), q_np.astype(npdt).astype(np.float64)
     if not (args.no_accuracy and (args.no_cpu_baseline or world > 1)):
         import oracle
-        green = oracle.green_table(lo, ln, (mesh,) * 3, p, 1, boundary == "periodic")
+        green = oracle.green_table(lo, ln, (mesh,) * 3, p, cut, boundary == "periodic")
     if not args.no_accuracy:
         import oracle
         cells = synth.rng(99).choice(mesh ** 3, size=4, replace=False)
-        r = oracle.pmmm(pos64, q64, lo, ln, (mesh,) * 3, p, 1, boundary == "periodic", target_cells=cells,
+        r = oracle.pmmm(pos64, q64, lo, ln, (mesh,) * 3, p, cut, boundary == "periodic", target_cells=cells,
                         green=green)
         sel = ~np.isnan(r["phi"])
         plan.compute_raw(n, pos.data_ptr(), q.data_ptr(), phi.data_ptr(), force.data_ptr())

@@ -386,7 +386,7 @@ __device__ __forceinline__ void pp_sum2(const ulonglong2* __restrict__ src, int 
   }
 }
 
-// FP32 near field (c = 1) on the pair-interleaved sources; same work items,
+// FP32 near field (c = 1 or 2) on the pair-interleaved sources; same work items,
 // lane mapping and output as pp_kernel.  The warp walks its 27 neighbour cells
 // in pieces of up to 16 source pairs (32 words of 16 bytes): every piece is
 // fetched with one coalesced 128-bit load per lane one piece ahead of its use,
@@ -394,6 +394,7 @@ __device__ __forceinline__ void pp_sum2(const ulonglong2* __restrict__ src, int 
 // broadcast loads, so each warp keeps a whole cell's sources in flight.
 constexpr int PIECE = 16;  // source pairs per piece (one 16-byte word per lane)
 
+template <int CUT>
 __global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel_f32x2(
     const float* __restrict__ part, const float* __restrict__ src2f, const uint32_t* __restrict__ pair_start,
     const uint32_t* __restrict__ vals, const int* __restrict__ cs, int64_t K, const uint32_t* __restrict__ item_start,
@@ -429,56 +430,70 @@ __global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel_f32
     if (active) xi = P[tbeg + tl];
     const int sbase = cell - cell % pp.ksys, lc = cell - sbase;  // system's first cell, local cell
     const int ix = lc % nx, iy = (lc / nx) % ny, iz = lc / (nx * ny);
-    // neighbour table: lane k < 27 holds the first pair and pair count of cell
-    // (ix + k%3 - 1, iy + (k/3)%3 - 1, iz + k/9 - 1)
-    int nbb = 0, nbc = 0;
-    if (lane < 27) {
-      int jx = ix + lane % 3 - 1, jy = iy + (lane / 3) % 3 - 1, jz = iz + lane / 9 - 1;
-      bool ok = true;
-      if (jx < 0 || jx >= nx) { ok = ok && pp.periodic; jx += (jx < 0) ? nx : -nx; }
-      if (jy < 0 || jy >= ny) { ok = ok && pp.periodic; jy += (jy < 0) ? ny : -ny; }
-      if (jz < 0 || jz >= nz) { ok = ok && pp.periodic; jz += (jz < 0) ? nz : -nz; }
-      if (ok) {
-        const int cj = sbase + jx + nx * (jy + ny * jz);
-        nbb = (int)__ldg(pair_start + cj);
-        nbc = (int)__ldg(pair_start + cj + 1) - nbb;
+    // neighbour table: entry k (x fastest) of the (2 CUT + 1)^3 cells
+    // (ix + k%W - CUT, iy + (k/W)%W - CUT, iz + k/W^2 - CUT) in lane k % 32, slot k / 32:
+    // first pair and pair count
+    constexpr int W = 2 * CUT + 1, NN = W * W * W, SLOTS = (NN + 31) / 32, SELFK = (NN - 1) / 2;
+    int nbb[SLOTS], nbc[SLOTS];
+#pragma unroll
+    for (int j = 0; j < SLOTS; ++j) {
+      const int kk = lane + 32 * j;
+      nbb[j] = 0;
+      nbc[j] = 0;
+      if (kk < NN) {
+        int jx = ix + kk % W - CUT, jy = iy + (kk / W) % W - CUT, jz = iz + kk / (W * W) - CUT;
+        bool ok = true;
+        if (jx < 0 || jx >= nx) { ok = ok && pp.periodic; jx += (jx < 0) ? nx : -nx; }
+        if (jy < 0 || jy >= ny) { ok = ok && pp.periodic; jy += (jy < 0) ? ny : -ny; }
+        if (jz < 0 || jz >= nz) { ok = ok && pp.periodic; jz += (jz < 0) ? nz : -nz; }
+        if (ok) {
+          const int cj = sbase + jx + nx * (jy + ny * jz);
+          nbb[j] = (int)__ldg(pair_start + cj);
+          nbc[j] = (int)__ldg(pair_start + cj + 1) - nbb[j];
+        }
       }
     }
+    auto nbget = [&](int kk, int& bo, int& no) {
+      int bb = nbb[0], cc = nbc[0];
+#pragma unroll
+      for (int q = 1; q < SLOTS; ++q)
+        if ((kk >> 5) == q) {
+          bb = nbb[q];
+          cc = nbc[q];
+        }
+      bo = __shfl_sync(0xffffffffu, bb, kk & 31);
+      no = __shfl_sync(0xffffffffu, cc, kk & 31);
+    };
     // piece iterator over (neighbour k, pair offset off)
     int k = 0, off = 0;
-    int b = __shfl_sync(0xffffffffu, nbb, 0), n = __shfl_sync(0xffffffffu, nbc, 0);
-    while (k < 27 && n == 0) {
+    int b, n;
+    nbget(0, b, n);
+    while (k < NN && n == 0) {
       ++k;
-      if (k < 27) {
-        b = __shfl_sync(0xffffffffu, nbb, k);
-        n = __shfl_sync(0xffffffffu, nbc, k);
-      }
+      if (k < NN) nbget(k, b, n);
     }
     ulonglong2 reg = make_ulonglong2(0ull, 0ull);
-    if (k < 27 && lane < 2 * min(PIECE, n - off)) reg = S2[2 * (b + off) + lane];
+    if (k < NN && lane < 2 * min(PIECE, n - off)) reg = S2[2 * (b + off) + lane];
     f2 pot = pk2(0.f, 0.f), gx = pot, gy = pot, gz = pot;
     int cur = 0;
-    while (k < 27) {
+    while (k < NN) {
       const int kc = k, len = min(PIECE, n - off);
       stage[warp][cur][lane] = reg;
       __syncwarp();
       // advance to the next piece and fetch it
       off += PIECE;
-      while (k < 27 && off >= n) {
+      while (k < NN && off >= n) {
         ++k;
         off = 0;
-        if (k < 27) {
-          b = __shfl_sync(0xffffffffu, nbb, k);
-          n = __shfl_sync(0xffffffffu, nbc, k);
-        }
+        if (k < NN) nbget(k, b, n);
       }
-      if (k < 27 && lane < 2 * min(PIECE, n - off)) reg = S2[2 * (b + off) + lane];
+      if (k < NN && lane < 2 * min(PIECE, n - off)) reg = S2[2 * (b + off) + lane];
       // target in the frame of the source cell centre (units of hs)
-      const float txs = xi.x - (float)(kc % 3 - 1) * csx;
-      const float tys = xi.y - (float)((kc / 3) % 3 - 1) * csy;
-      const float tzs = xi.z - (float)(kc / 9 - 1) * csz;
+      const float txs = xi.x - (float)(kc % W - CUT) * csx;
+      const float tys = xi.y - (float)((kc / W) % W - CUT) * csy;
+      const float tzs = xi.z - (float)(kc / (W * W) - CUT) * csz;
       const f2 tx = pk2(txs, txs), ty = pk2(tys, tys), tz = pk2(tzs, tzs);
-      if (kc == 13)
+      if (kc == SELFK)
         pp_sum2<true>(stage[warp][cur], len, ph, SP, tx, ty, tz, pot, gx, gy, gz);
       else
         pp_sum2<false>(stage[warp][cur], len, ph, SP, tx, ty, tz, pot, gx, gy, gz);
@@ -534,7 +549,7 @@ __global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel_f32
   }
 }
 
-// FP32 near field (c = 1) with one thread per target: for sparsely filled cells,
+// FP32 near field (c = 1 or 2) with one thread per target: for sparsely filled cells,
 // where the per-item set-up of the cell-item kernels costs more than the
 // interactions.  Thread i takes sorted target i; it walks the 9 neighbour rows
 // (dy, dz) and in each row the pairs of the cells x-1, x, x+1 of the pair layout
@@ -545,6 +560,7 @@ __global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel_f32
 // split between two warps.
 constexpr int PPS_THREADS = 256;
 
+template <int CUT>
 __global__ void __launch_bounds__(PPS_THREADS, 4) pp_target_kernel(
     const float4* __restrict__ P, const ulonglong2* __restrict__ S2, const uint32_t* __restrict__ pair_start,
     const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, const int* __restrict__ cs,
@@ -569,7 +585,7 @@ __global__ void __launch_bounds__(PPS_THREADS, 4) pp_target_kernel(
     const int ix = lc % nx, iy = (lc / nx) % ny, iz = lc / (nx * ny);
     const float csx = pp.cs32[0], csy = pp.cs32[1], csz = pp.cs32[2];
     f2 pot = pk2(0.f, 0.f), gx = pot, gy = pot, gz = pot;
-    for (int dz = -1; dz <= 1; ++dz) {
+    for (int dz = -CUT; dz <= CUT; ++dz) {
       int jz = iz + dz;
       if (jz < 0 || jz >= nz) {
         if (!pp.periodic) continue;
@@ -577,7 +593,7 @@ __global__ void __launch_bounds__(PPS_THREADS, 4) pp_target_kernel(
       }
       const float tzs = xi.z - (float)dz * csz;
       const f2 tz = pk2(tzs, tzs);
-      for (int dy = -1; dy <= 1; ++dy) {
+      for (int dy = -CUT; dy <= CUT; ++dy) {
         int jy = iy + dy;
         if (jy < 0 || jy >= ny) {
           if (!pp.periodic) continue;
@@ -587,14 +603,14 @@ __global__ void __launch_bounds__(PPS_THREADS, 4) pp_target_kernel(
         const f2 ty = pk2(tys, tys);
         const int row = sbase + nx * (jy + ny * jz);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          int jx = ix + d - 1;
+        for (int d = 0; d < 2 * CUT + 1; ++d) {
+          int jx = ix + d - CUT;
           if (jx < 0 || jx >= nx) {
             if (!pp.periodic) continue;
             jx += (jx < 0) ? nx : -nx;
           }
           const int pb = (int)__ldg(pair_start + row + jx), pe = (int)__ldg(pair_start + row + jx + 1);
-          const float txs = xi.x - (float)(d - 1) * csx;
+          const float txs = xi.x - (float)(d - CUT) * csx;
           const f2 tx = pk2(txs, txs);
 #pragma unroll 1
           for (int pr = pb; pr < pe; ++pr)
@@ -684,7 +700,7 @@ cudaError_t launch_pair_pack(const void* part, const uint32_t* keys, const int* 
   return cudaGetLastError();
 }
 
-bool pp_per_target_applies(bool fp64, int c) { return !fp64 && c <= 1; }
+bool pp_per_target_applies(bool fp64, int c) { return !fp64 && c <= 2; }
 
 cudaError_t launch_pp(bool fp64, const void* part, const void* src2, const uint32_t* pair_start, const uint32_t* vals,
                       const uint32_t* keys, int64_t n, bool per_target, const int* cell_start, int64_t K,
@@ -693,16 +709,25 @@ cudaError_t launch_pp(bool fp64, const void* part, const void* src2, const uint3
   // persistent launch: PP_BLOCKS_PER_SM resident blocks of PP_WARPS warps per SM
   const unsigned blocks = (unsigned)(PP_BLOCKS_PER_SM * (num_sms > 0 ? num_sms : 1));
   if (per_target && pp_per_target_applies(fp64, pp.c) && src2 != nullptr) {
-    if (n > 0)
-      pp_target_kernel<<<(unsigned)((n + PPS_THREADS - 1) / PPS_THREADS), PPS_THREADS, 0, s>>>(
-          (const float4*)part, (const ulonglong2*)src2, pair_start, keys, vals, cell_start, item_start, n,
-          (const float4*)far, pp, (float*)phi, (float*)force, epart);
+    if (n <= 0) return cudaSuccess;
+    const unsigned g = (unsigned)((n + PPS_THREADS - 1) / PPS_THREADS);
+    if (pp.c <= 1)
+      pp_target_kernel<1><<<g, PPS_THREADS, 0, s>>>((const float4*)part, (const ulonglong2*)src2, pair_start, keys,
+                                                    vals, cell_start, item_start, n, (const float4*)far, pp,
+                                                    (float*)phi, (float*)force, epart);
     else
-      return cudaSuccess;
-  } else if (!fp64 && pp.c <= 1 && src2 != nullptr) {
-    pp_kernel_f32x2<<<blocks, PP_WARPS * 32, 0, s>>>((const float*)part, (const float*)src2, pair_start, vals,
-                                                     cell_start, K, item_start, item_cell, counter, (const float*)far,
-                                                     pp, (float*)phi, (float*)force, epart);
+      pp_target_kernel<2><<<g, PPS_THREADS, 0, s>>>((const float4*)part, (const ulonglong2*)src2, pair_start, keys,
+                                                    vals, cell_start, item_start, n, (const float4*)far, pp,
+                                                    (float*)phi, (float*)force, epart);
+  } else if (!fp64 && pp.c <= 2 && src2 != nullptr) {
+    if (pp.c <= 1)
+      pp_kernel_f32x2<1><<<blocks, PP_WARPS * 32, 0, s>>>((const float*)part, (const float*)src2, pair_start, vals,
+                                                          cell_start, K, item_start, item_cell, counter,
+                                                          (const float*)far, pp, (float*)phi, (float*)force, epart);
+    else
+      pp_kernel_f32x2<2><<<blocks, PP_WARPS * 32, 0, s>>>((const float*)part, (const float*)src2, pair_start, vals,
+                                                          cell_start, K, item_start, item_cell, counter,
+                                                          (const float*)far, pp, (float*)phi, (float*)force, epart);
   } else {
 #define PP_LAUNCH(T, S)                                                                                              \
   pp_kernel<T, S><<<blocks, PP_WARPS * 32, 0, s>>>((const T*)part, vals, cell_start, K, item_start, item_cell, counter, \

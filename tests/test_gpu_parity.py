@@ -400,3 +400,27 @@ def test_bounded_wait_times_out_and_context_survives(pk):
     assert _rel(force, -(q[:, None] * ref["grad"])) < FP64_TOL
     assert plan.status() == pk.OK
     plan.close()
+
+
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_cutoff2_fp32_both_near_field_kernels(pk, boundary):
+    """c = 2 (125 near cells) in FP32 with each near-field kernel (cell items with the
+    multi-slot neighbour table, one thread per target with rows of five cells): both
+    within the FP32 tolerance of the oracle and of each other."""
+    pos, q = synth.uniform_pm1(6000, synth.seed(1, 37 + boundary))
+    pos = pos.astype(np.float32).astype(np.float64)
+    out = {}
+    for nf in (pk.NEAR_CELL_ITEMS, pk.NEAR_PER_TARGET):
+        cfg = pk.Config(mesh=(8, 8, 8), p=4, cutoff=2, boundary=boundary, precision=pk.FP32, near_field=nf)
+        plan, phi, force, e = _run(pk, cfg, pos, q)
+        plan.close()
+        out[nf] = (phi, force, e)
+    cfg = pk.Config(mesh=(8, 8, 8), p=4, cutoff=2, boundary=boundary, precision=pk.FP32)
+    ref = _oracle(cfg, pk, pos, q)
+    rf = -(q[:, None] * ref["grad"])
+    for nf, (phi, force, e) in out.items():
+        ef, ep = _rel(force, rf), _rel(phi, ref["phi"])
+        print(f"c=2 FP32 bnd={boundary} kernel {nf}: force {ef:.2e} phi {ep:.2e}")
+        assert ef < FP32_TOL[4] and ep < FP32_TOL[4]
+    a, b = out[pk.NEAR_CELL_ITEMS], out[pk.NEAR_PER_TARGET]
+    assert _rel(a[1], b[1]) < 2e-6 and abs(a[2] - b[2]) < 1e-6 * abs(a[2])
