@@ -27,8 +27,18 @@ template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; };
 template <> struct V4<double> { using type = double4; };
 
+// FP32 reciprocal square root: the hardware approximation (PTX rsqrt.approx,
+// relative error below 2^-22.9) with subnormal inputs flushed to zero.  A pair
+// distance is never subnormal (the self pair gives exactly zero and is masked),
+// so the flush changes no result and spares the subnormal handling of rsqrtf.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 template <typename T> __device__ __forceinline__ T rsq(T x);
-template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrt_ftz(x); }
 template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
 
 // item counts per cell: ceil(count / CHUNK)
@@ -315,7 +325,7 @@ __device__ __forceinline__ void pp_pair2(const ulonglong2& A, const ulonglong2& 
   const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
   float a, b;
   up2(r2, a, b);
-  float ra = rsqrtf(a), rb = rsqrtf(b);
+  float ra = rsqrt_ftz(a), rb = rsqrt_ftz(b);
   if (SELF) {
     ra = a > 0.f ? ra : 0.f;
     rb = b > 0.f ? rb : 0.f;
@@ -339,7 +349,7 @@ __device__ __forceinline__ void pp_pair2_mixed(const ulonglong2& A, const ulongl
   const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
   float a, b;
   up2(r2, a, b);
-  float ra = rsqrtf(a), rb = rsqrtf(b);
+  float ra = rsqrt_ftz(a), rb = rsqrt_ftz(b);
   if (SELF) {
     ra = a > 0.f ? ra : 0.f;
     rb = b > 0.f ? rb : 0.f;
