@@ -79,6 +79,7 @@ def _L():
                 "orc_green_open": (None, [i32, i32, vp, vp, vp]),
                 "orc_green_periodic": (None, [i32, i32, vp, vp, d, i32, vp, vp]),
                 "orc_pmmm": (i32, [vp, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp]),
+                "orc_pmmm_hier": (i32, [vp, i32, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp]),
                 "orc_green_table_size": (i64, [vp]),
                 "orc_green_table": (None, [vp, vp]),
             }
@@ -356,6 +357,40 @@ def pmmm(pos, q, lo, length, mesh, p: int, c: int = 1, periodic: bool = False, a
     st = _L().orc_pmmm(ctypes.byref(cfg), n, _p(pos), _p(q), ntc, _p(tc), _p(phi), _p(g), _p(M), _p(Lo), _p(corr),
                        _p(green))
     out = {"status": int(st), "phi": phi, "grad": g, "corr": corr, "alpha": cfg.alpha}
+    if want_ml:
+        out["M"] = M
+        out["L"] = Lo
+    return out
+
+
+def pmmm_hier(pos, q, lo, length, mesh, p: int, refine: int, c: int = 1, periodic: bool = False,
+              alpha: float | None = None, nmax: int = 5, target_cells=None, want_ml: bool = False,
+              green_coarse: np.ndarray | None = None):
+    """Two-level PMMM (Sec. 5, hierarchical treatment) by its definition: PMMM on the
+    coarse mesh (mesh / refine cells per axis, the coarse (2c+1)^3 block masked),
+    free-space M2L between the fine cells of the masked coarse block (fine (2c+1)^3
+    block masked), near field over the fine (2c+1)^3 cells.
+
+    `mesh` is the fine mesh.  Returns dict(status, phi, grad, [M, L]) like pmmm():
+    M the fine multipoles, L per target fine cell the total local expansion before the
+    periodic corrections, L2L(coarse local) + the fine-level sum.
+    green_coarse: optional green_table() of the coarse geometry."""
+    pos = _f64(pos).reshape(-1, 3)
+    q = _f64(q).reshape(-1)
+    cfg = _cfg(lo, length, mesh, p, c, periodic, alpha, nmax)
+    n = pos.shape[0]
+    K = int(mesh[0]) * int(mesh[1]) * int(mesh[2])
+    tc = None if target_cells is None else np.ascontiguousarray(target_cells, dtype=np.int64)
+    ntc = -1 if tc is None else tc.shape[0]
+    phi = np.full(n, np.nan)
+    g = np.full((n, 3), np.nan)
+    M = np.zeros((K, nterms(p)), dtype=np.complex128) if want_ml else None
+    Lo = np.zeros((K, nterms(p)), dtype=np.complex128) if want_ml else None
+    if green_coarse is not None:
+        green_coarse = np.ascontiguousarray(green_coarse, dtype=np.complex128)
+    st = _L().orc_pmmm_hier(ctypes.byref(cfg), int(refine), n, _p(pos), _p(q), ntc, _p(tc), _p(phi), _p(g), _p(M),
+                            _p(Lo), _p(green_coarse))
+    out = {"status": int(st), "phi": phi, "grad": g, "alpha": cfg.alpha}
     if want_ml:
         out["M"] = M
         out["L"] = Lo

@@ -26,6 +26,11 @@
  *   near field ...................... Sec. 2.1/2.2: pure Newtonian 1/r over the
  *                                      masked (2c+1)^3 cells
  *   direct O(N^2) sum, Ewald sum .... Sec. 4 and App. B.3, Eq. refewald
+ *   two-level PMMM .................. Sec. 5 (hierarchical treatment) and
+ *                                      Fig. refine: PMMM on a coarse mesh plus
+ *                                      free-space M2L between the fine cells of
+ *                                      each masked coarse block, cell pair by
+ *                                      cell pair
  *
  * Where the paper is ambiguous or its printed formula is defective, the
  * readings taken here are the ones listed in the design notes of this
@@ -48,7 +53,7 @@
 
 typedef double complex cplx;
 
-#define ORC_VERSION 3
+#define ORC_VERSION 4
 #define LMAX_ORACLE 48
 
 static inline int hidx(int l, int m) { return l * l + l + m; }
@@ -679,6 +684,44 @@ void orc_green_table(const orc_cfg *cfg, double *out)
     }
 }
 
+/* Near field of particle i (binned position wp[3i], in cell (ix, iy, iz) of
+ * cfg's mesh): pure 1/r over the particles of the (2c+1)^3 masked cells
+ * (Sec. 2.1), periodic neighbours shifted by a box length; adds to *f and g
+ * (gradient of Phi). */
+static void near_field(const orc_cfg *cfg, const int64_t *cs, const int64_t *perm, const double *wp,
+                       const double *q, int64_t i, int ix, int iy, int iz, double *f, double g[3])
+{
+    const int c = cfg->c, nx = cfg->mesh[0], ny = cfg->mesh[1], nz = cfg->mesh[2];
+    const double *ri = wp + 3 * i;
+    for (int ez = -c; ez <= c; ++ez)
+        for (int ey = -c; ey <= c; ++ey)
+            for (int ex = -c; ex <= c; ++ex) {
+                int jx = ix + ex, jy = iy + ey, jz = iz + ez;
+                double sh[3] = {0, 0, 0};
+                if (cfg->periodic) {
+                    int wx = ((jx % nx) + nx) % nx, wy = ((jy % ny) + ny) % ny, wz = ((jz % nz) + nz) % nz;
+                    sh[0] = (double)((jx - wx) / nx) * cfg->len[0];
+                    sh[1] = (double)((jy - wy) / ny) * cfg->len[1];
+                    sh[2] = (double)((jz - wz) / nz) * cfg->len[2];
+                    jx = wx; jy = wy; jz = wz;
+                } else if (jx < 0 || jy < 0 || jz < 0 || jx >= nx || jy >= ny || jz >= nz) {
+                    continue;
+                }
+                int64_t cj = jx + (int64_t)nx * (jy + (int64_t)ny * jz);
+                for (int64_t u = cs[cj]; u < cs[cj + 1]; ++u) {
+                    int64_t j = perm[u];
+                    if (j == i) continue;
+                    double d[3] = {ri[0] - (wp[3 * j] + sh[0]), ri[1] - (wp[3 * j + 1] + sh[1]),
+                                   ri[2] - (wp[3 * j + 2] + sh[2])};
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (r2 == 0.0) continue;
+                    double rinv = 1.0 / sqrt(r2);
+                    *f += q[j] * rinv;
+                    for (int a = 0; a < 3; ++a) g[a] -= q[j] * rinv * rinv * rinv * d[a];
+                }
+            }
+}
+
 /* green_table: optional table from orc_green_table for the same cfg (not owned). */
 int orc_pmmm(const orc_cfg *cfg, int64_t n, const double *pos, const double *q, int64_t ntc, const int64_t *tcells,
              double *phi, double *grad, double *M_out, double *L_out, double *corr_out, const double *green_table)
@@ -827,34 +870,7 @@ int orc_pmmm(const orc_cfg *cfg, int64_t n, const double *pos, const double *q, 
                 f += 2.0 * M_PI / (3.0 * V) * Qtot * (rr - 3.0 / (2.0 * cfg->alpha * cfg->alpha));
                 for (int a = 0; a < 3; ++a) g[a] += 4.0 * M_PI / (3.0 * V) * Qtot * rel[a];
             }
-            /* near field over the (2c+1)^3 masked cells, pure 1/r */
-            for (int ez = -c; ez <= c; ++ez)
-                for (int ey = -c; ey <= c; ++ey)
-                    for (int ex = -c; ex <= c; ++ex) {
-                        int jx = ix + ex, jy = iy + ey, jz = iz + ez;
-                        double sh[3] = {0, 0, 0};
-                        if (cfg->periodic) {
-                            int wx = ((jx % nx) + nx) % nx, wy = ((jy % ny) + ny) % ny, wz = ((jz % nz) + nz) % nz;
-                            sh[0] = (double)((jx - wx) / nx) * cfg->len[0];
-                            sh[1] = (double)((jy - wy) / ny) * cfg->len[1];
-                            sh[2] = (double)((jz - wz) / nz) * cfg->len[2];
-                            jx = wx; jy = wy; jz = wz;
-                        } else if (jx < 0 || jy < 0 || jz < 0 || jx >= nx || jy >= ny || jz >= nz) {
-                            continue;
-                        }
-                        int64_t cj = jx + (int64_t)nx * (jy + (int64_t)ny * jz);
-                        for (int64_t u = cs[cj]; u < cs[cj + 1]; ++u) {
-                            int64_t j = perm[u];
-                            if (j == i) continue;
-                            double d[3] = {ri[0] - (wp[3 * j] + sh[0]), ri[1] - (wp[3 * j + 1] + sh[1]),
-                                           ri[2] - (wp[3 * j + 2] + sh[2])};
-                            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                            if (r2 == 0.0) continue;
-                            double rinv = 1.0 / sqrt(r2);
-                            f += q[j] * rinv;
-                            for (int a = 0; a < 3; ++a) g[a] -= q[j] * rinv * rinv * rinv * d[a];
-                        }
-                    }
+            near_field(cfg, cs, perm, wp, q, i, ix, iy, iz, &f, g);
             phi[i] = f;
             for (int a = 0; a < 3; ++a) grad[3 * i + a] = g[a];
         }
@@ -866,5 +882,256 @@ int orc_pmmm(const orc_cfg *cfg, int64_t n, const double *pos, const double *q, 
     free(perm);
     free(cs);
     free(wp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Two-level PMMM (Sec. 5, hierarchical treatment; Fig. refine).             */
+/*                                                                          */
+/* The mesh of cfg is the fine mesh; every `refine`^3 block of fine cells is */
+/* one coarse cell.  By the definition of the method:                       */
+/*  1. coarse level: PMMM on the coarse mesh (coarse multipoles by Eq. P2M  */
+/*     at the coarse centres, L_T = sum_S G(T - S) M_S over all coarse     */
+/*     pairs with the coarse Green function, whose nearest (2c+1)^3 coarse */
+/*     cells are masked), with the periodic corrections of App. B.3 taken  */
+/*     at the coarse level (coarse-cell-relative positions, coarse M_0^0);  */
+/*  2. fine level: every fine source cell s whose coarse cell S lies in the */
+/*     masked (2c+1)^3 block of the target's coarse cell T contributes      */
+/*     M2L(M_s, r_t - r_s) with the free-space kernel, unless the fine      */
+/*     cells are themselves nearest neighbours (|t - s|_inf <= c);          */
+/*  3. the rest, the fine (2c+1)^3 near cells, by the direct 1/r sum.      */
+/* The potential of a particle is the coarse local expansion evaluated at   */
+/* its offset from the coarse centre (Eq. L2P, with the order-one L2L       */
+/* gradient) plus the fine local expansion at its offset from the fine      */
+/* centre plus its near field.                                              */
+/*                                                                          */
+/* M_out (K_fine * (p+1)^2 complex, optional): fine multipoles.             */
+/* L_out (optional): for each target fine cell t, the total local expansion */
+/* before the periodic corrections, as one fine-centred expansion:          */
+/* L2L(L_T, r_t - r_T) + the fine-level sum.                                */
+/* green_coarse (optional): orc_green_table of the coarse geometry.         */
+/* ------------------------------------------------------------------------ */
+int orc_pmmm_hier(const orc_cfg *cfg, int refine, int64_t n, const double *pos, const double *q, int64_t ntc,
+                  const int64_t *tcells, double *phi, double *grad, double *M_out, double *L_out,
+                  const double *green_coarse)
+{
+    const int p = cfg->p, c = cfg->c, r = refine, J = 2 * p;
+    const int np = (p + 1) * (p + 1), ng = (J + 1) * (J + 1);
+    if (r < 1) return -1;
+    for (int a = 0; a < 3; ++a)
+        if (cfg->mesh[a] % r != 0) return -1;
+    const int nx = cfg->mesh[0], ny = cfg->mesh[1], nz = cfg->mesh[2];
+    const int64_t K = (int64_t)nx * ny * nz;
+    orc_cfg cc = *cfg;
+    for (int a = 0; a < 3; ++a) cc.mesh[a] = cfg->mesh[a] / r;
+    const int mx = cc.mesh[0], my = cc.mesh[1], mz = cc.mesh[2];
+    const int64_t Kc = (int64_t)mx * my * mz;
+    double hf[3], hc[3], V = cfg->len[0] * cfg->len[1] * cfg->len[2];
+    for (int a = 0; a < 3; ++a) {
+        hf[a] = cfg->len[a] / cfg->mesh[a];
+        hc[a] = hf[a] * r;
+    }
+
+    int32_t *cell = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    int64_t *cs = (int64_t *)malloc(sizeof(int64_t) * (K + 1));
+    double *wp = (double *)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    int st = orc_bin(n, pos, cfg->lo, cfg->len, cfg->mesh, cfg->periodic, cell, perm, cs, wp);
+    if (st != 0) {
+        free(cell); free(perm); free(cs); free(wp);
+        return st;
+    }
+
+    /* fine and coarse multipoles (Eq. P2M at the fine and at the coarse centres) */
+    cplx *Mf = (cplx *)calloc((size_t)K * np, sizeof(cplx));
+    cplx *Mc = (cplx *)calloc((size_t)Kc * np, sizeof(cplx));
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t ci = 0; ci < K; ++ci) {
+        int ix = (int)(ci % nx), iy = (int)((ci / nx) % ny), iz = (int)(ci / ((int64_t)nx * ny));
+        double ctr[3] = {cfg->lo[0] + (ix + 0.5) * hf[0], cfg->lo[1] + (iy + 0.5) * hf[1],
+                         cfg->lo[2] + (iz + 0.5) * hf[2]};
+        for (int64_t s = cs[ci]; s < cs[ci + 1]; ++s) {
+            int64_t i = perm[s];
+            p2m(p, 1, wp + 3 * i, q + i, ctr, Mf + ci * np);
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t T = 0; T < Kc; ++T) {
+        int Tx = (int)(T % mx), Ty = (int)((T / mx) % my), Tz = (int)(T / ((int64_t)mx * my));
+        double ctr[3] = {cfg->lo[0] + (Tx + 0.5) * hc[0], cfg->lo[1] + (Ty + 0.5) * hc[1],
+                         cfg->lo[2] + (Tz + 0.5) * hc[2]};
+        for (int bz = 0; bz < r; ++bz)
+            for (int by = 0; by < r; ++by)
+                for (int bx = 0; bx < r; ++bx) {
+                    int64_t ci = (Tx * r + bx) + (int64_t)nx * ((Ty * r + by) + (int64_t)ny * (Tz * r + bz));
+                    for (int64_t s = cs[ci]; s < cs[ci + 1]; ++s) {
+                        int64_t i = perm[s];
+                        p2m(p, 1, wp + 3 * i, q + i, ctr, Mc + T * np);
+                    }
+                }
+    }
+    if (M_out) memcpy(M_out, Mf, sizeof(cplx) * K * np);
+
+    /* target fine cells and the coarse cells they lie in */
+    int64_t nT = ntc < 0 ? K : ntc;
+    char *need = (char *)calloc((size_t)Kc, 1);
+    for (int64_t t = 0; t < nT; ++t) {
+        int64_t ci = ntc < 0 ? t : tcells[t];
+        int ix = (int)(ci % nx), iy = (int)((ci / nx) % ny), iz = (int)(ci / ((int64_t)nx * ny));
+        need[(ix / r) + (int64_t)mx * ((iy / r) + (int64_t)my * (iz / r))] = 1;
+    }
+
+    /* coarse level: cell-pair convolution with the coarse Green function */
+    int gx = cc.periodic ? mx : 2 * mx - 1, gy = cc.periodic ? my : 2 * my - 1, gz = cc.periodic ? mz : 2 * mz - 1;
+    int64_t NG = (int64_t)gx * gy * gz;
+    cplx *Gc = (cplx *)green_coarse;
+    int owned = 0;
+    if (!Gc) {
+        Gc = (cplx *)malloc(sizeof(cplx) * NG * ng);
+        orc_green_table(&cc, (double *)Gc);
+        owned = 1;
+    }
+    cplx *Lc = (cplx *)calloc((size_t)Kc * np, sizeof(cplx));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t T = 0; T < Kc; ++T) {
+        if (!need[T]) continue;
+        int Tx = (int)(T % mx), Ty = (int)((T / mx) % my), Tz = (int)(T / ((int64_t)mx * my));
+        for (int64_t S = 0; S < Kc; ++S) {
+            int Sx = (int)(S % mx), Sy = (int)((S / mx) % my), Sz = (int)(S / ((int64_t)mx * my));
+            int64_t gi;
+            if (cc.periodic) {
+                int d[3] = {((Tx - Sx) % mx + mx) % mx, ((Ty - Sy) % my + my) % my, ((Tz - Sz) % mz + mz) % mz};
+                gi = d[0] + (int64_t)gx * (d[1] + (int64_t)gy * d[2]);
+            } else {
+                gi = (Tx - Sx + mx - 1) + (int64_t)gx * ((Ty - Sy + my - 1) + (int64_t)gy * (Tz - Sz + mz - 1));
+            }
+            m2l_green(p, Mc + S * np, Gc + gi * ng, Lc + T * np);
+        }
+    }
+    if (owned) free(Gc);
+    cplx *Lc0 = (cplx *)malloc(sizeof(cplx) * (size_t)Kc * np);
+    memcpy(Lc0, Lc, sizeof(cplx) * (size_t)Kc * np);
+
+    /* periodic corrections (App. B.3) at the coarse level */
+    double Qtot = 0, q2sum = 0;
+    for (int64_t i = 0; i < n; ++i) Qtot += q[i];
+    if (cfg->periodic) {
+        cplx sM10 = 0, sM11 = 0;
+        for (int64_t T = 0; T < Kc; ++T) {
+            if (p >= 1) {
+                sM10 += Mc[T * np + hidx(1, 0)];
+                sM11 += Mc[T * np + hidx(1, 1)];
+            }
+        }
+        for (int64_t ci = 0; ci < K; ++ci) {
+            int ix = (int)(ci % nx), iy = (int)((ci / nx) % ny), iz = (int)(ci / ((int64_t)nx * ny));
+            double ctr[3] = {cfg->lo[0] + (ix / r + 0.5) * hc[0], cfg->lo[1] + (iy / r + 0.5) * hc[1],
+                             cfg->lo[2] + (iz / r + 0.5) * hc[2]};
+            for (int64_t s = cs[ci]; s < cs[ci + 1]; ++s) {
+                int64_t i = perm[s];
+                double rr = 0;
+                for (int a = 0; a < 3; ++a) rr += (wp[3 * i + a] - ctr[a]) * (wp[3 * i + a] - ctr[a]);
+                q2sum += q[i] * rr;
+            }
+        }
+        for (int64_t T = 0; T < Kc; ++T) {
+            if (!need[T]) continue;
+            cplx *L = Lc + T * np;
+            if (p >= 1) {
+                L[hidx(1, 0)] += 4.0 * M_PI / (3.0 * V) * sM10;
+                cplx d11 = 8.0 * M_PI / (3.0 * V) * conj(sM11);
+                L[hidx(1, 1)] += d11;
+                L[hidx(1, -1)] += -conj(d11);
+            }
+            L[0] += -2.0 * cfg->alpha / sqrt(M_PI) * Mc[T * np] + 2.0 * M_PI / (3.0 * V) * q2sum;
+        }
+    }
+
+    /* fine level: free-space kernel of every fine offset the masked coarse block can hold */
+    const int D = (c + 1) * r - 1, W = 2 * D + 1;
+    cplx *Gf = (cplx *)malloc(sizeof(cplx) * (size_t)W * W * W * ng);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t u = 0; u < (int64_t)W * W * W; ++u) {
+        int d[3] = {(int)(u % W) - D, (int)((u / W) % W) - D, (int)(u / ((int64_t)W * W)) - D};
+        orc_green_open(p, c, hf, d, (double *)(Gf + u * ng));
+    }
+    cplx *Lf = (cplx *)calloc((size_t)nT * np, sizeof(cplx));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < nT; ++t) {
+        int64_t ci = ntc < 0 ? t : tcells[t];
+        int tx = (int)(ci % nx), ty = (int)((ci / nx) % ny), tz = (int)(ci / ((int64_t)nx * ny));
+        int T3[3] = {tx / r, ty / r, tz / r}, A3[3] = {tx % r, ty % r, tz % r};
+        for (int ez = -c; ez <= c; ++ez)
+            for (int ey = -c; ey <= c; ++ey)
+                for (int ex = -c; ex <= c; ++ex) {
+                    int E3[3] = {ex, ey, ez}, S3[3];
+                    int skip = 0;
+                    for (int a = 0; a < 3; ++a) {
+                        S3[a] = T3[a] + E3[a];
+                        if (S3[a] < 0 || S3[a] >= cc.mesh[a]) {
+                            if (!cfg->periodic) skip = 1;
+                            S3[a] = ((S3[a] % cc.mesh[a]) + cc.mesh[a]) % cc.mesh[a];
+                        }
+                    }
+                    if (skip) continue;
+                    for (int bz = 0; bz < r; ++bz)
+                        for (int by = 0; by < r; ++by)
+                            for (int bx = 0; bx < r; ++bx) {
+                                int B3[3] = {bx, by, bz}, d[3];
+                                for (int a = 0; a < 3; ++a) d[a] = A3[a] - B3[a] - E3[a] * r;
+                                int64_t sc = (S3[0] * r + bx) + (int64_t)nx * ((S3[1] * r + by) +
+                                                                                (int64_t)ny * (S3[2] * r + bz));
+                                int64_t u = (d[0] + D) + (int64_t)W * ((d[1] + D) + (int64_t)W * (d[2] + D));
+                                m2l_green(p, Mf + sc * np, Gf + u * ng, Lf + t * np);
+                            }
+                }
+    }
+    free(Gf);
+
+    if (L_out)
+        for (int64_t t = 0; t < nT; ++t) {
+            int64_t ci = ntc < 0 ? t : tcells[t];
+            int tx = (int)(ci % nx), ty = (int)((ci / nx) % ny), tz = (int)(ci / ((int64_t)nx * ny));
+            int64_t T = (tx / r) + (int64_t)mx * ((ty / r) + (int64_t)my * (tz / r));
+            double sh[3] = {((tx % r) + 0.5) * hf[0] - 0.5 * hc[0], ((ty % r) + 0.5) * hf[1] - 0.5 * hc[1],
+                            ((tz % r) + 0.5) * hf[2] - 0.5 * hc[2]};
+            cplx *Lo = (cplx *)L_out + ci * np;
+            l2l(p, p, Lc0 + T * np, sh, Lo);
+            for (int k = 0; k < np; ++k) Lo[k] += Lf[t * np + k];
+        }
+
+    /* potential and gradient of the particles of the target cells */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < nT; ++t) {
+        int64_t ci = ntc < 0 ? t : tcells[t];
+        int ix = (int)(ci % nx), iy = (int)((ci / nx) % ny), iz = (int)(ci / ((int64_t)nx * ny));
+        int64_t T = (ix / r) + (int64_t)mx * ((iy / r) + (int64_t)my * (iz / r));
+        double cf[3] = {cfg->lo[0] + (ix + 0.5) * hf[0], cfg->lo[1] + (iy + 0.5) * hf[1],
+                        cfg->lo[2] + (iz + 0.5) * hf[2]};
+        double cC[3] = {cfg->lo[0] + (ix / r + 0.5) * hc[0], cfg->lo[1] + (iy / r + 0.5) * hc[1],
+                        cfg->lo[2] + (iz / r + 0.5) * hc[2]};
+        for (int64_t s = cs[ci]; s < cs[ci + 1]; ++s) {
+            int64_t i = perm[s];
+            const double *ri = wp + 3 * i;
+            double relc[3] = {ri[0] - cC[0], ri[1] - cC[1], ri[2] - cC[2]};
+            double relf[3] = {ri[0] - cf[0], ri[1] - cf[1], ri[2] - cf[2]};
+            double f, g[3], f2, g2[3];
+            l2p(p, Lc + T * np, relc, &f, g);
+            if (cfg->periodic && Qtot != 0.0) {
+                double rr = relc[0] * relc[0] + relc[1] * relc[1] + relc[2] * relc[2];
+                f += 2.0 * M_PI / (3.0 * V) * Qtot * (rr - 3.0 / (2.0 * cfg->alpha * cfg->alpha));
+                for (int a = 0; a < 3; ++a) g[a] += 4.0 * M_PI / (3.0 * V) * Qtot * relc[a];
+            }
+            l2p(p, Lf + t * np, relf, &f2, g2);
+            f += f2;
+            for (int a = 0; a < 3; ++a) g[a] += g2[a];
+            near_field(cfg, cs, perm, wp, q, i, ix, iy, iz, &f, g);
+            phi[i] = f;
+            for (int a = 0; a < 3; ++a) grad[3 * i + a] = g[a];
+        }
+    }
+
+    free(Lf); free(Lc0); free(Lc); free(need); free(Mc); free(Mf);
+    free(cell); free(perm); free(cs); free(wp);
     return 0;
 }
