@@ -55,6 +55,11 @@ WORKLOADS = {
     # c = 2 (125 near cells, the paper's recommended cutoff): lower p for the same accuracy
     "periodic_uniform_n1048576_mesh32_p5_c2_fp32": (1 << 20, "periodic", 32, 5, "fp32", (0, 0, 0), (1, 1, 1),
                                                     "uniform_pm1", 1.0, 2),
+    # two-level PMMM (Sec. 5 hierarchical treatment): fine mesh 32^3, every 4^3 block one coarse cell
+    "periodic_hier_n1048576_mesh32_r4_p7_fp32": (1 << 20, "periodic", 32, 7, "fp32", (0, 0, 0), (1, 1, 1),
+                                                 "uniform_pm1", 1.0, 1, 4),
+    "periodic_hier_n1048576_mesh32_r4_p7_splitbf16": (1 << 20, "periodic", 32, 7, "splitbf16", (0, 0, 0),
+                                                      (1, 1, 1), "uniform_pm1", 1.0, 1, 4),
     # same particle density as the default (32 per cell), 8x smaller: the ncu profiling case
     "periodic_uniform_n131072_mesh16_p7_fp32": (1 << 17, "periodic", 16, 7, "fp32", (0, 0, 0), (1, 1, 1),
                                                  "uniform_pm1", 1.0),
@@ -89,7 +94,32 @@ L2_FLUSH_BYTES = 256 << 20
 def _wl(name: str):
     """(n, boundary, mesh, p, precision, box lo, box length, generator, sign, cutoff) of a workload."""
     w = WORKLOADS[name]
-    return tuple(w) + ((1,) if len(w) == 9 else ())
+    return tuple(w[:10]) + ((1,) if len(w) == 9 else ())
+
+
+def _refine(name: str) -> int:
+    """Refinement of a two-level workload (0: one level)."""
+    w = WORKLOADS.get(name, ())
+    return int(w[10]) if len(w) > 10 else 0
+
+
+def _oracle_eval(name, pos, q, cells, green):
+    """The oracle on target cells of workload `name`: the one-level or two-level definition."""
+    import oracle
+    n, boundary, mesh, p, prec, lo, ln, gen, sign, cut = _wl(name)
+    r = _refine(name)
+    if r > 1:
+        return oracle.pmmm_hier(pos, q, lo, ln, (mesh,) * 3, p, r, cut, boundary == "periodic", target_cells=cells,
+                                green_coarse=green)
+    return oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, cut, boundary == "periodic", target_cells=cells, green=green)
+
+
+def _oracle_green(name):
+    """Green-function table of the oracle for workload `name` (the coarse mesh's for two levels)."""
+    import oracle
+    n, boundary, mesh, p, prec, lo, ln, gen, sign, cut = _wl(name)
+    m = mesh // max(_refine(name), 1)
+    return oracle.green_table(lo, ln, (m,) * 3, p, cut, boundary == "periodic")
 
 
 def _inputs(name: str, rank: int):
@@ -249,7 +279,7 @@ def _cpu_baseline(name: str, pos, q, g, budget_s: float = 20.0):
     while True:
         cells = rng.choice(mesh ** 3, size=ncell, replace=False)
         t0 = time.perf_counter()
-        r = oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, cut, per, target_cells=cells, green=g)
+        r = _oracle_eval(name, pos, q, cells, g)
         dt = time.perf_counter() - t0
         done = int((~np.isnan(r["phi"])).sum())
         if dt >= 0.5 * budget_s or ncell >= mesh ** 3:
@@ -257,7 +287,7 @@ def _cpu_baseline(name: str, pos, q, g, budget_s: float = 20.0):
         t_one = dt
         ncell = min(mesh ** 3, int(ncell * max(2.0, 0.8 * budget_s / max(dt, 1e-3))))
     return {"value": done / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"FP64 oracle (cell-pair convolution of Eq. pmmm), one evaluation of the same {n}-particle "
+            "sample": f"FP64 oracle ({'two-level cell-pair definition, Sec. 5' if _refine(name) > 1 else 'cell-pair convolution of Eq. pmmm'}), one evaluation of the same {n}-particle "
                       f"workload restricted to {ncell} seeded target cells ({done} particles) after its Green-function "
                       f"table; {dt:.1f} s"}
 
@@ -293,14 +323,21 @@ def run_reference(args, rank, world):
         per = boundary == "periodic"
         systems = [_inputs(name, 0)]
     pos, q = systems[0]
-    g = oracle.green_table(lo, ln, (mesh,) * 3, p, cut, per)
+    hier = name in WORKLOADS and _refine(name) > 1
+    g = _oracle_green(name) if hier else oracle.green_table(lo, ln, (mesh,) * 3, p, cut, per)
+
+    def evaluate(pos, q, cells):
+        if hier:
+            return _oracle_eval(name, pos, q, cells, g)
+        return oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, cut, per, target_cells=cells, green=g)
+
     rng = synth.rng(777)
     # size one step to ~3 s so that warmup + steps end within a few minutes
     ncell = 8
     while True:
         cells = rng.choice(mesh ** 3, size=ncell, replace=False)
         t0 = time.perf_counter()
-        oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, cut, per, target_cells=cells, green=g)
+        evaluate(pos, q, cells)
         dt = time.perf_counter() - t0
         if dt > 1.5 or ncell >= mesh ** 3:
             break
@@ -310,7 +347,7 @@ def run_reference(args, rank, world):
         cells = rng.choice(mesh ** 3, size=ncell, replace=False)
         pos, q = systems[it % len(systems)]
         t0 = time.perf_counter()
-        r = oracle.pmmm(pos, q, lo, ln, (mesh,) * 3, p, cut, per, target_cells=cells, green=g)
+        r = evaluate(pos, q, cells)
         dt = time.perf_counter() - t0
         if it >= args.warmup:
             times.append(dt)
@@ -342,6 +379,13 @@ def _config(name, world, near="auto"):
                 "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
                 "launch": "CUDA graph of the whole batched evaluation", "near_field_kernel": near}
     n, boundary, mesh, p, prec, lo, ln, gen, sign, cut = _wl(name)
+    if _refine(name) > 1:
+        r = _refine(name)
+        return {"workload": name, "n_particles": n, "boundary": boundary, "mesh": [mesh] * 3, "refine": r,
+                "coarse_mesh": [mesh // r] * 3, "p": p, "cutoff_cells": (2 * cut + 1) ** 3, "distribution": gen,
+                "m2l": "split-BF16 tensor cores" if prec == "splitbf16" else "FP32 SIMT",
+                "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
+                "near_field_kernel": near}
     return {"workload": name, "n_particles": n, "boundary": boundary, "mesh": [mesh] * 3,
             "fft_grid": [mesh if boundary == "periodic" else 2 * mesh] * 3, "p": p, "cutoff_cells": (2 * cut + 1) ** 3,
             "distribution": gen, "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
@@ -363,9 +407,11 @@ def run_ours(args, rank, world, local_rank):
     pk._lib()  # fails loudly when the library is missing
     fp64 = prec == "fp64"
     dt = torch.float64 if fp64 else torch.float32
+    refine = _refine(name)
+    precision = {"fp64": pk.FP64, "fp32": pk.FP32, "splitbf16": pk.FP32_SPLITBF16_M2L}[prec]
     cfg = pk.Config(box_lo=lo, box_len=ln, mesh=(mesh,) * 3, p=p, cutoff=cut,
                     boundary=pk.PERIODIC if boundary == "periodic" else pk.OPEN,
-                    precision=pk.FP64 if fp64 else pk.FP32, sign=sign, near_field=_near(pk, args))
+                    precision=precision, sign=sign, near_field=_near(pk, args), refine=refine)
     stream = torch.cuda.current_stream()
     t_plan = time.perf_counter()
     plan = pk.Plan(cfg, stream)
@@ -445,6 +491,21 @@ def run_ours(args, rank, world, local_rank):
     pp_ms = statistics.median(stage_acc.get("near_field", [float("nan")]))
     mesh_ms = sum(statistics.median(stage_acc.get(s, [0.0])) for s in ("fft_forward", "m2l", "fft_inverse"))
     mesh_bytes = esz * (2 * C * K + 4 * 2 * C * Kh + 2 * CG * Kh)
+    bytes_model = "4B*(2CK + 8CKh + 2C_G Kh): M read, spectra written/read, G~ read, L written"
+    if refine > 1:
+        # two levels: fine M read twice (M2M, block transform), the coarse mesh stage, block spectra
+        # written and read twice, the block kernel spectra, kept outputs written and read, fine L written
+        Kc = K // refine ** 3
+        Khc = (mesh // refine) ** 2 * (mesh // refine // 2 + 1)
+        mb = 1
+        while mb < 2 * (cut + 1) * refine:
+            mb *= 2
+        Khh, W = mb * mb * (mb // 2 + 1), (2 * cut + 1) * refine
+        mesh_bytes = esz * (3 * C * K + 2 * C * Kc + 8 * C * Kc * Khh + 2 * CG * Khh + 2 * C * Kc * W ** 3
+                            + 8 * C * Khc + 2 * CG * Khc)
+        bytes_model = ("4B*(3CK + 2CKc + 8CKcKhh + 2C_G Khh + 2CKcW^3 + 8CKhc + 2C_G Khc): fine M read twice, "
+                       "coarse M written/read, block spectra written/read twice, block kernel spectra, kept "
+                       "outputs written/read, coarse spectra and kernel, fine L written")
     hbm, sm_max, peak_kind = _peaks()
     sm_clock = clocks.get("sm_max_mhz") or sm_max
     alu_peak = 2.0 * FP32_LANES_PER_SM * NUM_SMS * sm_max * 1e6 / 1e12
@@ -463,13 +524,10 @@ def run_ours(args, rank, world, local_rank):
     green = None
     pos64, q64 = pos_np.astype(npdt).astype(np.float64), q_np.astype(npdt).astype(np.float64)
     if not (args.no_accuracy and (args.no_cpu_baseline or world > 1)):
-        import oracle
-        green = oracle.green_table(lo, ln, (mesh,) * 3, p, cut, boundary == "periodic")
+        green = _oracle_green(name)
     if not args.no_accuracy:
-        import oracle
         cells = synth.rng(99).choice(mesh ** 3, size=4, replace=False)
-        r = oracle.pmmm(pos64, q64, lo, ln, (mesh,) * 3, p, cut, boundary == "periodic", target_cells=cells,
-                        green=green)
+        r = _oracle_eval(name, pos64, q64, cells, green)
         sel = ~np.isnan(r["phi"])
         plan.compute_raw(n, pos.data_ptr(), q.data_ptr(), phi.data_ptr(), force.data_ptr())
         f = force.cpu().numpy().astype(np.float64)[sel]
@@ -491,8 +549,7 @@ def run_ours(args, rank, world, local_rank):
                                    f"(FMA peak; HBM peak {hbm} GB/s {peak_kind})"},
         "mesh_roofline": {"bound": "hbm", "achieved": mesh_bytes / (mesh_ms * 1e-3) / 1e9, "peak": hbm,
                           "unit": "GB/s", "frac": mesh_bytes / (mesh_ms * 1e-3) / 1e9 / hbm,
-                          "bytes_model": "4B*(2CK + 8CKh + 2C_G Kh): M read, spectra written/read, G~ read, "
-                                         "L written", "stages": "fft_forward + m2l + fft_inverse",
+                          "bytes_model": bytes_model, "stages": "fft_forward + m2l + fft_inverse",
                           "peak_kind": peak_kind},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * esz * n,
                 "d2h_bytes_per_step": 4 * esz * n + 8},

@@ -85,7 +85,11 @@ typedef struct pmmm_config {
   double sign;         /* +1 Coulomb, -1 gravity */
   double ewald_alpha;  /* periodic splitting parameter; 0 -> 1.5 / min(box_len) (App. B.1 example) */
   int32_t ewald_nmax;  /* periodic lattice sums over |n|_2 <= nmax (both sums); 0 -> 5 */
-  int32_t reserved[7];
+  int32_t refine;      /* two-level PMMM (Sec. 5, hierarchical treatment): 0 or 1 -> one level;
+                        * r = 2, 4, 8 or 16 -> mesh is the fine mesh, every r^3 block of fine cells
+                        * one coarse cell (mesh divisible by r; the coarse mesh obeys the mesh rules
+                        * above); single-system evaluations only (pmmm_compute, pmmm_compute_host) */
+  int32_t reserved[6];
 } pmmm_config;
 
 typedef struct pmmm_plan pmmm_plan;
@@ -116,6 +120,14 @@ int pmmm_plan_reserve(pmmm_plan* plan, int64_t n_max);
  * FFTs of the (p+1)^2 channels, per-wavevector M2L (Eq. realmatrix), inverse
  * FFTs, periodic corrections (App. B.3), L2P with the order-one gradient
  * (Eqs. L2P, L2L, phigrad) and the (2c+1)^3-cell near field.
+ * Two-level plans (cfg.refine = r >= 2, Sec. 5 hierarchical treatment): the
+ * cell convolution becomes M2M of the fine multipoles to the coarse cells
+ * (Eq. M2M), the one-level convolution on the coarse mesh (its (2c+1)^3 nearest
+ * coarse cells masked, periodic corrections taken at the coarse level), the
+ * free-space M2L between the fine cells of every masked coarse block (a
+ * zero-padded block convolution, its (2c+1)^3 nearest fine cells masked) and L2L
+ * of the coarse locals to the fine centres (Eq. L2L); the near field covers the
+ * (2c+1)^3 nearest fine cells.
  *   n       number of particles (>= 0; n <= 2^31 - 1)
  *   pos     device, n x 3 positions (double for FP64, float otherwise)
  *   q       device, n charges / masses
@@ -225,7 +237,8 @@ enum {
   PMMM_INFO_LAUNCHES = 7,
   PMMM_INFO_SYSTEMS = 8,
   PMMM_INFO_TUNED_NEAR = 9, /* near-field kernel chosen by pmmm_plan_autotune (0: none, from the config) */
-  PMMM_INFO_M2L_TILE = 10   /* systems per CTA of the tensor-core batched M2L (32 or 64; default 64) */
+  PMMM_INFO_M2L_TILE = 10,  /* systems per CTA of the tensor-core batched M2L (32 or 64; default 64) */
+  PMMM_INFO_REFINE = 11     /* refinement of a two-level plan (1: one level) */
 };
 int pmmm_plan_info(pmmm_plan* plan, int what, int64_t* value);
 

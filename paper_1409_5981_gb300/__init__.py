@@ -27,7 +27,7 @@ EXPORT_PERM, EXPORT_SORTED_CELL, EXPORT_CELL_START = 1, 2, 3
 EXPORT_MULTIPOLE, EXPORT_LOCAL, EXPORT_CORR, EXPORT_FAR = 4, 5, 6, 7
 INFO_K, INFO_C, INFO_CG, INFO_KH, INFO_N, INFO_WORKSPACE_BYTES, INFO_LAUNCHES = 1, 2, 3, 4, 5, 6, 7
 INFO_SYSTEMS = 8
-INFO_TUNED_NEAR, INFO_M2L_TILE = 9, 10
+INFO_TUNED_NEAR, INFO_M2L_TILE, INFO_REFINE = 9, 10, 11
 MAX_SYSTEMS = 65535
 SUR_PARAMS, SUR_ADAM_M, SUR_ADAM_V, SUR_IN_SCALE, SUR_OUT_SCALE = 1, 2, 3, 4, 5
 SUR_INFO_STEP, SUR_INFO_FALLBACK, SUR_INFO_CLOW, SUR_INFO_CHIGH, SUR_INFO_ROWS = 1, 2, 3, 4, 5
@@ -54,7 +54,8 @@ class _Config(ctypes.Structure):
         ("sign", ctypes.c_double),
         ("ewald_alpha", ctypes.c_double),
         ("ewald_nmax", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("refine", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
     ]
 
 
@@ -187,6 +188,7 @@ class Config:
     ewald_alpha: float = 0.0
     ewald_nmax: int = 0
     near_field: int = NEAR_AUTO
+    refine: int = 0  # two-level PMMM (Sec. 5): r >= 2 -> every r^3 block of the mesh is one coarse cell
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -198,6 +200,7 @@ class Config:
         c.p, c.cutoff, c.boundary, c.precision = int(self.p), int(self.cutoff), int(self.boundary), int(self.precision)
         c.sign, c.ewald_alpha, c.ewald_nmax = float(self.sign), float(self.ewald_alpha), int(self.ewald_nmax)
         c.near_field = int(self.near_field)
+        c.refine = int(self.refine)
         return c
 
     @property

@@ -91,6 +91,43 @@ PMMM_HD void regular_stream(T x, T y, T z, F&& f) {
   }
 }
 
+// The regular harmonics of regular_real for a runtime order p, handed to a
+// callback f(c, value) with c the real storage index of App. A.7 (used for the
+// small translation tables built once per plan).
+template <typename T, class F>
+PMMM_HD void regular_real_rt(int p, T x, T y, T z, F&& f) {
+  const T r2 = x * x + y * y + z * z;
+  T mmr = T(1), mmi = T(0);
+  for (int m = 0; m <= p; ++m) {
+    if (m > 0) {
+      const T s = T(-1) / T(2 * m);
+      const T nr = s * (x * mmr - y * mmi);
+      const T ni = s * (x * mmi + y * mmr);
+      mmr = nr;
+      mmi = ni;
+    }
+    f(sidx(m, m), mmr);
+    if (m > 0) f(sidx(m, -m), mmi);
+    T ar = mmr, ai = mmi, br = T(0), bi = T(0);
+    if (m + 1 <= p) {
+      br = z * mmr;
+      bi = z * mmi;
+      f(sidx(m + 1, m), br);
+      if (m > 0) f(sidx(m + 1, -m), bi);
+    }
+    for (int l = m + 2; l <= p; ++l) {
+      const T c1 = T(2 * l - 1) / T((l - m) * (l + m));
+      const T c2 = T(1) / T((l - m) * (l + m));
+      const T cr = c1 * z * br - c2 * r2 * ar;
+      const T ci = c1 * z * bi - c2 * r2 * ai;
+      f(sidx(l, m), cr);
+      if (m > 0) f(sidx(l, -m), ci);
+      ar = br; ai = bi;
+      br = cr; bi = ci;
+    }
+  }
+}
+
 // Singular harmonics S_l^m for one m >= 0 and l = m .. J, handed to a callback
 // f(l, Re S_l^m, Im S_l^m).  Runtime orders (used by the Green function set-up).
 template <typename T, typename F>

@@ -85,10 +85,41 @@ struct CorrParams {
   double c_self;       // 2 alpha / sqrt(pi)
   int periodic;
   int64_t ksys;        // cells per system (corrections corr[16 s ...] of system s = cell / ksys)
+  // two-level plans: the corrections are those of the coarse level (positions
+  // relative to the coarse centre, Q of the coarse cell in the self term)
+  int refine;          // 0 / 1: one level; r >= 2: coarse cell = r^3 fine cells
+  int nf[3], nc[3];    // fine and coarse cells per axis
+  double cs[3];        // fine cell sides in units of hs
 };
 cudaError_t launch_l2p(int p, bool fp64, const void* part, const uint32_t* keys, int64_t n, const void* L,
                        int64_t K, const double* corr, const double* cellq, CorrParams cp, void* far,
                        cudaStream_t s, int* nlaunch);
+
+// ---------------------------------------------------------------- hier.cu
+// Two-level PMMM (Sec. 5, hierarchical treatment): geometry of the levels.
+struct HierGeo {
+  int r, c, m;        // refinement per axis, cutoff, block transform length (>= 2 (c+1) r)
+  int nf[3], nc[3];   // fine and coarse cells per axis
+  int wavemajor;      // block spectra [k][channel][coarse cell] (else [channel][coarse cell][k])
+};
+bool hier_block_fits(const HierGeo& h, bool fp64, int C);
+// R(coarse centre - child centre) in units of hs_f for the r^3 children, real storage, [r^3][C]
+cudaError_t launch_hier_rtab(const HierGeo& h, int p, bool fp64, const double* cs, void* rtab, cudaStream_t s);
+// coarse multipoles [C][Kc] from the fine ones [C][Kf] (Eq. M2M)
+cudaError_t launch_hier_m2m(const HierGeo& h, int p, bool fp64, const void* Mf, void* Mc, const void* rtab,
+                            cudaStream_t s, int* nlaunch);
+// coarse per-cell sums [5][Kc] of the periodic corrections from the fine ones [5][Kf]
+cudaError_t launch_hier_cellsum(const HierGeo& h, const double* fine, double* coarse, const double* cs,
+                                cudaStream_t s, int* nlaunch);
+// block spectra of the fine multipoles of every coarse cell (tw: exp(-2 pi i j / m), j < m)
+cudaError_t launch_hier_forward(const HierGeo& h, int C, bool fp64, const void* Mf, void* spec, const void* tw,
+                                cudaStream_t s, int* nlaunch);
+// kept outputs [C][Kc][W^3] of the block convolution from the local block spectra
+cudaError_t launch_hier_inverse(const HierGeo& h, int C, bool fp64, const void* spec, void* region, const void* tw,
+                                cudaStream_t s, int* nlaunch);
+// fine locals [C][Kf] = L2L(coarse locals [C][Kc]) + the kept block outputs
+cudaError_t launch_hier_local(const HierGeo& h, int p, bool fp64, const void* Lc, const void* region,
+                              const void* rtab, void* Lf, int periodic, cudaStream_t s, int* nlaunch);
 
 // ---------------------------------------------------------------- fft.cu
 struct FftTw {

@@ -200,10 +200,20 @@ __global__ void __launch_bounds__(128) l2p_kernel(const T* __restrict__ part, co
   T g[3] = {gx * ih2, gy * ih2, gz * ih2};
   if (cp.periodic) {
     const T hs = (T)cp.hs;
-    const T rel[3] = {r.x * hs, r.y * hs, r.z * hs};
+    T rel[3] = {r.x * hs, r.y * hs, r.z * hs};
+    int64_t qcell = cell;
+    if (cp.refine > 1) {
+      // two-level plan: position relative to the coarse centre, charge of the coarse cell
+      const int R = cp.refine;
+      const int64_t ix = cell % cp.nf[0], iy = (cell / cp.nf[0]) % cp.nf[1], iz = cell / ((int64_t)cp.nf[0] * cp.nf[1]);
+      rel[0] += (T)(((double)(ix % R) + 0.5 - 0.5 * R) * cp.cs[0] * cp.hs);
+      rel[1] += (T)(((double)(iy % R) + 0.5 - 0.5 * R) * cp.cs[1] * cp.hs);
+      rel[2] += (T)(((double)(iz % R) + 0.5 - 0.5 * R) * cp.cs[2] * cp.hs);
+      qcell = ix / R + (int64_t)cp.nc[0] * (iy / R + (int64_t)cp.nc[1] * (iz / R));
+    }
     const T rr = rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2];
     const T qf = (T)corr[4];
-    phi += (T)corr[0] + qf * (rr - (T)cp.c_charged) - (T)cp.c_self * (T)cellq[cell];
+    phi += (T)corr[0] + qf * (rr - (T)cp.c_charged) - (T)cp.c_self * (T)cellq[qcell];
 #pragma unroll
     for (int a = 0; a < 3; ++a) g[a] += T(2) * qf * rel[a];
     // the dipole term corrects L_1 (App. B.3), which exists only for p >= 1

@@ -71,6 +71,16 @@ struct pmmm_plan {
   // choices of pmmm_plan_autotune: near-field kernel (0: from the config), tensor-core M2L system tile
   int tuned_near = 0;
   int m2l_tile = 64;
+  // two-level evaluation (cfg.refine >= 2): the coarse level runs on a one-level
+  // plan of the coarse mesh; the block convolution of the fine level takes its
+  // free-space kernel spectra and twiddles from an open plan of (m/2)^3 fine cells
+  bool hier = false;
+  pmmm::HierGeo hg{};
+  pmmm_plan* coarse = nullptr;
+  pmmm_plan* block = nullptr;
+  void *hspecM = nullptr, *hspecL = nullptr;  // block spectra, C * Kc * m^2 (m/2+1) complex
+  void* hregion = nullptr;                    // kept block outputs, C * Kc * ((2c+1) r)^3
+  void* hrtab = nullptr;                      // R(coarse centre - child centre), r^3 * C
   // particle workspace
   int64_t cap = 0;
   SortWork sw{};

@@ -100,6 +100,10 @@ void free_all(pmmm_plan* pl) {
   dfree(pl, pl->err);
   dfree(pl, pl->m2l_tab);
   dfree(pl, pl->m2l_tab_tc);
+  dfree(pl, pl->hspecM); dfree(pl, pl->hspecL); dfree(pl, pl->hregion); dfree(pl, pl->hrtab);
+  if (pl->coarse) pmmm_plan_destroy(pl->coarse);
+  if (pl->block) pmmm_plan_destroy(pl->block);
+  pl->coarse = pl->block = nullptr;
   dfree(pl, pl->hpos); dfree(pl, pl->hq); dfree(pl, pl->hphi); dfree(pl, pl->hforce);
   if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
   pl->gexec = nullptr;
@@ -138,6 +142,7 @@ cudaError_t alloc_mesh(pmmm_plan* pl, int B) {
 }
 
 int ensure_particles(pmmm_plan* pl, int64_t n);
+int ensure_m2l_tables(pmmm_plan* pl);
 
 // Grows the mesh workspace to B systems (the particle workspace, sized by the
 // cell count, is rebuilt with it).
@@ -178,6 +183,12 @@ int validate(const pmmm_config* c) {
   }
   const int64_t K = (int64_t)c->mesh[0] * c->mesh[1] * c->mesh[2];
   if (K > (int64_t)1 << 28) return PMMM_ERR_UNSUPPORTED;
+  if (c->refine < 0) return PMMM_ERR_INVALID_ARG;
+  if (c->refine > 1) {
+    if (!pow2(c->refine) || c->refine > 16) return PMMM_ERR_UNSUPPORTED;
+    for (int a = 0; a < 3; ++a)
+      if (c->mesh[a] % c->refine != 0 || c->mesh[a] / c->refine < 2) return PMMM_ERR_UNSUPPORTED;
+  }
   return PMMM_OK;
 }
 
@@ -269,6 +280,56 @@ int build_green(pmmm_plan* pl) {
   return map_cuda(e);
 }
 
+// Two-level plan (Sec. 5, hierarchical treatment): the coarse one-level plan,
+// the open plan of (m/2)^3 fine cells whose kernel spectra are those of the
+// fine-level block convolution (free-space S(d h_fine), nearest (2c+1)^3 masked,
+// offsets up to m/2 - 1 >= (c+1) r - 1), the block workspace and the child table.
+int setup_hier(pmmm_plan* pl) {
+  const pmmm_config& cf = pl->cfg;
+  HierGeo& h = pl->hg;
+  h.r = cf.refine;
+  h.c = cf.cutoff;
+  h.m = 1;
+  while (h.m < 2 * (h.c + 1) * h.r) h.m <<= 1;
+  pmmm_config cc = cf;
+  cc.refine = 0;
+  for (int a = 0; a < 3; ++a) {
+    h.nf[a] = cf.mesh[a];
+    h.nc[a] = cf.mesh[a] / h.r;
+    cc.mesh[a] = h.nc[a];
+  }
+  int rc = pmmm_plan_create(&cc, pl->stream, &pl->coarse);
+  if (rc != PMMM_OK) return rc;
+  pmmm_config bc;
+  pmmm_config_init(&bc);
+  for (int a = 0; a < 3; ++a) {
+    bc.box_lo[a] = 0.0;
+    bc.mesh[a] = h.m / 2;
+    bc.box_len[a] = (h.m / 2) * pl->g.h[a];
+  }
+  bc.p = cf.p;
+  bc.cutoff = cf.cutoff;
+  bc.boundary = PMMM_OPEN;
+  bc.precision = cf.precision;
+  rc = pmmm_plan_create(&bc, pl->stream, &pl->block);
+  if (rc != PMMM_OK) return rc;
+  const int64_t Kc = pl->coarse->d.K, Khh = pl->block->d.Kh;
+  h.wavemajor = (pl->m2l_tc || m2l_batched_gemm(pl->fp64, pl->p, (int)Kc)) ? 1 : 0;
+  if (!h.wavemajor && Kc > 65535) return PMMM_ERR_UNSUPPORTED;
+  if (!hier_block_fits(h, pl->fp64, pl->C)) return PMMM_ERR_UNSUPPORTED;
+  const size_t T = pl->tsize, W = (size_t)(2 * h.c + 1) * h.r;
+  cudaError_t e = dalloc(pl, &pl->hspecM, 2 * T * pl->C * (size_t)Kc * Khh);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->hspecL, 2 * T * pl->C * (size_t)Kc * Khh);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->hregion, T * pl->C * (size_t)Kc * W * W * W);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->hrtab, T * pl->C * (size_t)h.r * h.r * h.r);
+  if (e == cudaSuccess) e = launch_hier_rtab(h, pl->p, pl->fp64, pl->g.cs, pl->hrtab, pl->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
+  if (e != cudaSuccess) return map_cuda(e);
+  if (h.wavemajor) rc = ensure_m2l_tables(pl);
+  if (rc == PMMM_OK) pl->hier = true;
+  return rc;
+}
+
 int read_device_status(pmmm_plan* pl) {
   int h = 0;
   cudaError_t e = cudaMemcpyAsync(&h, pl->err, sizeof(int), cudaMemcpyDeviceToHost, pl->stream);
@@ -283,6 +344,70 @@ int read_device_status(pmmm_plan* pl) {
 
 void mark(pmmm_plan* pl, int st) {
   if (pl->timing && !pl->capturing) cudaEventRecord(pl->ev[st], pl->stream);
+}
+
+// The cell convolution of Sec. 2.1 for B systems: forward FFTs of the C
+// channels, per-wavevector M2L, inverse FFTs (M -> L of the plan).
+cudaError_t mesh_stage(pmmm_plan* pl, int B, int* nl) {
+  cudaStream_t s = pl->stream;
+  const bool fp64 = pl->fp64;
+  cudaError_t e = cudaSuccess;
+  FftTw tw{pl->twx, pl->twy, pl->twz};
+  const bool fused = fft_fused_applies(fp64, pl->d);
+  e = fused ? launch_fft_fused_forward(pl->M, pl->specM, pl->d, pl->C * B, tw, s, nl)
+            : launch_fft_forward(fp64, pl->M, pl->specM, pl->d, pl->C * B, tw, s, nl);
+  if (e != cudaSuccess) return e;
+  mark(pl, ST_M2L);
+  const int64_t R = (int64_t)pl->C * B;
+  if (B == 1) {
+    e = launch_m2l(pl->p, fp64, pl->specM, pl->G, pl->specL, pl->d.Kh, s, nl);
+  } else if (pl->m2l_tc || m2l_batched_gemm(fp64, pl->p, B)) {
+    // matrix products per wavevector on wavevector-major spectra:
+    // specM -> specL (transposed) -> M2L -> specM -> specL (channel-major)
+    e = launch_transpose(fp64, pl->specM, pl->specL, R, pl->d.Kh, s, nl);
+    if (e == cudaSuccess)
+      e = pl->m2l_tc ? launch_m2l_tc(pl->specL, pl->G, pl->specM, pl->m2l_tab_tc, pl->p, B, pl->d.Kh, pl->num_sms,
+                                     pl->m2l_tile, pl->err, s, nl)
+                     : launch_m2l_batched(fp64, pl->specL, pl->G, pl->specM, pl->m2l_tab, pl->p, B, pl->d.Kh, s, nl);
+    if (e == cudaSuccess) e = launch_transpose(fp64, pl->specM, pl->specL, pl->d.Kh, R, s, nl);
+  } else {
+    e = launch_m2l_systems(pl->p, fp64, pl->specM, pl->G, pl->specL, pl->d.Kh, B, s, nl);
+  }
+  if (e != cudaSuccess) return e;
+  mark(pl, ST_FFT_INV);
+  return fused ? launch_fft_fused_inverse(pl->specL, pl->L, pl->d, pl->C * B, tw, s, nl)
+               : launch_fft_inverse(fp64, pl->specL, pl->L, pl->d, pl->C * B, tw, s, nl);
+}
+
+// Two-level cell convolution (Sec. 5, hierarchical treatment): coarse
+// multipoles by M2M, the one-level convolution on the coarse mesh, the block
+// convolution of the fine level, and the fine locals as L2L of the coarse ones
+// plus the kept block outputs (M of the plan -> L of the plan).
+cudaError_t hier_stage(pmmm_plan* pl, int* nl) {
+  cudaStream_t s = pl->stream;
+  const HierGeo& h = pl->hg;
+  pmmm_plan* cp = pl->coarse;
+  pmmm_plan* bp = pl->block;
+  const bool fp64 = pl->fp64;
+  const int64_t Kc = cp->d.K, Khh = bp->d.Kh;
+  cudaError_t e = launch_hier_m2m(h, pl->p, fp64, pl->M, cp->M, pl->hrtab, s, nl);
+  if (e == cudaSuccess) e = mesh_stage(cp, 1, nl);
+  if (e == cudaSuccess) e = launch_hier_forward(h, pl->C, fp64, pl->M, pl->hspecM, bp->twx, s, nl);
+  if (e != cudaSuccess) return e;
+  mark(pl, ST_M2L);
+  if (!h.wavemajor)
+    e = launch_m2l_systems(pl->p, fp64, pl->hspecM, bp->G, pl->hspecL, Khh, (int)Kc, s, nl);
+  else if (pl->m2l_tc)
+    e = launch_m2l_tc(pl->hspecM, bp->G, pl->hspecL, pl->m2l_tab_tc, pl->p, (int)Kc, Khh, pl->num_sms, pl->m2l_tile,
+                      pl->err, s, nl);
+  else
+    e = launch_m2l_batched(fp64, pl->hspecM, bp->G, pl->hspecL, pl->m2l_tab, pl->p, (int)Kc, Khh, s, nl);
+  if (e != cudaSuccess) return e;
+  mark(pl, ST_FFT_INV);
+  e = launch_hier_inverse(h, pl->C, fp64, pl->hspecL, pl->hregion, bp->twx, s, nl);
+  if (e == cudaSuccess)
+    e = launch_hier_local(h, pl->p, fp64, cp->L, pl->hregion, pl->hrtab, pl->L, pl->g.periodic, s, nl);
+  return e;
 }
 
 // One evaluation of B systems (B = 1: the single-system path; B > 1: the
@@ -326,42 +451,20 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
   mark(pl, ST_P2M);
   CK(launch_p2m(pl->p, fp64, pl->part, pl->cs, K, pl->M, pl->cellsum, pl->cellsum + K, sparse, s, &nl));
   mark(pl, ST_FFT_FWD);
-  {
-    FftTw tw{pl->twx, pl->twy, pl->twz};
-    const bool fused = fft_fused_applies(fp64, pl->d);
-    if (fused)
-      CK(launch_fft_fused_forward(pl->M, pl->specM, pl->d, pl->C * B, tw, s, &nl));
-    else
-      CK(launch_fft_forward(fp64, pl->M, pl->specM, pl->d, pl->C * B, tw, s, &nl));
-    mark(pl, ST_M2L);
-    const int64_t R = (int64_t)pl->C * B;
-    if (B == 1) {
-      CK(launch_m2l(pl->p, fp64, pl->specM, pl->G, pl->specL, pl->d.Kh, s, &nl));
-    } else if (pl->m2l_tc || m2l_batched_gemm(fp64, pl->p, B)) {
-      // matrix products per wavevector on wavevector-major spectra:
-      // specM -> specL (transposed) -> M2L -> specM -> specL (channel-major)
-      CK(launch_transpose(fp64, pl->specM, pl->specL, R, pl->d.Kh, s, &nl));
-      if (pl->m2l_tc)
-        CK(launch_m2l_tc(pl->specL, pl->G, pl->specM, pl->m2l_tab_tc, pl->p, B, pl->d.Kh, pl->num_sms, pl->m2l_tile,
-                         pl->err, s, &nl));
-      else
-        CK(launch_m2l_batched(fp64, pl->specL, pl->G, pl->specM, pl->m2l_tab, pl->p, B, pl->d.Kh, s, &nl));
-      CK(launch_transpose(fp64, pl->specM, pl->specL, pl->d.Kh, R, s, &nl));
-    } else {
-      CK(launch_m2l_systems(pl->p, fp64, pl->specM, pl->G, pl->specL, pl->d.Kh, B, s, &nl));
-    }
-    mark(pl, ST_FFT_INV);
-    if (fused)
-      CK(launch_fft_fused_inverse(pl->specL, pl->L, pl->d, pl->C * B, tw, s, &nl));
-    else
-      CK(launch_fft_inverse(fp64, pl->specL, pl->L, pl->d, pl->C * B, tw, s, &nl));
-  }
+  CK(pl->hier ? hier_stage(pl, &nl) : mesh_stage(pl, B, &nl));
   mark(pl, ST_L2P);
   if (pl->g.periodic) {
-    if (B == 1)
+    if (pl->hier) {
+      // the corrections belong to the coarse level (its Ewald split, its cells)
+      pmmm_plan* cp = pl->coarse;
+      CK(launch_hier_cellsum(pl->hg, pl->cellsum, cp->cellsum, pl->g.cs, s, &nl));
+      CK(launch_corrections(cp->cellsum, cp->cellsum + cp->d.K, cp->d.K, cp->g.hs, pl->g.V, pl->partial, pl->corr, s,
+                            &nl));
+    } else if (B == 1) {
       CK(launch_corrections(pl->cellsum, pl->cellsum + K, K, pl->g.hs, pl->g.V, pl->partial, pl->corr, s, &nl));
-    else
+    } else {
       CK(launch_corrections_batched(pl->cellsum, K, Ks, B, pl->g.hs, pl->g.V, pl->bpartial, pl->corr, s, &nl));
+    }
   }
   {
     CorrParams cp;
@@ -374,6 +477,13 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
     cp.c_self = 2.0 * pl->g.alpha * 0.56418958354775628695;  // 2 alpha / sqrt(pi)
     cp.periodic = pl->g.periodic;
     cp.ksys = Ks;
+    cp.refine = pl->hier ? pl->hg.r : 0;
+    for (int a = 0; a < 3; ++a) {
+      cp.nf[a] = pl->g.n[a];
+      cp.nc[a] = pl->hier ? pl->hg.nc[a] : pl->g.n[a];
+      cp.cs[a] = pl->g.cs[a];
+    }
+    const double* cellq = pl->hier ? pl->coarse->cellsum : pl->cellsum;
     const void* Luse = pl->L;
     int puse = pl->p;
     if (pl->hook) {
@@ -381,7 +491,7 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
       Luse = pl->hook->L;
       puse = pl->hook->p_l2p;
     }
-    CK(launch_l2p(puse, fp64, pl->part, pl->keys_sorted, n, Luse, K, pl->corr, pl->cellsum, cp, pl->far, s, &nl));
+    CK(launch_l2p(puse, fp64, pl->part, pl->keys_sorted, n, Luse, K, pl->corr, cellq, cp, pl->far, s, &nl));
   }
   mark(pl, ST_PP);
   {
@@ -424,12 +534,33 @@ done:
 // when they equal the last upload).  Returns the particle count in *n.
 int upload_offsets(pmmm_plan* pl, int B, const int64_t* off, int64_t* n) {
   if (!off || off[0] != 0) return PMMM_ERR_INVALID_ARG;
+  if (pl->hier && B > 1) return PMMM_ERR_UNSUPPORTED;  // two-level plans evaluate one system
   for (int s = 0; s < B; ++s)
     if (off[s + 1] < off[s]) return PMMM_ERR_INVALID_ARG;
   if (off[B] > INT32_MAX) return PMMM_ERR_INVALID_ARG;
   *n = off[B];
   int rc = ensure_systems(pl, B);
+  if (rc == PMMM_OK) rc = ensure_m2l_tables(pl);
   if (rc != PMMM_OK) return rc;
+  if (pl->offsets_up.size() == (size_t)B + 1 && memcmp(pl->offsets_up.data(), off, sizeof(int64_t) * (B + 1)) == 0)
+    return PMMM_OK;
+  // the staging buffer may still feed an earlier copy on the stream
+  cudaError_t e = cudaStreamSynchronize(pl->stream);
+  if (e == cudaSuccess) {
+    memcpy(pl->offsets_pinned, off, sizeof(int64_t) * (B + 1));
+    e = cudaMemcpyAsync(pl->offsets_d, pl->offsets_pinned, sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice,
+                        pl->stream);
+  }
+  if (e != cudaSuccess) {
+    pl->offsets_up.clear();
+    return map_cuda(e);
+  }
+  pl->offsets_up.assign(off, off + B + 1);
+  return PMMM_OK;
+}
+
+// Entry tables of the matrix-product M2L (SIMT and, for split-BF16 plans, tensor core).
+int ensure_m2l_tables(pmmm_plan* pl) {
   if (!pl->m2l_tab) {
     std::vector<int> t = build_m2l_table_int4(pl->p);
     void* v = nullptr;
@@ -452,20 +583,6 @@ int upload_offsets(pmmm_plan* pl, int B, const int64_t* off, int64_t* n) {
     }
     pl->m2l_tab_tc = (uint32_t*)v;
   }
-  if (pl->offsets_up.size() == (size_t)B + 1 && memcmp(pl->offsets_up.data(), off, sizeof(int64_t) * (B + 1)) == 0)
-    return PMMM_OK;
-  // the staging buffer may still feed an earlier copy on the stream
-  cudaError_t e = cudaStreamSynchronize(pl->stream);
-  if (e == cudaSuccess) {
-    memcpy(pl->offsets_pinned, off, sizeof(int64_t) * (B + 1));
-    e = cudaMemcpyAsync(pl->offsets_d, pl->offsets_pinned, sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice,
-                        pl->stream);
-  }
-  if (e != cudaSuccess) {
-    pl->offsets_up.clear();
-    return map_cuda(e);
-  }
-  pl->offsets_up.assign(off, off + B + 1);
   return PMMM_OK;
 }
 
@@ -645,6 +762,7 @@ int pmmm_plan_create(const pmmm_config* cfg, void* stream, pmmm_plan** out) {
     return rc;
   }
   rc = build_green(pl);
+  if (rc == PMMM_OK && cfg->refine > 1) rc = setup_hier(pl);
   if (rc != PMMM_OK) {
     free_all(pl);
     delete pl;
@@ -670,6 +788,7 @@ int pmmm_plan_reserve(pmmm_plan* pl, int64_t n) {
 int pmmm_plan_reserve_batched(pmmm_plan* pl, int32_t nsys, int64_t n) {
   if (!pl || nsys < 1 || nsys > PMMM_MAX_SYSTEMS || n < 0 || n > INT32_MAX) return PMMM_ERR_INVALID_ARG;
   if (pl->d.K * nsys > ((int64_t)1 << 30)) return PMMM_ERR_UNSUPPORTED;
+  if (pl->hier && nsys > 1) return PMMM_ERR_UNSUPPORTED;
   int rc = ensure_systems(pl, nsys);
   if (rc == PMMM_OK) rc = ensure_particles(pl, n);
   return rc;
@@ -870,7 +989,7 @@ int pmmm_plan_export(pmmm_plan* pl, int what, void* dst, size_t bytes) {
       if (bytes != sizeof(double) * 8 * (size_t)B) return PMMM_ERR_INVALID_ARG;
       std::vector<double> c(16 * (size_t)B);
       e = cudaMemcpy(c.data(), pl->corr, sizeof(double) * c.size(), cudaMemcpyDeviceToHost);
-      const double hs = pl->g.hs;
+      const double hs = pl->hier ? pl->coarse->g.hs : pl->g.hs;  // sums of the level that is corrected
       for (int b = 0; b < B; ++b) {
         const double* cb = c.data() + 16 * (size_t)b;
         double* o = (double*)dst + 8 * (size_t)b;
@@ -911,11 +1030,15 @@ int pmmm_plan_info(pmmm_plan* pl, int what, int64_t* value) {
     case PMMM_INFO_CG: *value = pl->CG; break;
     case PMMM_INFO_KH: *value = pl->d.Kh; break;
     case PMMM_INFO_N: *value = pl->n_last; break;
-    case PMMM_INFO_WORKSPACE_BYTES: *value = (int64_t)pl->ws_bytes; break;
+    case PMMM_INFO_WORKSPACE_BYTES:
+      *value = (int64_t)pl->ws_bytes + (pl->coarse ? (int64_t)pl->coarse->ws_bytes : 0) +
+               (pl->block ? (int64_t)pl->block->ws_bytes : 0);
+      break;
     case PMMM_INFO_LAUNCHES: *value = pl->launches; break;
     case PMMM_INFO_SYSTEMS: *value = pl->nsys_last; break;
     case PMMM_INFO_TUNED_NEAR: *value = pl->tuned_near; break;
     case PMMM_INFO_M2L_TILE: *value = pl->m2l_tile; break;
+    case PMMM_INFO_REFINE: *value = pl->hier ? pl->hg.r : 1; break;
     default: return PMMM_ERR_INVALID_ARG;
   }
   return PMMM_OK;

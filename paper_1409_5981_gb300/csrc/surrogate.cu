@@ -249,7 +249,7 @@ int pmmm_surrogate_create(const pmmm_config* cfg, int32_t p_high, void* stream, 
   if (!out || !cfg) return PMMM_ERR_INVALID_ARG;
   *out = nullptr;
   if (cfg->p != 3 || p_high <= 3 || p_high > 10 || cfg->cutoff != 1) return PMMM_ERR_UNSUPPORTED;
-  if (cfg->precision != PMMM_FP32) return PMMM_ERR_UNSUPPORTED;
+  if (cfg->precision != PMMM_FP32 || cfg->refine > 1) return PMMM_ERR_UNSUPPORTED;
   pmmm_surrogate* s = new (std::nothrow) pmmm_surrogate();
   if (!s) return PMMM_ERR_OOM;
   s->stream = (cudaStream_t)stream;
