@@ -121,8 +121,8 @@ int pmmm_plan_reserve(pmmm_plan* plan, int64_t n_max);
  * FFTs, periodic corrections (App. B.3), L2P with the order-one gradient
  * (Eqs. L2P, L2L, phigrad) and the (2c+1)^3-cell near field.
  * Two-level plans (cfg.refine = r >= 2, Sec. 5 hierarchical treatment): the
- * cell convolution becomes M2M of the fine multipoles to the coarse cells
- * (Eq. M2M), the one-level convolution on the coarse mesh (its (2c+1)^3 nearest
+ * cell convolution becomes P2M about the coarse centres (Eq. P2M), the
+ * one-level convolution on the coarse mesh (its (2c+1)^3 nearest
  * coarse cells masked, periodic corrections taken at the coarse level), the
  * free-space M2L between the fine cells of every masked coarse block (a
  * zero-padded block convolution, its (2c+1)^3 nearest fine cells masked) and L2L

@@ -91,6 +91,16 @@ struct CorrParams {
   int nf[3], nc[3];    // fine and coarse cells per axis
   double cs[3];        // fine cell sides in units of hs
 };
+// Two-level plans: multipoles of the coarse cells (r^3 fine cells each) from the
+// particles sorted by fine cell, and the coarse per-cell sums [5][Kc].
+struct CoarseGeo {
+  int r;
+  int nf[3], nc[3];
+  int64_t Kc;
+  double cs[3];  // fine cell sides in units of the fine hs
+};
+cudaError_t launch_p2m_coarse(int p, bool fp64, const void* part, const int* cell_start, const CoarseGeo& cg,
+                              void* Mc, double* cellsum, cudaStream_t s, int* nlaunch);
 cudaError_t launch_l2p(int p, bool fp64, const void* part, const uint32_t* keys, int64_t n, const void* L,
                        int64_t K, const double* corr, const double* cellq, CorrParams cp, void* far,
                        cudaStream_t s, int* nlaunch);
@@ -105,21 +115,20 @@ struct HierGeo {
 bool hier_block_fits(const HierGeo& h, bool fp64, int C);
 // R(coarse centre - child centre) in units of hs_f for the r^3 children, real storage, [r^3][C]
 cudaError_t launch_hier_rtab(const HierGeo& h, int p, bool fp64, const double* cs, void* rtab, cudaStream_t s);
-// coarse multipoles [C][Kc] from the fine ones [C][Kf] (Eq. M2M)
-cudaError_t launch_hier_m2m(const HierGeo& h, int p, bool fp64, const void* Mf, void* Mc, const void* rtab,
-                            cudaStream_t s, int* nlaunch);
-// coarse per-cell sums [5][Kc] of the periodic corrections from the fine ones [5][Kf]
-cudaError_t launch_hier_cellsum(const HierGeo& h, const double* fine, double* coarse, const double* cs,
-                                cudaStream_t s, int* nlaunch);
+// whether the L2L child matrices (r^3 C^2 values) are built
+bool hier_use_matrices(const HierGeo& h, int p);
+// the L2L child matrices (coarse -> child), [r^3][C][C]
+cudaError_t launch_hier_matrices(const HierGeo& h, int p, bool fp64, const void* rtab, void* um, cudaStream_t s);
 // block spectra of the fine multipoles of every coarse cell (tw: exp(-2 pi i j / m), j < m)
 cudaError_t launch_hier_forward(const HierGeo& h, int C, bool fp64, const void* Mf, void* spec, const void* tw,
                                 cudaStream_t s, int* nlaunch);
 // kept outputs [C][Kc][W^3] of the block convolution from the local block spectra
 cudaError_t launch_hier_inverse(const HierGeo& h, int C, bool fp64, const void* spec, void* region, const void* tw,
                                 cudaStream_t s, int* nlaunch);
-// fine locals [C][Kf] = L2L(coarse locals [C][Kc]) + the kept block outputs
+// fine locals [C][Kf] = L2L(coarse locals [C][Kc]) + the kept block outputs (L2L through um when not null)
 cudaError_t launch_hier_local(const HierGeo& h, int p, bool fp64, const void* Lc, const void* region,
-                              const void* rtab, void* Lf, int periodic, cudaStream_t s, int* nlaunch);
+                              const void* rtab, const void* um, void* Lf, int periodic, cudaStream_t s,
+                              int* nlaunch);
 
 // ---------------------------------------------------------------- fft.cu
 struct FftTw {

@@ -169,6 +169,80 @@ __global__ void __launch_bounds__(256) p2m_cell_kernel(const T* __restrict__ par
   }
 }
 
+// Two-level plans (Sec. 5, hierarchical treatment): the multipoles of the coarse
+// cells straight from the particles (Eq. P2M about the coarse centres), with the
+// coarse per-cell sums of the periodic corrections.  One block per coarse cell;
+// thread t takes the particles of the cell's r^3 fine cells whose running index
+// is t modulo the block size (an even share whatever the fine occupancies);
+// positions move to the coarse frame, u_c = (u_f + d_a) / r with d_a the fine
+// centre minus the coarse centre in fine units; warp butterflies, then a
+// fixed-order sum over the warps in shared memory.
+constexpr int P2MC_THREADS = 256;
+
+template <int P, typename T>
+__global__ void __launch_bounds__(P2MC_THREADS) p2m_coarse_kernel(const T* __restrict__ part,
+                                                                  const int* __restrict__ cs, CoarseGeo cg,
+                                                                  T* __restrict__ Mc, double* __restrict__ cellsum) {
+  constexpr int C = (P + 1) * (P + 1), NW = P2MC_THREADS / 32;
+  __shared__ T red[NW][C + 5];
+  const int64_t S = blockIdx.x;
+  const int r = cg.r, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Sx = (int)(S % cg.nc[0]), Sy = (int)((S / cg.nc[0]) % cg.nc[1]), Sz = (int)(S / ((int64_t)cg.nc[0] * cg.nc[1]));
+  const T ir = T(1) / T(r);
+  T acc[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) acc[c] = T(0);
+  T sq = 0, sx = 0, sy = 0, sz = 0, sr = 0;
+  int run = 0;
+  for (int az = 0; az < r; ++az)
+    for (int ay = 0; ay < r; ++ay)
+      for (int ax = 0; ax < r; ++ax) {
+        const int64_t f = (int64_t)(Sx * r + ax) + (int64_t)cg.nf[0] * ((Sy * r + ay) + (int64_t)cg.nf[1] * (Sz * r + az));
+        const int beg = cs[f], n = cs[f + 1] - beg;
+        const T dx = (T)((ax + 0.5 - 0.5 * r) * cg.cs[0]), dy = (T)((ay + 0.5 - 0.5 * r) * cg.cs[1]),
+                dz = (T)((az + 0.5 - 0.5 * r) * cg.cs[2]);
+        for (int j = (tid - (run & (P2MC_THREADS - 1))) & (P2MC_THREADS - 1); j < n; j += P2MC_THREADS) {
+          const typename V4<T>::type v = reinterpret_cast<const typename V4<T>::type*>(part)[beg + j];
+          const T ux = (v.x + dx) * ir, uy = (v.y + dy) * ir, uz = (v.z + dz) * ir;
+          p2m_accumulate<P, T>(ux, uy, uz, v.w, acc);
+          sq += v.w;
+          sx = fma(v.w, ux, sx);
+          sy = fma(v.w, uy, sy);
+          sz = fma(v.w, uz, sz);
+          sr = fma(v.w, ux * ux + uy * uy + uz * uz, sr);
+        }
+        run += n;
+      }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) red[warp][c] = acc[c];
+    red[warp][C] = sq;
+    red[warp][C + 1] = sx;
+    red[warp][C + 2] = sy;
+    red[warp][C + 3] = sz;
+    red[warp][C + 4] = sr;
+  }
+  __syncthreads();
+  for (int c = tid; c < C + 5; c += P2MC_THREADS) {
+    T v = red[0][c];
+    for (int w = 1; w < NW; ++w) v += red[w][c];
+    if (c < C)
+      Mc[(int64_t)c * cg.Kc + S] = v;
+    else
+      cellsum[(int64_t)(c - C) * cg.Kc + S] = (double)v;
+  }
+}
+
 // One thread per sorted particle.  Far-field potential and gradient in
 // physical units, with the periodic corrections of App. B.3:
 //   phi  += c0 + c1 . r_rel + qfac (|r_rel|^2 - 3/(2 alpha^2)) - 2 alpha/sqrt(pi) Q_cell
@@ -282,6 +356,31 @@ cudaError_t launch_p2m(int p, bool fp64, const void* part, const int* cell_start
                        double* celld, bool sparse, cudaStream_t s, int* nl) {
   ++*nl;
   return p2m_dispatch<0>(p, fp64, part, cell_start, K, M, cellq, celld, sparse, s);
+}
+
+namespace {
+template <int P>
+cudaError_t p2m_coarse_dispatch(int p, bool fp64, const void* part, const int* cs, const CoarseGeo& cg, void* Mc,
+                                double* cellsum, cudaStream_t s) {
+  if (p == P) {
+    if (fp64)
+      p2m_coarse_kernel<P, double><<<(unsigned)cg.Kc, P2MC_THREADS, 0, s>>>((const double*)part, cs, cg, (double*)Mc,
+                                                                            cellsum);
+    else
+      p2m_coarse_kernel<P, float><<<(unsigned)cg.Kc, P2MC_THREADS, 0, s>>>((const float*)part, cs, cg, (float*)Mc,
+                                                                           cellsum);
+    return cudaGetLastError();
+  }
+  if constexpr (P < PMMM_PMAX) return p2m_coarse_dispatch<P + 1>(p, fp64, part, cs, cg, Mc, cellsum, s);
+  return cudaErrorInvalidValue;
+}
+}  // namespace
+
+cudaError_t launch_p2m_coarse(int p, bool fp64, const void* part, const int* cell_start, const CoarseGeo& cg,
+                              void* Mc, double* cellsum, cudaStream_t s, int* nl) {
+  if (cg.Kc < 1 || cg.Kc > 0x7fffffff) return cudaErrorInvalidValue;
+  ++*nl;
+  return p2m_coarse_dispatch<0>(p, fp64, part, cell_start, cg, Mc, cellsum, s);
 }
 
 cudaError_t launch_l2p(int p, bool fp64, const void* part, const uint32_t* keys, int64_t n, const void* L, int64_t K,

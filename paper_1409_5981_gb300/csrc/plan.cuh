@@ -81,6 +81,7 @@ struct pmmm_plan {
   void *hspecM = nullptr, *hspecL = nullptr;  // block spectra, C * Kc * m^2 (m/2+1) complex
   void* hregion = nullptr;                    // kept block outputs, C * Kc * ((2c+1) r)^3
   void* hrtab = nullptr;                      // R(coarse centre - child centre), r^3 * C
+  void* hum = nullptr;                        // L2L child matrices, r^3 * C * C (or none)
   // particle workspace
   int64_t cap = 0;
   SortWork sw{};

@@ -101,6 +101,7 @@ void free_all(pmmm_plan* pl) {
   dfree(pl, pl->m2l_tab);
   dfree(pl, pl->m2l_tab_tc);
   dfree(pl, pl->hspecM); dfree(pl, pl->hspecL); dfree(pl, pl->hregion); dfree(pl, pl->hrtab);
+  dfree(pl, pl->hum);
   if (pl->coarse) pmmm_plan_destroy(pl->coarse);
   if (pl->block) pmmm_plan_destroy(pl->block);
   pl->coarse = pl->block = nullptr;
@@ -323,6 +324,10 @@ int setup_hier(pmmm_plan* pl) {
   if (e == cudaSuccess) e = dalloc(pl, &pl->hregion, T * pl->C * (size_t)Kc * W * W * W);
   if (e == cudaSuccess) e = dalloc(pl, &pl->hrtab, T * pl->C * (size_t)h.r * h.r * h.r);
   if (e == cudaSuccess) e = launch_hier_rtab(h, pl->p, pl->fp64, pl->g.cs, pl->hrtab, pl->stream);
+  if (e == cudaSuccess && hier_use_matrices(h, pl->p)) {
+    e = dalloc(pl, &pl->hum, T * (size_t)h.r * h.r * h.r * pl->C * pl->C);
+    if (e == cudaSuccess) e = launch_hier_matrices(h, pl->p, pl->fp64, pl->hrtab, pl->hum, pl->stream);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
   if (e != cudaSuccess) return map_cuda(e);
   if (h.wavemajor) rc = ensure_m2l_tables(pl);
@@ -380,7 +385,8 @@ cudaError_t mesh_stage(pmmm_plan* pl, int B, int* nl) {
 }
 
 // Two-level cell convolution (Sec. 5, hierarchical treatment): coarse
-// multipoles by M2M, the one-level convolution on the coarse mesh, the block
+// multipoles by P2M about the coarse centres (with the coarse per-cell sums of
+// the periodic corrections), the one-level convolution on the coarse mesh, the block
 // convolution of the fine level, and the fine locals as L2L of the coarse ones
 // plus the kept block outputs (M of the plan -> L of the plan).
 cudaError_t hier_stage(pmmm_plan* pl, int* nl) {
@@ -390,7 +396,15 @@ cudaError_t hier_stage(pmmm_plan* pl, int* nl) {
   pmmm_plan* bp = pl->block;
   const bool fp64 = pl->fp64;
   const int64_t Kc = cp->d.K, Khh = bp->d.Kh;
-  cudaError_t e = launch_hier_m2m(h, pl->p, fp64, pl->M, cp->M, pl->hrtab, s, nl);
+  CoarseGeo cg;
+  cg.r = h.r;
+  cg.Kc = Kc;
+  for (int a = 0; a < 3; ++a) {
+    cg.nf[a] = h.nf[a];
+    cg.nc[a] = h.nc[a];
+    cg.cs[a] = pl->g.cs[a];
+  }
+  cudaError_t e = launch_p2m_coarse(pl->p, fp64, pl->part, pl->cs, cg, cp->M, cp->cellsum, s, nl);
   if (e == cudaSuccess) e = mesh_stage(cp, 1, nl);
   if (e == cudaSuccess) e = launch_hier_forward(h, pl->C, fp64, pl->M, pl->hspecM, bp->twx, s, nl);
   if (e != cudaSuccess) return e;
@@ -406,7 +420,7 @@ cudaError_t hier_stage(pmmm_plan* pl, int* nl) {
   mark(pl, ST_FFT_INV);
   e = launch_hier_inverse(h, pl->C, fp64, pl->hspecL, pl->hregion, bp->twx, s, nl);
   if (e == cudaSuccess)
-    e = launch_hier_local(h, pl->p, fp64, cp->L, pl->hregion, pl->hrtab, pl->L, pl->g.periodic, s, nl);
+    e = launch_hier_local(h, pl->p, fp64, cp->L, pl->hregion, pl->hrtab, pl->hum, pl->L, pl->g.periodic, s, nl);
   return e;
 }
 
@@ -455,9 +469,9 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
   mark(pl, ST_L2P);
   if (pl->g.periodic) {
     if (pl->hier) {
-      // the corrections belong to the coarse level (its Ewald split, its cells)
+      // the corrections belong to the coarse level (its Ewald split, its cells;
+      // the coarse per-cell sums come from the coarse P2M)
       pmmm_plan* cp = pl->coarse;
-      CK(launch_hier_cellsum(pl->hg, pl->cellsum, cp->cellsum, pl->g.cs, s, &nl));
       CK(launch_corrections(cp->cellsum, cp->cellsum + cp->d.K, cp->d.K, cp->g.hs, pl->g.V, pl->partial, pl->corr, s,
                             &nl));
     } else if (B == 1) {

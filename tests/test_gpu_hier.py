@@ -156,3 +156,29 @@ def test_refusals(pk):
     plan.close()
     with pytest.raises(pk.PmmmError):
         pk.Surrogate(pk.Config(mesh=(8, 8, 8), p=3, boundary=pk.PERIODIC, precision=pk.FP32, refine=2), 10)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_refine8_long_block_transforms(pk, precision):
+    """r = 8 (blocks of 32^3 fine cells, 24^3 kept outputs): the FP32 FFT inverse with
+    one cell per block and the FP64 register-column inverse."""
+    pos, q = synth.uniform_pm1(6000, synth.seed(7, 60))
+    fp64 = precision == "fp64"
+    if not fp64:
+        pos = pos.astype(np.float32).astype(np.float64)
+    cfg = pk.Config(mesh=(16, 16, 16), p=3, boundary=pk.OPEN, precision=pk.FP64 if fp64 else pk.FP32, refine=8)
+    plan, phi, force, energy = _run(pk, cfg, pos, q)
+    cells = synth.rng(703).choice(16 ** 3, size=300, replace=False)
+    ref = _oracle(cfg, pk, pos, q, target_cells=cells)
+    sel = ~np.isnan(ref["phi"])
+    rf = -(q[sel, None] * ref["grad"][sel])
+    e_f, e_p = _rel(force[sel], rf), _rel(phi[sel], ref["phi"][sel])
+    bound = FP64_TOL if fp64 else FP32_TOL[3]
+    print(f"{precision} two-level r=8: force {e_f:.2e} phi {e_p:.2e}")
+    assert e_f < bound and e_p < bound
+    plan.close()
+
+
+def test_refine16_blocks_too_large_refused(pk):
+    with pytest.raises(pk.PmmmError):
+        pk.Plan(pk.Config(mesh=(32, 32, 32), p=3, boundary=pk.OPEN, precision=pk.FP32, refine=16))
