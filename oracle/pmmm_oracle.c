@@ -33,11 +33,12 @@
  *                                      cell pair
  *
  * Where the paper is ambiguous or its printed formula is defective, the
- * readings taken here are the ones listed in the design notes of this
- * repository (Ewald self term with a minus sign, q_j in the real-space Ewald
- * term, (-i pi)^l with exp(+2 pi i k.r), n = 0 image left out of the self
- * cell, only the image with |cell offset|_inf <= c masked, FP64 binning
- * formula, forward DFT with exp(-2 pi i)).
+ * readings taken here are: the Ewald self term with a minus sign, q_j in the
+ * real-space Ewald term, (-i pi)^l with exp(+2 pi i k.r), the n = 0 image
+ * left out of the self cell, only the image with |cell offset|_inf <= c
+ * masked, the FP64 binning formula, the forward DFT with exp(-2 pi i), and
+ * for the two-level method the same cutoff at both levels with the periodic
+ * corrections taken at the coarse level.
  *
  * Complex harmonic arrays use the full index l*l + l + m, m in [-l, l], as
  * interleaved (re, im) doubles: (p+1)^2 complex numbers for order p.

@@ -66,10 +66,6 @@ cudaError_t launch_radix_sort(SortWork& w, int64_t n, int key_bits, uint32_t** k
                               cudaStream_t s, int* nlaunch);
 cudaError_t launch_cell_bounds(const uint32_t* keys, int64_t n, int64_t K, int* cell_start, cudaStream_t s,
                                int* nlaunch);
-// Sorted particle records part[s] = rec[vals[s]]: position relative to the cell
-// centre in units of hs, and the charge.
-cudaError_t launch_gather(const void* rec, bool fp64, const uint32_t* vals, int64_t n, void* part, cudaStream_t s,
-                          int* nlaunch);
 // In-place exclusive scan of n uint32 values (chunks: scratch of scan_chunk_count(n)).
 int64_t scan_chunk_count(int64_t n);
 cudaError_t launch_exclusive_scan(uint32_t* data, int64_t n, uint32_t* chunks, cudaStream_t s, int* nlaunch);
@@ -258,19 +254,25 @@ struct PPParams {
   double csf[3], ihf, ih2f, signf;
   float cs32[3], ih32, ih2_32, sign32;
 };
-// Near-field work items, one per (cell, chunk of up to 32 target particles):
-// item_start[K+1] (exclusive scan of the chunk counts), item_cell[item]; resets
-// the work counter and zeroes the energy partials of unused item slots.
+// Near-field work items, one per (cell, chunk of up to 32 target particles): at
+// most pp_items_max of them; source pairs of the FP32 near field: at most
+// (n + K) / 2 + 1.
 int64_t pp_items_max(int64_t K, int64_t n);
-// source pairs of the FP32 near field: at most (n + K) / 2 + 1
 int64_t pp_pairs_max(int64_t K, int64_t n);
-// zero_all: zero the energy partials of every item slot (the per-target kernel accumulates into them)
-cudaError_t launch_pp_items(const int* cell_start, int64_t K, uint32_t* item_start, uint32_t* item_cell,
-                            uint32_t* pair_start, uint32_t* chunks, unsigned int* counter, double* epart,
-                            int64_t max_items, bool zero_all, cudaStream_t s, int* nlaunch);
-// pair-interleaved FP32 source records (see pp.cu), src2: 32 bytes per pair
-cudaError_t launch_pair_pack(const void* part, const uint32_t* keys, const int* cell_start, const uint32_t* pair_start,
-                             int64_t n, void* src2, cudaStream_t s, int* nlaunch);
+// Near-field work lists: item_start / pair_start (exclusive scans of the per-cell
+// item and source-pair counts, K + 1 entries; pair_start may be null) and the
+// reset of the work counter.
+cudaError_t launch_pp_lists(const int* cell_start, int64_t K, uint32_t* item_start, uint32_t* pair_start,
+                            uint32_t* chunks, unsigned int* counter, cudaStream_t s, int* nlaunch);
+// Sorted records part[s] = rec[vals[s]] (position relative to the cell centre in
+// units of hs, and the charge), the cell of every work item (item_cell), the FP32
+// pair-interleaved sources (src2 not null; 32 bytes per pair, layout in pp.cu) and
+// zeroed energy partials of the unused item slots (of all of them with zero_all:
+// the per-target kernel accumulates into them).
+cudaError_t launch_gather_lists(const void* rec, bool fp64, const uint32_t* vals, const uint32_t* keys,
+                                const int* cell_start, const uint32_t* item_start, const uint32_t* pair_start,
+                                int64_t n, int64_t K, void* part, void* src2, uint32_t* item_cell, double* epart,
+                                int64_t max_items, bool zero_all, cudaStream_t s, int* nlaunch);
 // Near field over the (2c+1)^3 cells plus the far field from `far`, written in
 // the caller's order to phi / force; energy and force partials per work item
 // (epart[max_items][4]).  Persistent warps fetch items from *counter.  With

@@ -457,10 +457,11 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
       CK(launch_bin_batched(pos, q, fp64, n, pl->offsets_d, B, pl->g, Ks, pl->sw.keys0, pl->far, pl->err, s, &nl));
     CK(launch_radix_sort(pl->sw, n, key_bits, &pl->keys_sorted, &pl->vals_sorted, s, &nl));
     CK(launch_cell_bounds(pl->keys_sorted, n, K, pl->cs, s, &nl));
-    CK(launch_gather(pl->far, fp64, pl->vals_sorted, n, pl->part, s, &nl));
-    CK(launch_pp_items(pl->cs, K, pl->item_start, pl->item_cell, pl->pair_start, pl->item_chunks, pl->counter,
-                       pl->epart, pp_items_max(K, n), per_target, s, &nl));
-    if (!fp64) CK(launch_pair_pack(pl->part, pl->keys_sorted, pl->cs, pl->pair_start, n, pl->src2, s, &nl));
+    CK(launch_pp_lists(pl->cs, K, pl->item_start, fp64 ? nullptr : pl->pair_start, pl->item_chunks, pl->counter, s,
+                       &nl));
+    CK(launch_gather_lists(pl->far, fp64, pl->vals_sorted, pl->keys_sorted, pl->cs, pl->item_start, pl->pair_start, n,
+                           K, pl->part, fp64 ? nullptr : pl->src2, pl->item_cell, pl->epart, pp_items_max(K, n),
+                           per_target, s, &nl));
   }
   mark(pl, ST_P2M);
   CK(launch_p2m(pl->p, fp64, pl->part, pl->cs, K, pl->M, pl->cellsum, pl->cellsum + K, sparse, s, &nl));

@@ -20,7 +20,7 @@ namespace {
 
 constexpr int PP_WARPS = 4;
 constexpr int PP_BATCH = 4;  // work items taken per atomic by the FP32 near-field warps
-constexpr int PP_BLOCKS_PER_SM = 8;  // resident blocks per SM (64 registers per thread)
+constexpr int PP_BLOCKS_PER_SM = 6;  // resident blocks per SM (up to 80 registers per thread)
 constexpr int CHUNK = 32;
 
 template <typename T> struct V4;
@@ -57,38 +57,142 @@ __global__ void item_count_kernel(const int* __restrict__ cs, int64_t K, uint32_
 // dummy of zero charge far outside the box).  Pair j is two 16-byte words
 // {x_a, x_b, y_a, y_b}, {z_a, z_b, q_a, q_b}, so that one 128-bit load yields
 // the packed operands of two sources.
-__global__ void pair_pack_kernel(const float4* __restrict__ part, const uint32_t* __restrict__ keys,
-                                 const int* __restrict__ cs, const uint32_t* __restrict__ pair_start, int64_t n,
-                                 float* __restrict__ src2) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const uint32_t cell = keys[s];
-  const int j = (int)(s - cs[cell]);
-  const int64_t pj = (int64_t)pair_start[cell] + j / 2;
-  const int slot = j & 1;
-  const float4 r = part[s];
-  float* o = src2 + 8 * pj;
-  o[0 + slot] = r.x;
-  o[2 + slot] = r.y;
-  o[4 + slot] = r.z;
-  o[6 + slot] = r.w;
-  if (slot == 0 && s + 1 == (int64_t)cs[cell + 1]) {  // odd count: dummy partner
-    o[1] = 1.0e4f;
-    o[3] = 1.0e4f;
-    o[5] = 1.0e4f;
-    o[7] = 0.0f;
+
+// Work lists of cells small enough for one block (K + 1 <= LIST_SCAN_MAX): item and
+// source-pair counts from the cell offsets and their exclusive prefix sums in one
+// launch.  Warp w owns the contiguous chunk of cells [w CH, (w+1) CH) and walks it
+// 32 cells at a time (lane = cell, loads and stores coalesced, eight rows of loads
+// in flight): a first walk sums the chunk, a block scan of the 32 chunk totals
+// gives each chunk its offset, a second walk writes the prefix sums with warp
+// scans and a running carry.
+constexpr int LIST_SCAN_THREADS = 1024;
+constexpr int64_t LIST_SCAN_MAX = 65537;
+constexpr int LIST_UNROLL = 8;
+
+__device__ __forceinline__ void cell_counts(const int* __restrict__ cs, int64_t c, int64_t K, uint32_t& ni,
+                                            uint32_t& np) {
+  ni = np = 0u;
+  if (c < K) {
+    const int cnt = __ldg(cs + c + 1) - __ldg(cs + c);
+    ni = (uint32_t)((cnt + CHUNK - 1) / CHUNK);
+    np = (uint32_t)((cnt + 1) / 2);
   }
 }
 
-__global__ void item_fill_kernel(const uint32_t* __restrict__ item_start, int64_t K, uint32_t* __restrict__ item_cell,
-                                 double* __restrict__ epart, int64_t max_items, int zero_all) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // energy partials of unused item slots are zero (of every slot when the
-  // near-field kernel accumulates into them)
-  for (int64_t i = (zero_all ? 0 : (int64_t)item_start[K]) + c; i < max_items; i += (int64_t)gridDim.x * blockDim.x)
+__global__ void __launch_bounds__(LIST_SCAN_THREADS) list_scan_kernel(const int* __restrict__ cs, int64_t K,
+                                                                     uint32_t* __restrict__ item_start,
+                                                                     uint32_t* __restrict__ pair_start,
+                                                                     unsigned int* __restrict__ counter) {
+  __shared__ uint32_t wi[32], wp[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t nk = K + 1;
+  const int64_t CH = (nk + 31) / 32;
+  const int64_t c_beg = (int64_t)warp * CH, c_end = c_beg + CH < nk ? c_beg + CH : nk;
+  // first walk: the chunk's totals
+  uint32_t si = 0, sp = 0;
+  for (int64_t b = c_beg; b < c_end; b += 32 * LIST_UNROLL) {
+    uint32_t a[LIST_UNROLL], q[LIST_UNROLL];
+#pragma unroll
+    for (int u = 0; u < LIST_UNROLL; ++u) {
+      const int64_t c = b + 32 * u + lane;
+      cell_counts(cs, c < c_end ? c : K, K, a[u], q[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < LIST_UNROLL; ++u) {
+      si += a[u];
+      sp += q[u];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+    sp += __shfl_xor_sync(0xffffffffu, sp, o);
+  }
+  if (lane == 0) {
+    wi[warp] = si;
+    wp[warp] = sp;
+  }
+  __syncthreads();
+  // chunk offsets: exclusive scan of the 32 chunk totals (every warp computes it)
+  uint32_t ti = wi[lane], tp = wp[lane];
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, ti, o), y = __shfl_up_sync(0xffffffffu, tp, o);
+    if (lane >= o) {
+      ti += x;
+      tp += y;
+    }
+  }
+  uint32_t carry_i = __shfl_sync(0xffffffffu, ti - wi[lane], warp);
+  uint32_t carry_p = __shfl_sync(0xffffffffu, tp - wp[lane], warp);
+  // second walk: exclusive prefix sums, 32 cells per row
+  for (int64_t b = c_beg; b < c_end; b += 32 * LIST_UNROLL) {
+    uint32_t a[LIST_UNROLL], q[LIST_UNROLL];
+#pragma unroll
+    for (int u = 0; u < LIST_UNROLL; ++u) {
+      const int64_t c = b + 32 * u + lane;
+      cell_counts(cs, c < c_end ? c : K, K, a[u], q[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < LIST_UNROLL; ++u) {
+      const int64_t c = b + 32 * u + lane;
+      uint32_t ii = a[u], ip = q[u];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, ii, o), y = __shfl_up_sync(0xffffffffu, ip, o);
+        if (lane >= o) {
+          ii += x;
+          ip += y;
+        }
+      }
+      if (c < c_end) {
+        item_start[c] = carry_i + ii - a[u];
+        if (pair_start) pair_start[c] = carry_p + ip - q[u];
+      }
+      carry_i += __shfl_sync(0xffffffffu, ii, 31);
+      carry_p += __shfl_sync(0xffffffffu, ip, 31);
+    }
+  }
+  if (tid == 0) *counter = 0u;
+}
+
+// Sorted records part[s] = rec[vals[s]] (a pure permutation), and with them the
+// near-field work lists: the cell of every work item (the first particle of each
+// chunk of CHUNK writes it), the pair-interleaved FP32 sources (PACK, layout
+// above) and zeroed energy partials of the unused item slots (of all
+// slots when the near-field kernel accumulates into them).
+template <typename V, bool PACK>
+__global__ void gather_lists_kernel(const V* __restrict__ rec, const uint32_t* __restrict__ vals,
+                                    const uint32_t* __restrict__ keys, const int* __restrict__ cs,
+                                    const uint32_t* __restrict__ item_start, const uint32_t* __restrict__ pair_start,
+                                    int64_t n, int64_t K, V* __restrict__ part, float* __restrict__ src2,
+                                    uint32_t* __restrict__ item_cell, double* __restrict__ epart, int64_t max_items,
+                                    int zero_all) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t i = (zero_all ? 0 : (int64_t)item_start[K]) + s; i < max_items; i += (int64_t)gridDim.x * blockDim.x)
     epart[4 * i] = epart[4 * i + 1] = epart[4 * i + 2] = epart[4 * i + 3] = 0.0;
-  if (c >= K) return;
-  for (uint32_t it = item_start[c]; it < item_start[c + 1]; ++it) item_cell[it] = (uint32_t)c;
+  if (s >= n) return;
+  const V r = rec[vals[s]];
+  part[s] = r;
+  const uint32_t cell = keys[s];
+  const int c0 = cs[cell];
+  const int j = (int)(s - c0);
+  if (j % CHUNK == 0) item_cell[item_start[cell] + j / CHUNK] = cell;
+  if constexpr (PACK) {
+    const int64_t pj = (int64_t)pair_start[cell] + j / 2;
+    const int slot = j & 1;
+    float* o = src2 + 8 * pj;
+    o[0 + slot] = (float)r.x;
+    o[2 + slot] = (float)r.y;
+    o[4 + slot] = (float)r.z;
+    o[6 + slot] = (float)r.w;
+    if (slot == 0 && s + 1 == (int64_t)cs[cell + 1]) {  // odd count: dummy partner
+      o[1] = 1.0e4f;
+      o[3] = 1.0e4f;
+      o[5] = 1.0e4f;
+      o[7] = 0.0f;
+    }
+  }
 }
 
 // Accumulates the interactions of target (tx, ty, tz) with sources P[b + e],
@@ -385,6 +489,14 @@ __device__ __forceinline__ void pp_sum2(const ulonglong2* __restrict__ src, int 
                                         f2 tz, f2& pot, f2& gx, f2& gy, f2& gz) {
   if (SP == 1) {
     int j = 0;
+    for (; j + 4 <= npair; j += 4) {
+      const ulonglong2 A0 = src[2 * j], B0 = src[2 * j + 1], A1 = src[2 * j + 2], B1 = src[2 * j + 3];
+      const ulonglong2 A2 = src[2 * j + 4], B2 = src[2 * j + 5], A3 = src[2 * j + 6], B3 = src[2 * j + 7];
+      pp_pair2<SELF>(A0, B0, tx, ty, tz, pot, gx, gy, gz);
+      pp_pair2<SELF>(A1, B1, tx, ty, tz, pot, gx, gy, gz);
+      pp_pair2<SELF>(A2, B2, tx, ty, tz, pot, gx, gy, gz);
+      pp_pair2<SELF>(A3, B3, tx, ty, tz, pot, gx, gy, gz);
+    }
     for (; j + 2 <= npair; j += 2) {
       const ulonglong2 A0 = src[2 * j], B0 = src[2 * j + 1], A1 = src[2 * j + 2], B1 = src[2 * j + 3];
       pp_pair2<SELF>(A0, B0, tx, ty, tz, pot, gx, gy, gz);
@@ -687,25 +799,38 @@ int64_t pp_items_max(int64_t K, int64_t n) { return K + (n + CHUNK - 1) / CHUNK 
 
 int64_t pp_pairs_max(int64_t K, int64_t n) { return (n + K) / 2 + 1; }
 
-cudaError_t launch_pp_items(const int* cell_start, int64_t K, uint32_t* item_start, uint32_t* item_cell,
-                            uint32_t* pair_start, uint32_t* chunks, unsigned int* counter, double* epart,
-                            int64_t max_items, bool zero_all, cudaStream_t s, int* nl) {
+cudaError_t launch_pp_lists(const int* cell_start, int64_t K, uint32_t* item_start, uint32_t* pair_start,
+                            uint32_t* chunks, unsigned int* counter, cudaStream_t s, int* nl) {
+  if (K + 1 <= LIST_SCAN_MAX) {
+    list_scan_kernel<<<1, LIST_SCAN_THREADS, 0, s>>>(cell_start, K, item_start, pair_start, counter);
+    ++*nl;
+    return cudaGetLastError();
+  }
   item_count_kernel<<<(unsigned)((K + 1 + 255) / 256), 256, 0, s>>>(cell_start, K, item_start, pair_start, counter);
   ++*nl;
   cudaError_t e = launch_exclusive_scan(item_start, K + 1, chunks, s, nl);
   if (e == cudaSuccess && pair_start) e = launch_exclusive_scan(pair_start, K + 1, chunks, s, nl);
-  if (e != cudaSuccess) return e;
-  item_fill_kernel<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(item_start, K, item_cell, epart, max_items,
-                                                               zero_all ? 1 : 0);
-  ++*nl;
-  return cudaGetLastError();
+  return e;
 }
 
-cudaError_t launch_pair_pack(const void* part, const uint32_t* keys, const int* cell_start, const uint32_t* pair_start,
-                             int64_t n, void* src2, cudaStream_t s, int* nl) {
-  if (n <= 0) return cudaSuccess;
-  pair_pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float4*)part, keys, cell_start, pair_start, n,
-                                                               (float*)src2);
+cudaError_t launch_gather_lists(const void* rec, bool fp64, const uint32_t* vals, const uint32_t* keys,
+                                const int* cell_start, const uint32_t* item_start, const uint32_t* pair_start,
+                                int64_t n, int64_t K, void* part, void* src2, uint32_t* item_cell, double* epart,
+                                int64_t max_items, bool zero_all, cudaStream_t s, int* nl) {
+  const int64_t work = n > max_items ? n : max_items;
+  const unsigned blocks = (unsigned)((work + 255) / 256 > 0 ? (work + 255) / 256 : 1);
+  if (fp64)
+    gather_lists_kernel<double4, false><<<blocks, 256, 0, s>>>((const double4*)rec, vals, keys, cell_start, item_start,
+                                                                 pair_start, n, K, (double4*)part, nullptr, item_cell,
+                                                                 epart, max_items, zero_all ? 1 : 0);
+  else if (src2)
+    gather_lists_kernel<float4, true><<<blocks, 256, 0, s>>>((const float4*)rec, vals, keys, cell_start, item_start,
+                                                               pair_start, n, K, (float4*)part, (float*)src2,
+                                                               item_cell, epart, max_items, zero_all ? 1 : 0);
+  else
+    gather_lists_kernel<float4, false><<<blocks, 256, 0, s>>>((const float4*)rec, vals, keys, cell_start, item_start,
+                                                                pair_start, n, K, (float4*)part, nullptr, item_cell,
+                                                                epart, max_items, zero_all ? 1 : 0);
   ++*nl;
   return cudaGetLastError();
 }

@@ -221,15 +221,6 @@ __global__ void scan_add_kernel(uint32_t* __restrict__ data, int64_t n, const ui
   if (i < n) data[i] += chunks[i / SCAN_CH];
 }
 
-// Sorted records: part[s] = rec[vals[s]] (a pure permutation).
-template <typename V>
-__global__ void gather_kernel(const V* __restrict__ rec, const uint32_t* __restrict__ vals, int64_t n,
-                              V* __restrict__ part) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  part[s] = rec[vals[s]];
-}
-
 inline int grid1(int64_t n, int b) { return (int)((n + b - 1) / b); }
 }  // namespace
 
@@ -312,17 +303,6 @@ cudaError_t launch_radix_sort(SortWork& w, int64_t n, int key_bits, uint32_t** k
 
 cudaError_t launch_cell_bounds(const uint32_t* keys, int64_t n, int64_t K, int* cs, cudaStream_t s, int* nl) {
   cell_bounds_kernel<<<grid1(n + 1, 256), 256, 0, s>>>(keys, n, K, cs);
-  ++*nl;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gather(const void* rec, bool fp64, const uint32_t* vals, int64_t n, void* part, cudaStream_t s,
-                          int* nl) {
-  if (n <= 0) return cudaSuccess;
-  if (fp64)
-    gather_kernel<double4><<<grid1(n, 256), 256, 0, s>>>((const double4*)rec, vals, n, (double4*)part);
-  else
-    gather_kernel<float4><<<grid1(n, 256), 256, 0, s>>>((const float4*)rec, vals, n, (float4*)part);
   ++*nl;
   return cudaGetLastError();
 }

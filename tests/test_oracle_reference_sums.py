@@ -1,6 +1,6 @@
 """Pins of the reference sums: the direct O(N^2) sum (open boundary) and the
-Ewald sum of Eq. refewald (periodic), with readings 1 and 2 of the design notes
-(self term -2 alpha/sqrt(pi) q_i, q_j in the real-space term)."""
+Ewald sum of Eq. refewald (periodic), with the printed formula's two defects
+read as: self term -2 alpha/sqrt(pi) q_i, and q_j in the real-space term."""
 import os
 
 import numpy as np
