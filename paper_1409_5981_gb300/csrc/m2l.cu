@@ -10,22 +10,51 @@ namespace pmmm {
 
 namespace {
 
-template <int P, typename T>
+// The output order l = blockIdx.y (uniform per block) selects a compile-time
+// instance, so that only the terms m <= l of that order are issued.
+template <int P, int L, typename T, class LM, class LG, class ST>
+__device__ __forceinline__ void m2l_order_dispatch(int l, int p, LM&& Mk, LG&& Gk, ST&& St) {
+  if (l == L) {
+    m2l_order_l<P, L, T>(p, Mk, Gk, St);
+    return;
+  }
+  if constexpr (L < P) m2l_order_dispatch<P, L + 1, T>(l, p, Mk, Gk, St);
+}
+
+// CT: the compile-time-order form (FP32, p <= 8).  Its eight order instances
+// together exceed the instruction cache, so it pays only when each SM keeps to
+// one order at a time, i.e. when one order alone fills the GPU (large meshes:
+// the blocks of one order launch together); small meshes take the runtime form.
+template <int P, typename T, bool CT>
 __global__ void __launch_bounds__(128, (P <= 7 ? 4 : 1)) m2l_kernel(const cpx<T>* __restrict__ Mt, const cpx<T>* __restrict__ Gt,
                                                   cpx<T>* __restrict__ Lt, int64_t Kh, int nsys, int p) {
   const int l = blockIdx.y;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= Kh) return;
   const int64_t cstride = (int64_t)nsys * Kh, mk0 = (int64_t)blockIdx.z * Kh + k;
-  m2l_order<P, T>(
-      l, p, [&](int c) { return Mt[c * cstride + mk0]; }, [&](int s) { return Gt[(int64_t)s * Kh + k]; },
-      [&](int c, cpx<T> v) { Lt[c * cstride + mk0] = v; });
+  auto Mk = [&](int c) { return Mt[c * cstride + mk0]; };
+  auto Gk = [&](int s) { return Gt[(int64_t)s * Kh + k]; };
+  auto St = [&](int c, cpx<T> v) { Lt[c * cstride + mk0] = v; };
+  if constexpr (CT)
+    m2l_order_dispatch<P, 0, T>(l, p, Mk, Gk, St);
+  else
+    m2l_order<P, T>(l, p, Mk, Gk, St);
 }
+
+// blocks of one order from which the compile-time form is taken (more than a wave of 4 x 152)
+constexpr int64_t M2L_CT_MIN_BLOCKS = 1024;
 
 template <int P, typename T>
 cudaError_t run(const void* Mt, const void* Gt, void* Lt, int64_t Kh, int nsys, cudaStream_t s) {
   dim3 grid((unsigned)((Kh + 127) / 128), P + 1, (unsigned)nsys);
-  m2l_kernel<P, T><<<grid, 128, 0, s>>>((const cpx<T>*)Mt, (const cpx<T>*)Gt, (cpx<T>*)Lt, Kh, nsys, P);
+  const bool ct = sizeof(T) == 4 && P <= 8 && (int64_t)grid.x * nsys >= M2L_CT_MIN_BLOCKS;
+  if constexpr (sizeof(T) == 4 && P <= 8) {
+    if (ct) {
+      m2l_kernel<P, T, true><<<grid, 128, 0, s>>>((const cpx<T>*)Mt, (const cpx<T>*)Gt, (cpx<T>*)Lt, Kh, nsys, P);
+      return cudaGetLastError();
+    }
+  }
+  m2l_kernel<P, T, false><<<grid, 128, 0, s>>>((const cpx<T>*)Mt, (const cpx<T>*)Gt, (cpx<T>*)Lt, Kh, nsys, P);
   return cudaGetLastError();
 }
 

@@ -77,6 +77,82 @@ struct M2LRow<P, T, P + 1> {
                             cpx<T>*) {}
 };
 
+// The same terms with the output order L known at compile time (m <= L is
+// resolved by the compiler; the source order lam stays a runtime loop, which
+// keeps the register arrays of one lam live at a time).
+template <int P, int L, typename T, int M, int MU>
+struct M2LTermL {
+  PMMM_HD static void apply(int lam, const cpx<T>* sre, const cpx<T>* sim, const cpx<T>* mre, const cpx<T>* mim,
+                            cpx<T>* Lre, cpx<T>* Lim) {
+    if (MU <= lam) {
+      const cpx<T> A = s_re<T, -(M + MU)>(sre, sim);
+      const cpx<T> B = s_im<T, -(M + MU)>(sre, sim);
+      if constexpr (MU == 0) {
+        cmac(Lre[M], A, mre[0]);
+        cmac(Lim[M], B, mre[0]);
+      } else {
+        cpx<T> C = s_re<T, MU - M>(sre, sim);
+        cpx<T> D = s_im<T, MU - M>(sre, sim);
+        if constexpr (MU & 1) {
+          C = mk(-C.x, -C.y);
+          D = mk(-D.x, -D.y);
+        }
+        cmac(Lre[M], A + C, mre[MU]);
+        cmac(Lre[M], D - B, mim[MU]);
+        cmac(Lim[M], B + D, mre[MU]);
+        cmac(Lim[M], A - C, mim[MU]);
+      }
+    }
+    if constexpr (MU < P) M2LTermL<P, L, T, M, MU + 1>::apply(lam, sre, sim, mre, mim, Lre, Lim);
+  }
+};
+template <int P, int L, typename T, int M>
+struct M2LRowL {
+  PMMM_HD static void apply(int lam, const cpx<T>* sre, const cpx<T>* sim, const cpx<T>* mre, const cpx<T>* mim,
+                            cpx<T>* Lre, cpx<T>* Lim) {
+    M2LTermL<P, L, T, M, 0>::apply(lam, sre, sim, mre, mim, Lre, Lim);
+    if constexpr (M < L) M2LRowL<P, L, T, M + 1>::apply(lam, sre, sim, mre, mim, Lre, Lim);
+  }
+};
+template <int P, int L, typename T, class LM, class LG, class ST>
+PMMM_HD void m2l_order_l(int p, LM&& Mk, LG&& Gk, ST&& St) {
+  cpx<T> Lre[L + 1], Lim[L + 1];
+#pragma unroll
+  for (int m = 0; m <= L; ++m) {
+    Lre[m] = mk(T(0), T(0));
+    Lim[m] = mk(T(0), T(0));
+  }
+  for (int lam = 0; lam <= p; ++lam) {
+    const int j = L + lam;
+    cpx<T> mre[P + 1], mim[P + 1];
+#pragma unroll
+    for (int mu = 0; mu <= P; ++mu) {
+      mre[mu] = mk(T(0), T(0));
+      mim[mu] = mk(T(0), T(0));
+      if (mu <= lam) {
+        mre[mu] = Mk(sidx(lam, mu));
+        if (mu > 0) mim[mu] = Mk(sidx(lam, -mu));
+      }
+    }
+    cpx<T> sre[L + P + 1], sim[L + P + 1];
+#pragma unroll
+    for (int a = 0; a <= L + P; ++a) {
+      sre[a] = mk(T(0), T(0));
+      sim[a] = mk(T(0), T(0));
+      if (a <= j) {
+        sre[a] = Gk(sidx(j, a));
+        if (a > 0) sim[a] = Gk(sidx(j, -a));
+      }
+    }
+    M2LRowL<P, L, T, 0>::apply(lam, sre, sim, mre, mim, Lre, Lim);
+  }
+#pragma unroll
+  for (int m = 0; m <= L; ++m) {
+    St(sidx(L, m), Lre[m]);
+    if (m > 0) St(sidx(L, -m), Lim[m]);
+  }
+}
+
 // One output order l of the M2L at one wavevector.
 //   Mk(c)  -> spectrum of real channel c of M at this k      (c < (p+1)^2)
 //   Gk(s)  -> spectrum of real component s of the kernel      (s < (2p+1)^2)
