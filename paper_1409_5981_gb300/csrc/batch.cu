@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(256) corrections_batched_kernel(const double* 
     c[2] = -2.0 * f * sh[2][0] * hs;
     c[3] = -2.0 * f * sh[3][0] * hs;
     c[4] = f * sh[0][0];
+    corr_store_f32(c);
     for (int qn = 0; qn < 5; ++qn) c[8 + qn] = sh[qn][0];
   }
 }

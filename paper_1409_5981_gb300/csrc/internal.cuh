@@ -86,7 +86,20 @@ struct CorrParams {
   int refine;          // 0 / 1: one level; r >= 2: coarse cell = r^3 fine cells
   int nf[3], nc[3];    // fine and coarse cells per axis
   double cs[3];        // fine cell sides in units of hs
+  // FP32 copies for the FP32 L2P, which then converts no FP64 value per particle
+  // (GB300 converts from FP64 at a small fraction of its FP32 rate)
+  float hs32, ih32, ih2_32, c_charged32, c_self32;
+  float cshs32[3];     // two-level: fine cell sides in units of the coarse hs
 };
+// Per-system correction block corr[16 s ...]: FP64 terms corr[0..4] (App. B.3),
+// their FP32 copies as five floats from byte offset 8 CORR_F32 (doubles 5..7),
+// the FP64 sums corr[8..12].
+constexpr int CORR_F32 = 5;
+__device__ __forceinline__ void corr_store_f32(double* c) {
+  float* f = reinterpret_cast<float*>(c + CORR_F32);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) f[k] = (float)c[k];
+}
 // Two-level plans: multipoles of the coarse cells (r^3 fine cells each) from the
 // particles sorted by fine cell, and the coarse per-cell sums [5][Kc].
 struct CoarseGeo {
@@ -289,11 +302,13 @@ cudaError_t launch_pp(bool fp64, const void* part, const void* src2, const uint3
 // Sums per-cell FP64 quantities and builds the periodic correction terms:
 // corr[0] = c0 (potential constant), corr[1..3] = c1 (linear term), corr[4] = qfac,
 // corr[8..12] = raw sums (Q, sum q u_x, sum q u_y, sum q u_z, sum q |u|^2) in hs units.
+// One launch each: partial holds RD_BLOCKS (256) x 5 doubles, ticket one zeroed
+// counter that the launch leaves zeroed again.
 cudaError_t launch_corrections(const double* cellq, const double* celld, int64_t K, double hs, double V,
-                               double* partial, double* corr, cudaStream_t s, int* nlaunch);
+                               double* partial, unsigned int* ticket, double* corr, cudaStream_t s, int* nlaunch);
 // energy[0] = sum of epart[i*4 + 0] over i < count, energy[1..3] = net force
-cudaError_t launch_energy(const double* epart, int64_t count, double* partial, double* energy, cudaStream_t s,
-                          int* nlaunch);
+cudaError_t launch_energy(const double* epart, int64_t count, double* partial, unsigned int* ticket, double* energy,
+                          cudaStream_t s, int* nlaunch);
 cudaError_t launch_to_physical(bool fp64, const void* X, double* out, int p, int64_t K, double hs, int power_shift,
                                cudaStream_t s);
 

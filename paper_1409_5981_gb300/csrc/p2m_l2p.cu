@@ -258,8 +258,10 @@ __global__ void __launch_bounds__(128) l2p_kernel(const T* __restrict__ part, co
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const typename V4<T>::type r = reinterpret_cast<const typename V4<T>::type*>(part)[i];
-  const int64_t cell = keys[i];
-  const double* corr = corr_all + 16 * (cell / cp.ksys);  // this particle's system
+  const uint32_t cell32 = keys[i];
+  const int64_t cell = cell32;
+  // this particle's system (one system: no division)
+  const double* corr = corr_all + (cp.ksys >= K ? 0 : 16 * (int64_t)(cell32 / (uint32_t)cp.ksys));
   T f, gx, gy, gz;
   if constexpr (P >= 9) {
     // high orders: harmonics streamed column by column (no (p+1)^2 array)
@@ -269,32 +271,50 @@ __global__ void __launch_bounds__(128) l2p_kernel(const T* __restrict__ part, co
     regular_real<P, T>(r.x, r.y, r.z, R);
     l2p_real<P, T>([&](int c) { return __ldg(L + (int64_t)c * K + cell); }, R, f, gx, gy, gz);
   }
-  const T ih = (T)cp.ih, ih2 = (T)cp.ih2;
+  constexpr bool F32 = sizeof(T) == 4;
+  const T ih = F32 ? (T)cp.ih32 : (T)cp.ih, ih2 = F32 ? (T)cp.ih2_32 : (T)cp.ih2;
   T phi = f * ih;
   T g[3] = {gx * ih2, gy * ih2, gz * ih2};
   if (cp.periodic) {
-    const T hs = (T)cp.hs;
+    // the correction terms: FP32 copies on the FP32 path (no FP64 conversion per particle)
+    T cr[5];
+    if constexpr (F32) {
+      const float* cf = reinterpret_cast<const float*>(corr + CORR_F32);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) cr[k] = cf[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) cr[k] = corr[k];
+    }
+    const T hs = F32 ? (T)cp.hs32 : (T)cp.hs;
     T rel[3] = {r.x * hs, r.y * hs, r.z * hs};
     int64_t qcell = cell;
     if (cp.refine > 1) {
       // two-level plan: position relative to the coarse centre, charge of the coarse cell
       const int R = cp.refine;
-      const int64_t ix = cell % cp.nf[0], iy = (cell / cp.nf[0]) % cp.nf[1], iz = cell / ((int64_t)cp.nf[0] * cp.nf[1]);
-      rel[0] += (T)(((double)(ix % R) + 0.5 - 0.5 * R) * cp.cs[0] * cp.hs);
-      rel[1] += (T)(((double)(iy % R) + 0.5 - 0.5 * R) * cp.cs[1] * cp.hs);
-      rel[2] += (T)(((double)(iz % R) + 0.5 - 0.5 * R) * cp.cs[2] * cp.hs);
+      const uint32_t nx = (uint32_t)cp.nf[0], ny = (uint32_t)cp.nf[1];
+      const uint32_t ix = cell32 % nx, iy = (cell32 / nx) % ny, iz = cell32 / (nx * ny);
+      const uint32_t ic[3] = {ix, iy, iz};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if constexpr (F32)
+          rel[a] += ((float)(ic[a] % (uint32_t)R) + (0.5f - 0.5f * (float)R)) * cp.cshs32[a];
+        else
+          rel[a] += ((double)(ic[a] % (uint32_t)R) + 0.5 - 0.5 * R) * cp.cs[a] * cp.hs;
+      }
       qcell = ix / R + (int64_t)cp.nc[0] * (iy / R + (int64_t)cp.nc[1] * (iz / R));
     }
     const T rr = rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2];
-    const T qf = (T)corr[4];
-    phi += (T)corr[0] + qf * (rr - (T)cp.c_charged) - (T)cp.c_self * (T)cellq[qcell];
+    const T qf = cr[4];
+    const T cch = F32 ? (T)cp.c_charged32 : (T)cp.c_charged, cself = F32 ? (T)cp.c_self32 : (T)cp.c_self;
+    phi += cr[0] + qf * (rr - cch) - cself * (T)cellq[qcell];
 #pragma unroll
     for (int a = 0; a < 3; ++a) g[a] += T(2) * qf * rel[a];
     // the dipole term corrects L_1 (App. B.3), which exists only for p >= 1
     if (P >= 1) {
-      phi += (T)corr[1] * rel[0] + (T)corr[2] * rel[1] + (T)corr[3] * rel[2];
+      phi += cr[1] * rel[0] + cr[2] * rel[1] + cr[3] * rel[2];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) g[a] += (T)corr[1 + a];
+      for (int a = 0; a < 3; ++a) g[a] += cr[1 + a];
     }
   }
   typename V4<T>::type o;

@@ -347,6 +347,10 @@ int read_device_status(pmmm_plan* pl) {
   return PMMM_OK;
 }
 
+// The two counters of the single-launch reductions (corrections, energy): the
+// last doubles of partial, which the reductions (256 x 9 doubles) leave unused.
+unsigned int* reduce_tickets(pmmm_plan* pl) { return reinterpret_cast<unsigned int*>(pl->partial + 256 * 15); }
+
 void mark(pmmm_plan* pl, int st) {
   if (pl->timing && !pl->capturing) cudaEventRecord(pl->ev[st], pl->stream);
 }
@@ -473,10 +477,11 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
       // the corrections belong to the coarse level (its Ewald split, its cells;
       // the coarse per-cell sums come from the coarse P2M)
       pmmm_plan* cp = pl->coarse;
-      CK(launch_corrections(cp->cellsum, cp->cellsum + cp->d.K, cp->d.K, cp->g.hs, pl->g.V, pl->partial, pl->corr, s,
-                            &nl));
+      CK(launch_corrections(cp->cellsum, cp->cellsum + cp->d.K, cp->d.K, cp->g.hs, pl->g.V, pl->partial,
+                            reduce_tickets(pl), pl->corr, s, &nl));
     } else if (B == 1) {
-      CK(launch_corrections(pl->cellsum, pl->cellsum + K, K, pl->g.hs, pl->g.V, pl->partial, pl->corr, s, &nl));
+      CK(launch_corrections(pl->cellsum, pl->cellsum + K, K, pl->g.hs, pl->g.V, pl->partial, reduce_tickets(pl),
+                            pl->corr, s, &nl));
     } else {
       CK(launch_corrections_batched(pl->cellsum, K, Ks, B, pl->g.hs, pl->g.V, pl->bpartial, pl->corr, s, &nl));
     }
@@ -497,7 +502,13 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
       cp.nf[a] = pl->g.n[a];
       cp.nc[a] = pl->hier ? pl->hg.nc[a] : pl->g.n[a];
       cp.cs[a] = pl->g.cs[a];
+      cp.cshs32[a] = (float)(cp.cs[a] * cp.hs);
     }
+    cp.hs32 = (float)cp.hs;
+    cp.ih32 = (float)cp.ih;
+    cp.ih2_32 = (float)cp.ih2;
+    cp.c_charged32 = (float)cp.c_charged;
+    cp.c_self32 = (float)cp.c_self;
     const double* cellq = pl->hier ? pl->coarse->cellsum : pl->cellsum;
     const void* Luse = pl->L;
     int puse = pl->p;
@@ -531,7 +542,7 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
                  &nl));
     mark(pl, ST_REDUCE);
     if (B == 1)
-      CK(launch_energy(pl->epart, mi, pl->partial + 256 * 5, pl->energy, s, &nl));
+      CK(launch_energy(pl->epart, mi, pl->partial + 256 * 5, reduce_tickets(pl) + 1, pl->energy, s, &nl));
     else
       CK(launch_energy_batched(pl->epart, pl->item_start, Ks, B, pl->bchunks, pl->bpartial, pl->energy, s, &nl));
   }
@@ -758,6 +769,8 @@ int pmmm_plan_create(const pmmm_config* cfg, void* stream, pmmm_plan** out) {
   if (e == cudaSuccess) e = dalloc(pl, &pl->twy, 2 * T * d.Ly);
   if (e == cudaSuccess) e = dalloc(pl, &pl->twz, 2 * T * d.Lz);
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 256 * 16); pl->partial = (double*)v; }
+  // the reduction tickets at the end of partial start at zero
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->partial, 0, sizeof(double) * 256 * 16, pl->stream);
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(int)); pl->err = (int*)v; }
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(unsigned int)); pl->counter = (unsigned int*)v; }
   if (e == cudaSuccess) {

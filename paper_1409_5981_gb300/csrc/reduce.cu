@@ -1,6 +1,7 @@
 // FP64 global reductions: the periodic correction terms of App. B.3 and the
-// energy / net force.  Both are two-level tree reductions with a fixed
-// assignment of cells to threads, so the results do not depend on scheduling.
+// energy / net force.  Both are two-level tree reductions in one launch with a
+// fixed assignment of cells to threads and of block partials to the final sum,
+// so the results do not depend on scheduling.
 #include "internal.cuh"
 
 namespace pmmm {
@@ -11,12 +12,36 @@ constexpr int RD_THREADS = 256;
 constexpr int RD_BLOCKS = 256;
 constexpr double kPi = 3.14159265358979323846;
 
-// Sums NQ per-cell quantities, quantity q of cell i at src[q * qstride + i * istride].
 template <int NQ>
-__global__ void __launch_bounds__(RD_THREADS) reduce_partial_kernel(const double* __restrict__ src, int64_t K,
-                                                                    int64_t qstride, int64_t istride,
-                                                                    double* __restrict__ partial) {
+__device__ void reduce_final(const double* __restrict__ partial, int nb, double* out) {
   __shared__ double sh[NQ][RD_THREADS];
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += RD_THREADS)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] += __ldcg(partial + b * NQ + q);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int w = RD_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < NQ) out[threadIdx.x] = sh[threadIdx.x][0];
+  __syncthreads();
+}
+
+// One launch for both levels of the tree: every block writes its NQ partial
+// sums, and the block that finishes last (atomic ticket) sums all partials in
+// block order into tot and re-arms the ticket.  Returns true in that block.
+template <int NQ>
+__device__ bool reduce_ticketed(const double* __restrict__ src, int64_t K, int64_t qstride, int64_t istride,
+                                double* __restrict__ partial, unsigned int* __restrict__ ticket, double* tot) {
+  __shared__ double sh[NQ][RD_THREADS];
+  __shared__ bool last;
   double acc[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
@@ -35,38 +60,29 @@ __global__ void __launch_bounds__(RD_THREADS) reduce_partial_kernel(const double
     __syncthreads();
   }
   if (threadIdx.x < NQ) partial[blockIdx.x * NQ + threadIdx.x] = sh[threadIdx.x][0];
-}
-
-template <int NQ>
-__device__ void reduce_final(const double* __restrict__ partial, int nb, double* out) {
-  __shared__ double sh[NQ][RD_THREADS];
-  double acc[NQ];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
-  for (int b = threadIdx.x; b < nb; b += RD_THREADS)
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) acc[q] += partial[b * NQ + q];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) sh[q][threadIdx.x] = acc[q];
+  __threadfence();
   __syncthreads();
-  for (int w = RD_THREADS / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x < NQ) out[threadIdx.x] = sh[threadIdx.x][0];
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  reduce_final<NQ>(partial, gridDim.x, tot);
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
 }
 
 // corr[0] = 2pi/(3V) sum q |r_rel|^2           (potential constant, App. B.3)
 // corr[1..3] = -4pi/(3V) sum q r_rel           (dipole term of Eq. phicorr)
 // corr[4] = 2pi/(3V) Q                         (charged-system factor)
+// doubles 5..7 = FP32 copies of corr[0..4]
 // corr[8..12] = Q, sum q u (3), sum q |u|^2 in units of hs
-__global__ void __launch_bounds__(RD_THREADS) corrections_kernel(const double* __restrict__ partial, int nb, double hs,
-                                                                 double V, double* __restrict__ corr) {
+__global__ void __launch_bounds__(RD_THREADS) corrections_fused_kernel(const double* __restrict__ cellsum, int64_t K,
+                                                                       double hs, double V,
+                                                                       double* __restrict__ partial,
+                                                                       unsigned int* __restrict__ ticket,
+                                                                       double* __restrict__ corr) {
   __shared__ double tot[5];
-  reduce_final<5>(partial, nb, tot);
+  if (!reduce_ticketed<5>(cellsum, K, K, 1, partial, ticket, tot)) return;
   if (threadIdx.x == 0) {
     const double f = 2.0 * kPi / (3.0 * V);
     const double Q = tot[0];
@@ -75,14 +91,17 @@ __global__ void __launch_bounds__(RD_THREADS) corrections_kernel(const double* _
     corr[2] = -2.0 * f * tot[2] * hs;
     corr[3] = -2.0 * f * tot[3] * hs;
     corr[4] = f * Q;
+    corr_store_f32(corr);
     for (int q = 0; q < 5; ++q) corr[8 + q] = tot[q];
   }
 }
 
-__global__ void __launch_bounds__(RD_THREADS) energy_final_kernel(const double* __restrict__ partial, int nb,
+__global__ void __launch_bounds__(RD_THREADS) energy_fused_kernel(const double* __restrict__ epart, int64_t count,
+                                                                  double* __restrict__ partial,
+                                                                  unsigned int* __restrict__ ticket,
                                                                   double* __restrict__ energy) {
   __shared__ double tot[4];
-  reduce_final<4>(partial, nb, tot);
+  if (!reduce_ticketed<4>(epart, count, 1, 4, partial, ticket, tot)) return;
   if (threadIdx.x < 4) energy[threadIdx.x] = tot[threadIdx.x];
 }
 
@@ -104,20 +123,18 @@ __global__ void to_physical_kernel(const T* __restrict__ X, double* __restrict__
 }  // namespace
 
 cudaError_t launch_corrections(const double* cellq, const double* celld, int64_t K, double hs, double V,
-                               double* partial, double* corr, cudaStream_t s, int* nl) {
+                               double* partial, unsigned int* ticket, double* corr, cudaStream_t s, int* nl) {
   // quantity 0 = cellq, quantities 1..4 = celld[0..3]; celld follows cellq in memory
   (void)celld;
-  reduce_partial_kernel<5><<<RD_BLOCKS, RD_THREADS, 0, s>>>(cellq, K, K, 1, partial);
-  corrections_kernel<<<1, RD_THREADS, 0, s>>>(partial, RD_BLOCKS, hs, V, corr);
-  *nl += 2;
+  corrections_fused_kernel<<<RD_BLOCKS, RD_THREADS, 0, s>>>(cellq, K, hs, V, partial, ticket, corr);
+  ++*nl;
   return cudaGetLastError();
 }
 
-cudaError_t launch_energy(const double* epart, int64_t count, double* partial, double* energy, cudaStream_t s,
-                          int* nl) {
-  reduce_partial_kernel<4><<<RD_BLOCKS, RD_THREADS, 0, s>>>(epart, count, 1, 4, partial);
-  energy_final_kernel<<<1, RD_THREADS, 0, s>>>(partial, RD_BLOCKS, energy);
-  *nl += 2;
+cudaError_t launch_energy(const double* epart, int64_t count, double* partial, unsigned int* ticket, double* energy,
+                          cudaStream_t s, int* nl) {
+  energy_fused_kernel<<<RD_BLOCKS, RD_THREADS, 0, s>>>(epart, count, partial, ticket, energy);
+  ++*nl;
   return cudaGetLastError();
 }
 
