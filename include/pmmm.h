@@ -138,12 +138,20 @@ int pmmm_plan_reserve(pmmm_plan* plan, int64_t n_max);
  *           reports input errors (out-of-box, non-finite) detected on device.
  * Without `energy` the call is asynchronous: input errors detected on the device
  * are reported by the next pmmm_plan_status().  Invalid positions never cause an
- * out-of-bounds access: they are clamped into a cell and flagged. */
+ * out-of-bounds access: they are clamped into a cell and flagged.
+ * Launch form: the first call with given n, pointers and plan workspace queues
+ * the kernels one by one; from the second such call in a row on, the plan
+ * launches a CUDA graph of the same sequence (captured once on a plan-owned
+ * stream, launched on the plan's stream: same kernels, same results bit for
+ * bit, one host call per evaluation).  Calls made while stage timing is on
+ * (pmmm_plan_set_timing) or while the caller is capturing the plan's stream
+ * queue the kernels one by one. */
 int pmmm_compute(pmmm_plan* plan, int64_t n, const void* pos, const void* q, void* phi, void* force, double* energy);
 
 /* Same as pmmm_compute with HOST arrays (pinned memory recommended): copies
- * the inputs to plan-owned device buffers, computes, and copies phi / force
- * back; synchronises the stream and returns the device-side status.  */
+ * the inputs to plan-owned device buffers, computes (with the launch form of
+ * pmmm_compute), and copies phi / force back; synchronises the stream and
+ * returns the device-side status.  */
 int pmmm_compute_host(pmmm_plan* plan, int64_t n, const void* pos, const void* q, void* phi, void* force,
                       double* energy);
 
@@ -178,13 +186,14 @@ int pmmm_compute_batched_host(pmmm_plan* plan, int32_t nsys, const int64_t* offs
                               void* phi, void* force, double* energies);
 
 /* pmmm_compute_batched replayed from a CUDA graph: the first call (and any call
- * whose offsets or array pointers differ from the previous graph call's) uploads
- * the offsets, reserves the workspace, captures the whole evaluation on the
- * plan's stream into a graph and instantiates it; every call then launches the
- * graph, so one host call queues every kernel of the evaluation.  The plan's
- * stream must not be the legacy default stream (PMMM_ERR_UNSUPPORTED).  The
- * graph reads the arrays at the pointers it was captured with: reuse the same
- * buffers to avoid a new capture.  Per-stage timing is not recorded. */
+ * whose offsets or array pointers differ from those of the graph, or made after
+ * the plan's workspace was reallocated or re-tuned) uploads the offsets,
+ * reserves the workspace, captures the whole evaluation into a graph on a
+ * plan-owned stream and instantiates it; every call then launches the graph on
+ * the plan's stream (any stream, the legacy default stream included), so one
+ * host call queues every kernel of the evaluation.  The graph reads the arrays
+ * at the pointers it was captured with: reuse the same buffers to avoid a new
+ * capture.  Per-stage timing is not recorded. */
 int pmmm_compute_batched_graph(pmmm_plan* plan, int32_t nsys, const int64_t* offsets, const void* pos,
                                const void* q, void* phi, void* force, double* energies);
 

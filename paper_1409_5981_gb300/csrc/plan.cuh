@@ -62,11 +62,22 @@ struct pmmm_plan {
   uint32_t* m2l_tab_tc = nullptr;     // packed entry table of the tensor-core M2L
   bool m2l_tc = false;                // batched M2L on the tensor cores (split BF16)
   std::unordered_map<void*, size_t> sizes;
-  // CUDA graph of one batched evaluation, and the arguments it was captured for
+  // CUDA graph of one evaluation, and what it was captured for: the systems'
+  // offsets, the caller's pointers, the workspace generation and the tuning
+  // choices.  Captured on a private stream, launched on the plan's stream.
   cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cstream = nullptr;
   std::vector<int64_t> gkey_off;
   const void* gkey_ptr[4] = {nullptr, nullptr, nullptr, nullptr};
+  uint64_t gkey_gen = 0;
+  int gkey_tune[2] = {0, 0};
   bool capturing = false;
+  // the last plain single-system call (pmmm_compute takes the graph from the
+  // second identical call on)
+  std::vector<int64_t> lkey_off;
+  const void* lkey_ptr[4] = {nullptr, nullptr, nullptr, nullptr};
+  uint64_t lkey_gen = 0;
+  uint64_t wgen = 0;  // bumped by every workspace allocation and release
   const pmmm::FarHook* hook = nullptr;  // set by the surrogate for one evaluation
   // choices of pmmm_plan_autotune: near-field kernel (0: from the config), tensor-core M2L system tile
   int tuned_near = 0;

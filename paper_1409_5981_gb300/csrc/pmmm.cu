@@ -36,6 +36,7 @@ cudaError_t dalloc(pmmm_plan* pl, void** ptr, size_t bytes) {
   if (e == cudaSuccess) {
     pl->ws_bytes += bytes;
     pl->sizes[*ptr] = bytes;
+    ++pl->wgen;
   }
   return e;
 }
@@ -49,6 +50,7 @@ void dfree(pmmm_plan* pl, P*& p) {
       pl->sizes.erase(it);
     }
     cudaFree((void*)p);
+    ++pl->wgen;
   }
   p = nullptr;
 }
@@ -108,6 +110,8 @@ void free_all(pmmm_plan* pl) {
   dfree(pl, pl->hpos); dfree(pl, pl->hq); dfree(pl, pl->hphi); dfree(pl, pl->hforce);
   if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
   pl->gexec = nullptr;
+  if (pl->cstream) cudaStreamDestroy(pl->cstream);
+  pl->cstream = nullptr;
   for (int i = 0; i <= ST_COUNT; ++i)
     if (pl->ev[i]) cudaEventDestroy(pl->ev[i]);
 }
@@ -622,6 +626,102 @@ int read_energies(pmmm_plan* pl, int B, double* out) {
   return rc;
 }
 
+// Workspace generation of a plan and its sub-plans (two-level plans): changes
+// whenever any buffer that a captured graph may reference is allocated or freed.
+uint64_t plan_gen(const pmmm_plan* pl) {
+  uint64_t g = pl->wgen;
+  if (pl->coarse) g += plan_gen(pl->coarse);
+  if (pl->block) g += plan_gen(pl->block);
+  return g;
+}
+
+void set_streams(pmmm_plan* pl, cudaStream_t s) {
+  pl->stream = s;
+  if (pl->coarse) set_streams(pl->coarse, s);
+  if (pl->block) set_streams(pl->block, s);
+}
+
+// One evaluation of B systems as a CUDA graph launched on the plan's stream:
+// replayed when it was captured for the same offsets, caller pointers,
+// workspace and tuning choices, captured again otherwise.  The capture runs on a
+// private stream, so any stream of the caller works (the legacy default stream
+// included).  The workspace must already hold B systems and n particles:
+// nothing is allocated while capturing.
+int graph_eval(pmmm_plan* pl, int B, int64_t n, const int64_t* off, const void* pos, const void* q, void* phi,
+               void* force) {
+  const void* ptrs[4] = {pos, q, phi, force};
+  const uint64_t gen = plan_gen(pl);
+  const bool same = pl->gexec && pl->gkey_off.size() == (size_t)B + 1 &&
+                    memcmp(pl->gkey_off.data(), off, sizeof(int64_t) * (B + 1)) == 0 &&
+                    memcmp(pl->gkey_ptr, ptrs, sizeof(ptrs)) == 0 && pl->gkey_gen == gen &&
+                    pl->gkey_tune[0] == pl->tuned_near && pl->gkey_tune[1] == pl->m2l_tile;
+  cudaError_t e = cudaSuccess;
+  if (!same) {
+    if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
+    pl->gexec = nullptr;
+    pl->gkey_off.clear();
+    if (!pl->cstream) {
+      e = cudaStreamCreateWithFlags(&pl->cstream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) {
+        pl->cstream = nullptr;
+        return map_cuda(e);
+      }
+    }
+    cudaStream_t user = pl->stream;
+    set_streams(pl, pl->cstream);
+    e = cudaStreamBeginCapture(pl->cstream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      set_streams(pl, user);
+      return map_cuda(e);
+    }
+    pl->capturing = true;
+    const int rc = run(pl, B, n, pos, q, phi, force);
+    pl->capturing = false;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(pl->cstream, &graph);
+    set_streams(pl, user);
+    if (e == cudaSuccess && rc == PMMM_OK) e = cudaGraphInstantiate(&pl->gexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != PMMM_OK || e != cudaSuccess) {
+      if (pl->gexec && e != cudaSuccess) cudaGraphExecDestroy(pl->gexec);
+      pl->gexec = nullptr;
+      return rc != PMMM_OK ? rc : map_cuda(e);
+    }
+    pl->gkey_off.assign(off, off + B + 1);
+    memcpy(pl->gkey_ptr, ptrs, sizeof(ptrs));
+    pl->gkey_gen = gen;
+    pl->gkey_tune[0] = pl->tuned_near;
+    pl->gkey_tune[1] = pl->m2l_tile;
+  }
+  e = cudaGraphLaunch(pl->gexec, pl->stream);
+  if (e != cudaSuccess) return map_cuda(e);
+  pl->n_last = n;
+  pl->nsys_last = B;
+  return PMMM_OK;
+}
+
+// A single-system evaluation: the plain launch sequence on the first call with
+// given pointers and sizes, a CUDA graph of it from the second identical call in
+// a row on (not while stage timing is on, nor while the caller captures the
+// plan's stream into a graph of its own, which then records the plain launches).
+int run_single(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, void* force) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (pl->timing || cudaStreamIsCapturing(pl->stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+    return run(pl, 1, n, pos, q, phi, force);
+  int rc = ensure_systems(pl, 1);
+  if (rc == PMMM_OK) rc = ensure_particles(pl, n);
+  if (rc != PMMM_OK) return rc;
+  const int64_t off[2] = {0, n};
+  const void* ptrs[4] = {pos, q, phi, force};
+  const uint64_t gen = plan_gen(pl);
+  const bool repeat = pl->lkey_off.size() == 2 && pl->lkey_off[1] == n &&
+                      memcmp(pl->lkey_ptr, ptrs, sizeof(ptrs)) == 0 && pl->lkey_gen == gen;
+  pl->lkey_off.assign(off, off + 2);
+  memcpy(pl->lkey_ptr, ptrs, sizeof(ptrs));
+  pl->lkey_gen = gen;
+  return repeat ? graph_eval(pl, 1, n, off, pos, q, phi, force) : run(pl, 1, n, pos, q, phi, force);
+}
+
 // Plan-owned device buffers for host-array calls of n particles.
 int ensure_host_staging(pmmm_plan* pl, int64_t n) {
   if (n <= pl->hcap) return PMMM_OK;
@@ -650,7 +750,8 @@ int run_host(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, vo
     if (e == cudaSuccess) e = cudaMemcpyAsync(pl->hq, q, T * (size_t)n, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return map_cuda(e);
   }
-  rc = run(pl, B, n, pl->hpos, pl->hq, phi ? pl->hphi : nullptr, force ? pl->hforce : nullptr);
+  rc = B == 1 ? run_single(pl, n, pl->hpos, pl->hq, phi ? pl->hphi : nullptr, force ? pl->hforce : nullptr)
+              : run(pl, B, n, pl->hpos, pl->hq, phi ? pl->hphi : nullptr, force ? pl->hforce : nullptr);
   if (rc != PMMM_OK) return rc;
   if (phi && n > 0) e = cudaMemcpyAsync(phi, pl->hphi, T * (size_t)n, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && force && n > 0)
@@ -825,7 +926,7 @@ int pmmm_plan_reserve_batched(pmmm_plan* pl, int32_t nsys, int64_t n) {
 int pmmm_compute(pmmm_plan* pl, int64_t n, const void* pos, const void* q, void* phi, void* force, double* energy) {
   if (!pl || n < 0 || n > INT32_MAX) return PMMM_ERR_INVALID_ARG;
   if (n > 0 && (!pos || !q)) return PMMM_ERR_INVALID_ARG;
-  int rc = run(pl, 1, n, pos, q, phi, force);
+  int rc = run_single(pl, n, pos, q, phi, force);
   if (rc != PMMM_OK) return rc;
   return energy ? read_energies(pl, 1, energy) : PMMM_OK;
 }
@@ -875,43 +976,14 @@ int pmmm_compute_batched_graph(pmmm_plan* pl, int32_t nsys, const int64_t* offse
                                void* phi, void* force, double* energies) {
   if (!pl || nsys < 1 || nsys > PMMM_MAX_SYSTEMS || !offsets) return PMMM_ERR_INVALID_ARG;
   if (pl->d.K * nsys > ((int64_t)1 << 30)) return PMMM_ERR_UNSUPPORTED;
-  if (!pl->stream) return PMMM_ERR_UNSUPPORTED;  // the legacy default stream cannot be captured
   int64_t n = 0;
   int rc = upload_offsets(pl, nsys, offsets, &n);  // may synchronise: before any capture
   if (rc != PMMM_OK) return rc;
   if (n > 0 && (!pos || !q)) return PMMM_ERR_INVALID_ARG;
   rc = ensure_particles(pl, n);
   if (rc != PMMM_OK) return rc;
-  const void* ptrs[4] = {pos, q, phi, force};
-  const bool same = pl->gexec && pl->gkey_off.size() == (size_t)nsys + 1 &&
-                    memcmp(pl->gkey_off.data(), offsets, sizeof(int64_t) * (nsys + 1)) == 0 &&
-                    memcmp(pl->gkey_ptr, ptrs, sizeof(ptrs)) == 0;
-  cudaError_t e = cudaSuccess;
-  if (!same) {
-    if (pl->gexec) cudaGraphExecDestroy(pl->gexec);
-    pl->gexec = nullptr;
-    pl->gkey_off.clear();
-    e = cudaStreamBeginCapture(pl->stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return map_cuda(e);
-    pl->capturing = true;
-    rc = run(pl, nsys, n, pos, q, phi, force);
-    pl->capturing = false;
-    cudaGraph_t graph = nullptr;
-    e = cudaStreamEndCapture(pl->stream, &graph);
-    if (e == cudaSuccess && rc == PMMM_OK) e = cudaGraphInstantiate(&pl->gexec, graph, 0);
-    if (graph) cudaGraphDestroy(graph);
-    if (rc != PMMM_OK) return rc;
-    if (e != cudaSuccess) {
-      pl->gexec = nullptr;
-      return map_cuda(e);
-    }
-    pl->gkey_off.assign(offsets, offsets + nsys + 1);
-    memcpy(pl->gkey_ptr, ptrs, sizeof(ptrs));
-  }
-  e = cudaGraphLaunch(pl->gexec, pl->stream);
-  if (e != cudaSuccess) return map_cuda(e);
-  pl->n_last = n;
-  pl->nsys_last = nsys;
+  rc = graph_eval(pl, nsys, n, offsets, pos, q, phi, force);
+  if (rc != PMMM_OK) return rc;
   return energies ? read_energies(pl, nsys, energies) : PMMM_OK;
 }
 
