@@ -25,93 +25,77 @@ PMMM_HD cpx<T> s_im(const cpx<T>* sre, const cpx<T>* sim) {
   return ((-KAP) & 1) ? sim[-KAP] : mk(-sim[-KAP].x, -sim[-KAP].y);
 }
 
-// Compile-time loops (the orders m, mu are template constants so that every
-// register array index and sign is fixed at compile time).
+// One term (m, mu) of the real-matrix M2L (Eq. realmatrix) for the current
+// output order l and source order lam: the orders m, mu are template constants,
+// so that every register array index and sign is fixed at compile time.
 template <int P, typename T, int M, int MU>
-struct M2LTerm {
-  PMMM_HD static void apply(int l, int lam, const cpx<T>* sre, const cpx<T>* sim, const cpx<T>* mre,
-                            const cpx<T>* mim, cpx<T>* Lre, cpx<T>* Lim) {
-    if (M <= l && MU <= lam) {
-      // G^{m,mu} = S_{l+lam}^{-(m+mu)}:  A = Re, B = Im  (Eq. realmatrix)
-      const cpx<T> A = s_re<T, -(M + MU)>(sre, sim);
-      const cpx<T> B = s_im<T, -(M + MU)>(sre, sim);
-      if (MU == 0) {
-        cmac(Lre[M], A, mre[0]);
-        cmac(Lim[M], B, mre[0]);
-      } else {
-        // (-1)^mu G^{m,-mu} = (-1)^mu S_{l+lam}^{-(m-mu)}:  C = Re, D = Im
-        cpx<T> C = s_re<T, MU - M>(sre, sim);
-        cpx<T> D = s_im<T, MU - M>(sre, sim);
-        if (MU & 1) {
-          C = mk(-C.x, -C.y);
-          D = mk(-D.x, -D.y);
-        }
-        // Re L += (A + C) Re M - (B - D) Im M ;  Im L += (B + D) Re M + (A - C) Im M
-        cmac(Lre[M], A + C, mre[MU]);
-        cmac(Lre[M], D - B, mim[MU]);
-        cmac(Lim[M], B + D, mre[MU]);
-        cmac(Lim[M], A - C, mim[MU]);
-      }
+PMMM_HD void m2l_term(const cpx<T>* sre, const cpx<T>* sim, const cpx<T>* mre, const cpx<T>* mim, cpx<T>* Lre,
+                      cpx<T>* Lim) {
+  // G^{m,mu} = S_{l+lam}^{-(m+mu)}:  A = Re, B = Im  (Eq. realmatrix)
+  const cpx<T> A = s_re<T, -(M + MU)>(sre, sim);
+  const cpx<T> B = s_im<T, -(M + MU)>(sre, sim);
+  if constexpr (MU == 0) {
+    cmac(Lre[M], A, mre[0]);
+    cmac(Lim[M], B, mre[0]);
+  } else {
+    // (-1)^mu G^{m,-mu} = (-1)^mu S_{l+lam}^{-(m-mu)}:  C = Re, D = Im
+    cpx<T> C = s_re<T, MU - M>(sre, sim);
+    cpx<T> D = s_im<T, MU - M>(sre, sim);
+    if constexpr (MU & 1) {
+      C = mk(-C.x, -C.y);
+      D = mk(-D.x, -D.y);
     }
-    M2LTerm<P, T, M, MU + 1>::apply(l, lam, sre, sim, mre, mim, Lre, Lim);
+    // Re L += (A + C) Re M - (B - D) Im M ;  Im L += (B + D) Re M + (A - C) Im M
+    cmac(Lre[M], A + C, mre[MU]);
+    cmac(Lre[M], D - B, mim[MU]);
+    cmac(Lim[M], B + D, mre[MU]);
+    cmac(Lim[M], A - C, mim[MU]);
+  }
+}
+
+// The terms of one source order lam, column by column (mu = 0 .. lam), each
+// column over the rows m = 0 .. l.  Both walks stop at their first term outside
+// the triangle (mu > lam, m > l): lam and l are the same for every thread of a
+// block, so what is left of the walk is skipped by one uniform branch instead of
+// being issued under a false predicate.  Each output accumulates its terms in
+// the order mu = 0, 1, ... as in a row-by-row walk.
+template <int P, typename T, int M, int MU>
+struct M2LCol {
+  PMMM_HD static void apply(int l, const cpx<T>* sre, const cpx<T>* sim, const cpx<T>* mre, const cpx<T>* mim,
+                            cpx<T>* Lre, cpx<T>* Lim) {
+    if (M > l) return;
+    m2l_term<P, T, M, MU>(sre, sim, mre, mim, Lre, Lim);
+    if constexpr (M < P) M2LCol<P, T, M + 1, MU>::apply(l, sre, sim, mre, mim, Lre, Lim);
   }
 };
-template <int P, typename T, int M>
-struct M2LTerm<P, T, M, P + 1> {
-  PMMM_HD static void apply(int l, int lam, const cpx<T>*, const cpx<T>*, const cpx<T>*, const cpx<T>*, cpx<T>*,
-                            cpx<T>*) {
-    (void)l; (void)lam;
-  }
-};
-template <int P, typename T, int M>
-struct M2LRow {
+template <int P, typename T, int MU>
+struct M2LCols {
   PMMM_HD static void apply(int l, int lam, const cpx<T>* sre, const cpx<T>* sim, const cpx<T>* mre,
                             const cpx<T>* mim, cpx<T>* Lre, cpx<T>* Lim) {
-    M2LTerm<P, T, M, 0>::apply(l, lam, sre, sim, mre, mim, Lre, Lim);
-    M2LRow<P, T, M + 1>::apply(l, lam, sre, sim, mre, mim, Lre, Lim);
+    if (MU > lam) return;
+    M2LCol<P, T, 0, MU>::apply(l, sre, sim, mre, mim, Lre, Lim);
+    if constexpr (MU < P) M2LCols<P, T, MU + 1>::apply(l, lam, sre, sim, mre, mim, Lre, Lim);
   }
-};
-template <int P, typename T>
-struct M2LRow<P, T, P + 1> {
-  PMMM_HD static void apply(int, int, const cpx<T>*, const cpx<T>*, const cpx<T>*, const cpx<T>*, cpx<T>*,
-                            cpx<T>*) {}
 };
 
-// The same terms with the output order L known at compile time (m <= L is
-// resolved by the compiler; the source order lam stays a runtime loop, which
+// The same walk with the output order L known at compile time (the rows m <= L
+// are resolved by the compiler; the source order lam stays a runtime loop, which
 // keeps the register arrays of one lam live at a time).
 template <int P, int L, typename T, int M, int MU>
-struct M2LTermL {
-  PMMM_HD static void apply(int lam, const cpx<T>* sre, const cpx<T>* sim, const cpx<T>* mre, const cpx<T>* mim,
-                            cpx<T>* Lre, cpx<T>* Lim) {
-    if (MU <= lam) {
-      const cpx<T> A = s_re<T, -(M + MU)>(sre, sim);
-      const cpx<T> B = s_im<T, -(M + MU)>(sre, sim);
-      if constexpr (MU == 0) {
-        cmac(Lre[M], A, mre[0]);
-        cmac(Lim[M], B, mre[0]);
-      } else {
-        cpx<T> C = s_re<T, MU - M>(sre, sim);
-        cpx<T> D = s_im<T, MU - M>(sre, sim);
-        if constexpr (MU & 1) {
-          C = mk(-C.x, -C.y);
-          D = mk(-D.x, -D.y);
-        }
-        cmac(Lre[M], A + C, mre[MU]);
-        cmac(Lre[M], D - B, mim[MU]);
-        cmac(Lim[M], B + D, mre[MU]);
-        cmac(Lim[M], A - C, mim[MU]);
-      }
-    }
-    if constexpr (MU < P) M2LTermL<P, L, T, M, MU + 1>::apply(lam, sre, sim, mre, mim, Lre, Lim);
+struct M2LColL {
+  PMMM_HD static void apply(const cpx<T>* sre, const cpx<T>* sim, const cpx<T>* mre, const cpx<T>* mim, cpx<T>* Lre,
+                            cpx<T>* Lim) {
+    m2l_term<P, T, M, MU>(sre, sim, mre, mim, Lre, Lim);
+    if constexpr (M < L) M2LColL<P, L, T, M + 1, MU>::apply(sre, sim, mre, mim, Lre, Lim);
   }
 };
-template <int P, int L, typename T, int M>
-struct M2LRowL {
+template <int P, int L, typename T, int MU>
+struct M2LColsL {
   PMMM_HD static void apply(int lam, const cpx<T>* sre, const cpx<T>* sim, const cpx<T>* mre, const cpx<T>* mim,
                             cpx<T>* Lre, cpx<T>* Lim) {
-    M2LTermL<P, L, T, M, 0>::apply(lam, sre, sim, mre, mim, Lre, Lim);
-    if constexpr (M < L) M2LRowL<P, L, T, M + 1>::apply(lam, sre, sim, mre, mim, Lre, Lim);
+    if (MU > lam) return;
+    M2LColL<P, L, T, 0, MU>::apply(sre, sim, mre, mim, Lre, Lim);
+    if constexpr (MU < P) M2LColsL<P, L, T, MU + 1>::apply(lam, sre, sim, mre, mim, Lre, Lim);
   }
 };
 template <int P, int L, typename T, class LM, class LG, class ST>
@@ -144,7 +128,7 @@ PMMM_HD void m2l_order_l(int p, LM&& Mk, LG&& Gk, ST&& St) {
         if (a > 0) sim[a] = Gk(sidx(j, -a));
       }
     }
-    M2LRowL<P, L, T, 0>::apply(lam, sre, sim, mre, mim, Lre, Lim);
+    M2LColsL<P, L, T, 0>::apply(lam, sre, sim, mre, mim, Lre, Lim);
   }
 #pragma unroll
   for (int m = 0; m <= L; ++m) {
@@ -188,7 +172,7 @@ PMMM_HD void m2l_order(int l, int p, LM&& Mk, LG&& Gk, ST&& St) {
         if (a > 0) sim[a] = Gk(sidx(j, -a));
       }
     }
-    M2LRow<P, T, 0>::apply(l, lam, sre, sim, mre, mim, Lre, Lim);
+    M2LCols<P, T, 0>::apply(l, lam, sre, sim, mre, mim, Lre, Lim);
   }
 #pragma unroll
   for (int m = 0; m <= P; ++m) {
