@@ -179,7 +179,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "50", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                                          "-lms", "20", "-i", self.gpu_id], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -290,6 +290,94 @@ def _cpu_baseline(name: str, pos, q, g, budget_s: float = 20.0):
             "sample": f"FP64 oracle ({'two-level cell-pair definition, Sec. 5' if _refine(name) > 1 else 'cell-pair convolution of Eq. pmmm'}), one evaluation of the same {n}-particle "
                       f"workload restricted to {ncell} seeded target cells ({done} particles) after its Green-function "
                       f"table; {dt:.1f} s"}
+
+
+def _probe_alu(pk):
+    """Measured FP32 FMA rate (flop/s) of this GPU: the larger of the scalar and the
+    packed (f32x2) probe, with both values."""
+    s32 = pk.probe_peak(pk.PROBE_FP32_FMA)
+    s32x2 = pk.probe_peak(pk.PROBE_FP32X2_FMA)
+    return max(s32, s32x2), {"fp32_fma_tflops": s32 / 1e12, "fp32x2_fma_tflops": s32x2 / 1e12}
+
+
+def _mesh_bytes(C, CG, K, Kh, esz):
+    """(bytes of the mesh stages fft_forward + m2l + fft_inverse: M read, each spectrum
+    written and read, G~ read, L written; the same plus the P2M write of M and the L2P
+    read of L, the ideal-pass model 16CK + 32CKh + 8C_G Kh for FP32)."""
+    own = esz * (2 * C * K + 8 * C * Kh + 2 * CG * Kh)
+    full = esz * (4 * C * K + 8 * C * Kh + 2 * CG * Kh)
+    return own, full
+
+
+def _mesh_roofline_64(pk, torch, dev, hbm, flush, steps=6):
+    """The mesh stage of the 2^24-particle, 64^3, p = 7, FP32 periodic workload (the
+    precision-sweep configuration, working set far above L2), timed per stage with
+    CUDA events (median of `steps` evaluations after two warm-ups, L2 flushed)."""
+    name = "periodic_uniform_n16777216_mesh64_p7_fp32"
+    n, boundary, mesh, p, prec, lo, ln, gen, sign, cut = _wl(name)
+    cfg = pk.Config(box_lo=lo, box_len=ln, mesh=(mesh,) * 3, p=p, boundary=pk.PERIODIC, precision=pk.FP32)
+    pos_np, q_np = synth.uniform_pm1(n, synth.seed(3, 0), lo, ln)
+    with pk.Plan(cfg) as plan:
+        pos = torch.tensor(pos_np.astype(np.float32), device=dev)
+        q = torch.tensor(q_np.astype(np.float32), device=dev)
+        phi = torch.empty(n, dtype=torch.float32, device=dev)
+        force = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        for _ in range(2):
+            plan.compute(pos, q, phi, force)
+        plan.set_timing(True)
+        acc, tot = {}, []
+        for _ in range(steps):
+            flush.zero_()
+            plan.compute(pos, q, phi, force)
+            st = plan.stage_times()
+            for k, v in st.items():
+                acc.setdefault(k, []).append(v)
+            tot.append(sum(st.values()))
+        plan.set_timing(False)
+        C, CG, Kh, K = plan.info(pk.INFO_C), plan.info(pk.INFO_CG), plan.info(pk.INFO_KH), plan.info(pk.INFO_K)
+        status = plan.status()
+    if status != 0:
+        raise pk.PmmmError(status, "mesh roofline 64^3")
+    med = {k: statistics.median(v) for k, v in acc.items()}
+    ms = med["fft_forward"] + med["m2l"] + med["fft_inverse"]
+    own, full = _mesh_bytes(C, CG, K, Kh, 4)
+    return {"workload": name, "bound": "hbm", "unit": "GB/s", "peak": hbm,
+            "stages": "fft_forward + m2l + fft_inverse", "ms": ms,
+            "stage_ms": {k: med[k] for k in ("p2m", "fft_forward", "m2l", "fft_inverse", "l2p")},
+            "eval_ms": statistics.median(tot),
+            "achieved": own / (ms * 1e-3) / 1e9, "frac": own / (ms * 1e-3) / 1e9 / hbm,
+            "bytes": own, "bytes_model": "4B*(2CK + 8CKh + 2C_G Kh): M read, spectra written and read, G~ read, "
+                                          "L written",
+            "frac_survey_model": full / (ms * 1e-3) / 1e9 / hbm,
+            "survey_model": "16CK + 32CKh + 8C_G Kh (adds the P2M write of M and the L2P read of L, whose "
+                            "time is not in the stages timed)"}
+
+
+def _physical_error(name, pos64, q64, f_gpu, phi_gpu, sign, ntarget=4096):
+    """Relative RMS force error of the GPU forces against the physical reference on a
+    seeded subset of targets: Ewald (Eq. refewald, all sources) for periodic
+    workloads, the direct sum for open ones."""
+    import oracle
+    n, boundary, mesh, p, prec, lo, ln, gen, sign_, cut = _wl(name)
+    tg = synth.rng(4096).choice(pos64.shape[0], size=min(ntarget, pos64.shape[0]), replace=False)
+    t0 = time.perf_counter()
+    if boundary == "periodic":
+        phi_r, g_r = oracle.ewald_targets(pos64 - np.asarray(lo), q64, ln, tg, tol=1e-9)
+        kind = "Ewald (Eq. refewald) on"
+    else:
+        phi_r, g_r = oracle.direct(pos64, q64, targets=tg)
+        kind = "direct sum on"
+    dt = time.perf_counter() - t0
+    rf = -sign * q64[tg, None] * g_r
+    f = f_gpu[tg]
+    d = np.sqrt(((f - rf) ** 2).sum(1))
+    r = np.sqrt((rf ** 2).sum(1))
+    rms = float(np.sqrt((d ** 2).sum() / (r ** 2).sum()))
+    per = d / np.maximum(r, 1e-300)
+    ephi = float(np.sqrt(((phi_gpu[tg] - sign * phi_r) ** 2).sum() / ((phi_r) ** 2).sum()))
+    return {"rel_rms": rms, "max_per_particle": float(per.max()), "p99_per_particle": float(np.percentile(per, 99)),
+            "phi_rel_rms": ephi, "reference": f"{kind} {len(tg)} seeded target particles, all {pos64.shape[0]} sources",
+            "reference_s": dt}
 
 
 def _batched_inputs(name: str, rank: int):
@@ -430,7 +518,7 @@ def run_ours(args, rank, world, local_rank):
         if st != 0:
             raise pk.PmmmError(st, "pmmm_compute")
 
-    # accuracy of this workload: sampled cells against the oracle (rank 0, outside timing)
+    alu_meas, alu_probes = _probe_alu(pk)
     sampler = ClockSampler(_gpu_id(torch, local_rank))
     sampler.start()
     for _ in range(args.warmup):
@@ -514,10 +602,13 @@ def run_ours(args, rank, world, local_rank):
                        "coarse M written/read, block spectra written/read twice, block kernel spectra, kept "
                        "outputs written/read, coarse spectra and kernel, fine L written")
     hbm, sm_max, peak_kind = _peaks()
-    sm_clock = clocks.get("sm_max_mhz") or sm_max
-    alu_peak = 2.0 * FP32_LANES_PER_SM * NUM_SMS * sm_max * 1e6 / 1e12
+    alu_derived = 2.0 * FP32_LANES_PER_SM * NUM_SMS * sm_max * 1e6 / 1e12
+    alu_peak = alu_meas / 1e12
     pp_tf = PP_FLOPS_PER_PAIR * pairs / (pp_ms * 1e-3) / 1e12
     sha = _src_sha(["paper_1409_5981_gb300/csrc/pp.cu"])
+    mesh64 = None
+    if world == 1 and name == DEFAULT_WORKLOAD and not args.no_mesh64:
+        mesh64 = _mesh_roofline_64(pk, torch, dev, hbm, flush)
 
     # reduce over ranks: max time
     tmax, e2e_tot = _max_over_ranks([total_ms, sum(e2e_ms)], world, dev)
@@ -532,32 +623,47 @@ def run_ours(args, rank, world, local_rank):
     pos64, q64 = pos_np.astype(npdt).astype(np.float64), q_np.astype(npdt).astype(np.float64)
     if not (args.no_accuracy and (args.no_cpu_baseline or world > 1)):
         green = _oracle_green(name)
+    phys = None
+    err_max = None
     if not args.no_accuracy:
-        cells = synth.rng(99).choice(mesh ** 3, size=4, replace=False)
+        cells = synth.rng(99).choice(mesh ** 3, size=32, replace=False)
         r = _oracle_eval(name, pos64, q64, cells, green)
         sel = ~np.isnan(r["phi"])
         plan.compute_raw(n, pos.data_ptr(), q.data_ptr(), phi.data_ptr(), force.data_ptr())
-        f = force.cpu().numpy().astype(np.float64)[sel]
+        f_all = force.cpu().numpy().astype(np.float64)
+        phi_all = phi.cpu().numpy().astype(np.float64)
+        f = f_all[sel]
         rf = -sign * q64[sel, None] * r["grad"][sel]
         err = float(np.sqrt(((f - rf) ** 2).sum() / (rf ** 2).sum()))
+        err_max = float((np.sqrt(((f - rf) ** 2).sum(1)) / np.maximum(np.sqrt((rf ** 2).sum(1)), 1e-300)).max())
+        if refine <= 1:
+            phys = _physical_error(name, pos64, q64, f_all, phi_all, sign)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
         "config": _config(name, world, args.near_field),
         "rel_rms_force_err_vs_fp64_oracle_pmmm": err,
+        "max_per_particle_force_err_vs_fp64_oracle_pmmm": err_max,
+        "oracle_sample": "32 seeded target cells, oracle PMMM (cell-pair convolution of Eq. pmmm, FP64)",
+        "rel_rms_force_err_vs_ewald": phys["rel_rms"] if phys else None,
+        "force_err_vs_physical_reference": phys,
         "stage_ms": {k: statistics.median(v) for k, v in stage_acc.items()},
         "plan_create_s": t_plan,
         "roofline": {"bound": "alu", "kernel": "near field (pp_kernel)", "achieved": pp_tf,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": pp_tf / alu_peak,
                      "traffic": _traffic("pp_kernel", name, sha),
                      "per_launch": f"{pairs} pair interactions x {PP_FLOPS_PER_PAIR} flop",
-                     "peak_basis": f"{NUM_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
-                                   f"(FMA peak; HBM peak {hbm} GB/s {peak_kind})"},
+                     "peak_basis": "measured FP32 FMA rate (pmmm_probe_peak, larger of scalar and packed f32x2 "
+                                   "FMA chains, CUDA events)",
+                     "peak_probes": alu_probes, "peak_derived_tflops": alu_derived,
+                     "measured_over": "10 stage-timed evaluations after the timed region (CUDA events on the "
+                                      "plan's stream, same inputs)"},
         "mesh_roofline": {"bound": "hbm", "achieved": mesh_bytes / (mesh_ms * 1e-3) / 1e9, "peak": hbm,
                           "unit": "GB/s", "frac": mesh_bytes / (mesh_ms * 1e-3) / 1e9 / hbm,
                           "bytes_model": bytes_model, "stages": "fft_forward + m2l + fft_inverse",
                           "peak_kind": peak_kind},
+        "mesh_roofline_64": mesh64,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * esz * n,
                 "d2h_bytes_per_step": 4 * esz * n + 8},
         "gpu_launches": launches * args.steps,
@@ -693,7 +799,8 @@ def run_ours_batched(args, rank, world, local_rank):
     pairs = sum(_pairs(cs[s_ * K:(s_ + 1) * K + 1] - cs[s_ * K], mesh, True) for s_ in range(nsys))
     C, CG, Kh = plan.info(pk.INFO_C), plan.info(pk.INFO_CG), plan.info(pk.INFO_KH)
     hbm, sm_max, peak_kind = _peaks()
-    alu_peak = 2.0 * FP32_LANES_PER_SM * NUM_SMS * sm_max * 1e6 / 1e12
+    alu_meas, alu_probes = _probe_alu(pk)
+    alu_peak = alu_meas / 1e12
     pp_ms = stage.get("near_field", float("nan"))
     pp_tf = PP_FLOPS_PER_PAIR * pairs / (pp_ms * 1e-3) / 1e12
     mesh_ms = sum(stage.get(k, 0.0) for k in ("fft_forward", "m2l", "fft_inverse"))
@@ -717,7 +824,7 @@ def run_ours_batched(args, rank, world, local_rank):
         import oracle
         s0 = int(np.argmin(counts))
         a, b = int(off[s0]), int(off[s0 + 1])
-        cells = synth.rng(98).choice(K, size=4, replace=False)
+        cells = synth.rng(98).choice(K, size=32, replace=False)
         r = oracle.pmmm(pos64[a:b], q64[a:b], (0, 0, 0), (1, 1, 1), (mesh,) * 3, p, 1, True, target_cells=cells,
                         green=green)
         sel = ~np.isnan(r["phi"])
@@ -738,7 +845,8 @@ def run_ours_batched(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "kernel": "near field (pp_kernel)", "achieved": pp_tf,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": pp_tf / alu_peak, "traffic": None,
                      "per_launch": f"{pairs} pair interactions x {PP_FLOPS_PER_PAIR} flop",
-                     "peak_basis": f"{NUM_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"},
+                     "peak_basis": "measured FP32 FMA rate (pmmm_probe_peak, larger of scalar and packed f32x2 "
+                                   "FMA chains, CUDA events)", "peak_probes": alu_probes},
         "mesh_roofline": {"bound": "hbm", "achieved": mesh_bytes / (mesh_ms * 1e-3) / 1e9, "peak": hbm,
                           "unit": "GB/s", "frac": mesh_bytes / (mesh_ms * 1e-3) / 1e9 / hbm,
                           "stages": "fft_forward + m2l + fft_inverse", "peak_kind": peak_kind,
@@ -886,13 +994,15 @@ def run_ours_surrogate(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCHED) + sorted(SURROGATE),
                     default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-mesh64", action="store_true",
+                    help="skip the 2^24-particle 64^3 mesh-stage measurement of the default workload")
     ap.add_argument("--near-field", choices=["auto", "items", "target"], default="auto",
                     help="near-field kernel: automatic by cell occupancy, cell items, or one thread per target")
     args = ap.parse_args()

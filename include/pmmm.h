@@ -247,7 +247,19 @@ enum {
   PMMM_INFO_SYSTEMS = 8,
   PMMM_INFO_TUNED_NEAR = 9, /* near-field kernel chosen by pmmm_plan_autotune (0: none, from the config) */
   PMMM_INFO_M2L_TILE = 10,  /* systems per CTA of the tensor-core batched M2L (32 or 64; default 64) */
-  PMMM_INFO_REFINE = 11     /* refinement of a two-level plan (1: one level) */
+  PMMM_INFO_REFINE = 11,    /* refinement of a two-level plan (1: one level) */
+  PMMM_INFO_M2L_ARITH = 12  /* arithmetic of the last compute's M2L: PMMM_M2L_ARITH_* (-1 before any) */
+};
+/* The M2L arithmetic that actually ran.  PMMM_FP32_SPLITBF16_M2L asks for the
+ * tensor cores, but they serve only where the per-wavevector M2L is a true matrix
+ * product: batched evaluations of more than one system, and the fine-level block
+ * M2L of two-level plans, both for p <= 7.  A single one-level system (each
+ * wavevector its own matrix-vector product) and p > 7 run the FP32 SIMT M2L;
+ * this key says which one a compute used. */
+enum {
+  PMMM_M2L_ARITH_FP64_SIMT = 0,
+  PMMM_M2L_ARITH_FP32_SIMT = 1,
+  PMMM_M2L_ARITH_SPLITBF16_TC = 2
 };
 int pmmm_plan_info(pmmm_plan* plan, int what, int64_t* value);
 
@@ -273,17 +285,19 @@ const char* pmmm_stage_name(int i);
 
 /* Binning and stable sort by cell WITHOUT ANY DEVICE ALLOCATION.  The paper has
  * no counterpart: this is a service for callers that cannot call cudaMalloc --
- * code running inside a CUDA-graph capture that must not allocate, under a
- * memory pool or framework that owns all device memory, or in a loop that must
- * never block in the allocator.  It computes the first step of pmmm_compute
+ * a host framework or memory pool that owns all device memory and forbids
+ * allocations behind its back, or a real-time loop that must never block in the
+ * allocator (cudaMalloc may synchronise the device and take an unbounded
+ * time).  It computes the first step of pmmm_compute
  * (same FP64 cell-index formula, same stable order) for the geometry of cfg
  * (box, mesh, boundary, precision; p and cutoff are ignored):
  *   n           number of particles, 0 <= n <= PMMM_STATIC_SORT_MAX_N
  *   pos         device, n x 3 positions (double for PMMM_FP64, float otherwise)
  *   perm        device int32[n] output: original index of each sorted slot
  *   cell_start  device int32[K+1] output: first sorted slot of each cell, [K] = n
- *   cuda_stream cudaStream_t or NULL; the call synchronises it and returns the
- *               device-side status (PMMM_ERR_OUT_OF_BOX / _NONFINITE_INPUT as in
+ *   cuda_stream cudaStream_t or NULL; every call waits for this stream to
+ *               finish (it reads the device-side status back) and returns that
+ *               status (PMMM_ERR_OUT_OF_BOX / _NONFINITE_INPUT as in
  *               pmmm_compute).
  * All scratch lives in one file-scope device array of about 3 MiB that every
  * GPU loading this library keeps until the process exits; n above
@@ -367,6 +381,16 @@ int pmmm_surrogate_train_step(pmmm_surrogate* s, const void* X, const float* T, 
  * method in fallback); arguments as pmmm_compute. */
 int pmmm_surrogate_compute(pmmm_surrogate* s, int64_t n, const void* pos, const void* q, void* phi, void* force,
                            double* energy);
+
+/* Peak probes (measurement, the paper has no counterpart): the FMA rate of this
+ * GPU, measured by a kernel of independent FMA chains (eight per thread, eight
+ * resident blocks of 256 threads on every SM) timed with CUDA events, best of
+ * five launches after a warm-up.  what: PMMM_PROBE_FP32_FMA (fma.rn.f32),
+ * PMMM_PROBE_FP32X2_FMA (packed fma.rn.f32x2, two lanes per instruction) or
+ * PMMM_PROBE_FP64_FMA.  *flops_per_s receives 2 x FMAs per second.  Allocates
+ * and frees one small device buffer; synchronises the stream. */
+enum { PMMM_PROBE_FP32_FMA = 0, PMMM_PROBE_FP32X2_FMA = 1, PMMM_PROBE_FP64_FMA = 2 };
+int pmmm_probe_peak(int what, void* cuda_stream, double* flops_per_s);
 
 /* Diagnostic of the failure detection (the paper has no counterpart): launches
  * one kernel that waits, with the same bounded mbarrier wait as the

@@ -75,6 +75,7 @@ def _L():
                 "orc_l2p_phi": (d, [i32, vp, vp]),
                 "orc_direct": (None, [i64, vp, vp, i64, vp, vp, vp]),
                 "orc_ewald": (None, [i64, vp, vp, vp, d, d, d, i64, vp, vp, vp]),
+                "orc_ewald_targets": (i32, [i64, vp, vp, vp, d, d, d, i64, vp, vp, vp]),
                 "orc_bin": (i32, [i64, vp, vp, vp, vp, i32, vp, vp, vp, vp]),
                 "orc_green_open": (None, [i32, i32, vp, vp, vp]),
                 "orc_green_periodic": (None, [i32, i32, vp, vp, d, i32, vp, vp]),
@@ -255,6 +256,30 @@ def ewald(pos, q, box, alpha=None, rcut=None, kmax=None, targets=None, tol: floa
     g = np.zeros((nt, 3))
     _L().orc_ewald(pos.shape[0], _p(pos), _p(q), _p(box), float(alpha), float(rcut), float(kmax), nt, _p(t),
                    _p(phi), _p(g))
+    return phi, g
+
+
+def ewald_targets(pos, q, box, targets, tol: float = 1e-9, rcut: float | None = None, alpha=None, kmax=None):
+    """The Ewald sum of Eq. refewald for a few targets among many sources: (phi, grad)
+    of the listed targets.  The same sum as ewald(); the real-space part visits only
+    cells of side >= rcut around each target and the structure factors use products
+    of per-axis phase factors, which keeps N = 2^20 sources affordable.  By default
+    rcut = 0.3 b_min, alpha and kmax from tol as in ewald_params."""
+    pos = _f64(pos).reshape(-1, 3)
+    q = _f64(q).reshape(-1)
+    box = _f64(box, (3,))
+    t = np.ascontiguousarray(targets, dtype=np.int64)
+    if alpha is None:
+        s = math.sqrt(-math.log(tol)) + 0.5
+        rcut = 0.3 * float(min(box)) if rcut is None else float(rcut)
+        alpha = s / rcut
+        kmax = s * alpha * float(max(box)) / math.pi
+    phi = np.zeros(t.shape[0])
+    g = np.zeros((t.shape[0], 3))
+    st = _L().orc_ewald_targets(pos.shape[0], _p(pos), _p(q), _p(box), float(alpha), float(rcut), float(kmax),
+                                t.shape[0], _p(t), _p(phi), _p(g))
+    if st != 0:
+        raise ValueError("ewald_targets needs rcut <= 3b/7 on every axis")
     return phi, g
 
 

@@ -54,7 +54,7 @@
 
 typedef double complex cplx;
 
-#define ORC_VERSION 4
+#define ORC_VERSION 5
 #define LMAX_ORACLE 48
 
 static inline int hidx(int l, int m) { return l * l + l + m; }
@@ -476,6 +476,183 @@ void orc_ewald(int64_t n, const double *pos, const double *q, const double *box,
     }
     free(kv);
     free(Sk);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same Ewald sum (Eq. refewald, same readings and truncations as        */
+/* orc_ewald) for a few targets among many sources, organised so that      */
+/* N = 2^20 sources stay affordable:                                        */
+/*   real space: the sources are listed by cells of side >= rcut/3 (at     */
+/*     least seven per axis, rcut <= 3b/7 on every axis), so a target visits */
+/*     the 7^3 cells around its own; rcut < b/2 makes the minimum image the */
+/*     only image within rcut;                                              */
+/*   reciprocal: exp(2 pi i k.r_j) = ex^kx ey^ky ez^kz with ex = exp(2 pi i */
+/*     x_j/b_x) etc., the powers taken by repeated multiplication per source */
+/*     (exponential of a sum = product of exponentials); structure factors  */
+/*     accumulated per thread, then summed.                                 */
+/* Returns 0, or -1 when rcut > 3b/7 on some axis.                          */
+/* ------------------------------------------------------------------------ */
+int orc_ewald_targets(int64_t n, const double *pos, const double *q, const double *box, double alpha, double rcut,
+                      double kmax, int64_t nt, const int64_t *targets, double *phi, double *grad)
+{
+    const double V = box[0] * box[1] * box[2];
+    const double sqpi = sqrt(M_PI);
+    int nc[3];
+    for (int a = 0; a < 3; ++a) {
+        nc[a] = (int)floor(3.0 * box[a] / rcut);
+        if (nc[a] < 7) return -1;
+    }
+    double Q = 0;
+    for (int64_t j = 0; j < n; ++j) Q += q[j];
+
+    /* cell list: counting sort of the sources by cell (positions wrapped into the box) */
+    const int64_t NC = (int64_t)nc[0] * nc[1] * nc[2];
+    int64_t *cstart = (int64_t *)calloc(NC + 1, sizeof(int64_t));
+    int64_t *cidx = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    int64_t *fill = (int64_t *)calloc(NC, sizeof(int64_t));
+    int64_t *cellof = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    for (int64_t j = 0; j < n; ++j) {
+        int c3[3];
+        for (int a = 0; a < 3; ++a) {
+            double x = pos[3 * j + a] - box[a] * floor(pos[3 * j + a] / box[a]);
+            int ia = (int)floor(x / box[a] * nc[a]);
+            if (ia < 0) ia = 0;
+            if (ia >= nc[a]) ia = nc[a] - 1;
+            c3[a] = ia;
+        }
+        cellof[j] = c3[0] + (int64_t)nc[0] * (c3[1] + (int64_t)nc[1] * c3[2]);
+        cstart[cellof[j] + 1]++;
+    }
+    for (int64_t c = 0; c < NC; ++c) cstart[c + 1] += cstart[c];
+    for (int64_t j = 0; j < n; ++j) cidx[cstart[cellof[j]] + fill[cellof[j]]++] = j;
+    /* sources copied in cell order, so that a cell's sources are read contiguously */
+    double *spos = (double *)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    double *sq = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    for (int64_t u = 0; u < n; ++u) {
+        for (int a = 0; a < 3; ++a) spos[3 * u + a] = pos[3 * cidx[u] + a];
+        sq[u] = q[cidx[u]];
+    }
+
+    /* reciprocal vectors in the half space, as in orc_ewald */
+    int km = (int)floor(kmax);
+    int64_t nk = 0;
+    for (int a = -km; a <= km; ++a)
+        for (int b = -km; b <= km; ++b)
+            for (int c = -km; c <= km; ++c) {
+                if (a * a + b * b + c * c == 0 || a * a + b * b + c * c > kmax * kmax) continue;
+                if (a > 0 || (a == 0 && (b > 0 || (b == 0 && c > 0)))) nk++;
+            }
+    int *kv = (int *)malloc(sizeof(int) * 3 * (nk > 0 ? nk : 1));
+    cplx *Sk = (cplx *)calloc(nk > 0 ? nk : 1, sizeof(cplx));
+    nk = 0;
+    for (int a = -km; a <= km; ++a)
+        for (int b = -km; b <= km; ++b)
+            for (int c = -km; c <= km; ++c) {
+                if (a * a + b * b + c * c == 0 || a * a + b * b + c * c > kmax * kmax) continue;
+                if (a > 0 || (a == 0 && (b > 0 || (b == 0 && c > 0)))) {
+                    kv[3 * nk] = a;
+                    kv[3 * nk + 1] = b;
+                    kv[3 * nk + 2] = c;
+                    nk++;
+                }
+            }
+    /* structure factors S(k) = sum_j q_j exp(2 pi i k . r_j), sources taken in
+     * blocks of SB (their phase factors ep[j][axis][m] = exp(2 pi i m x/b), m in
+     * [-km, km]); kv lists the vectors with kx, then ky, then kz increasing, so
+     * q_j ex^kx ey^ky is formed once per (kx, ky) run */
+    enum { SB = 256 };
+    const int W = 2 * km + 1;
+#pragma omp parallel
+    {
+        cplx *Sl = (cplx *)calloc(nk > 0 ? nk : 1, sizeof(cplx));
+        cplx *ep = (cplx *)malloc(sizeof(cplx) * SB * 3 * W);
+#pragma omp for schedule(static)
+        for (int64_t j0 = 0; j0 < n; j0 += SB) {
+            const int nb = (int)(n - j0 < SB ? n - j0 : SB);
+            for (int jj = 0; jj < nb; ++jj)
+                for (int a = 0; a < 3; ++a) {
+                    cplx *e = ep + ((int64_t)jj * 3 + a) * W;
+                    double ph = 2.0 * M_PI * pos[3 * (j0 + jj) + a] / box[a];
+                    cplx w = cos(ph) + I * sin(ph);
+                    e[km] = 1.0;
+                    for (int m = 1; m <= km; ++m) {
+                        e[km + m] = e[km + m - 1] * w;
+                        e[km - m] = conj(e[km + m]);
+                    }
+                }
+            int64_t t = 0;
+            while (t < nk) {
+                const int a = kv[3 * t], b = kv[3 * t + 1];
+                int64_t t1 = t;
+                while (t1 < nk && kv[3 * t1] == a && kv[3 * t1 + 1] == b) ++t1;
+                for (int jj = 0; jj < nb; ++jj) {
+                    const cplx *e = ep + (int64_t)jj * 3 * W;
+                    const cplx qxy = q[j0 + jj] * (e[km + a] * e[W + km + b]);
+                    for (int64_t u = t; u < t1; ++u) Sl[u] += qxy * e[2 * W + km + kv[3 * u + 2]];
+                }
+                t = t1;
+            }
+        }
+#pragma omp critical
+        for (int64_t t = 0; t < nk; ++t) Sk[t] += Sl[t];
+        free(ep);
+        free(Sl);
+    }
+
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t t = 0; t < nt; ++t) {
+        int64_t i = targets ? targets[t] : t;
+        const double *ri = pos + 3 * i;
+        double f = 0, g[3] = {0, 0, 0};
+        int ci[3];
+        for (int a = 0; a < 3; ++a) {
+            double x = ri[a] - box[a] * floor(ri[a] / box[a]);
+            ci[a] = (int)floor(x / box[a] * nc[a]);
+            if (ci[a] < 0) ci[a] = 0;
+            if (ci[a] >= nc[a]) ci[a] = nc[a] - 1;
+        }
+        for (int dz = -3; dz <= 3; ++dz)
+            for (int dy = -3; dy <= 3; ++dy)
+                for (int dx = -3; dx <= 3; ++dx) {
+                    int cx = (ci[0] + dx + nc[0]) % nc[0], cy = (ci[1] + dy + nc[1]) % nc[1],
+                        cz = (ci[2] + dz + nc[2]) % nc[2];
+                    int64_t c = cx + (int64_t)nc[0] * (cy + (int64_t)nc[1] * cz);
+                    for (int64_t u = cstart[c]; u < cstart[c + 1]; ++u) {
+                        const double *rj = spos + 3 * u;
+                        double d[3] = {ri[0] - rj[0], ri[1] - rj[1], ri[2] - rj[2]};
+                        for (int a = 0; a < 3; ++a) d[a] -= box[a] * floor(d[a] / box[a] + 0.5);
+                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        if (r2 >= rcut * rcut) continue;
+                        if (r2 == 0.0) continue; /* j == i */
+                        double r = sqrt(r2);
+                        double ec = erfc(alpha * r);
+                        f += sq[u] * ec / r;
+                        double dr = -(ec / r2 + 2.0 * alpha / sqpi * exp(-alpha * alpha * r2) / r) / r;
+                        for (int a = 0; a < 3; ++a) g[a] += sq[u] * dr * d[a];
+                    }
+                }
+        for (int64_t s = 0; s < nk; ++s) {
+            double k[3] = {kv[3 * s] / box[0], kv[3 * s + 1] / box[1], kv[3 * s + 2] / box[2]};
+            double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+            double coef = exp(-M_PI * M_PI * k2 / (alpha * alpha)) / (M_PI * V * k2);
+            double ph = 2.0 * M_PI * (k[0] * ri[0] + k[1] * ri[1] + k[2] * ri[2]);
+            cplx z = (cos(ph) + I * sin(ph)) * conj(Sk[s]);
+            f += 2.0 * coef * creal(z);
+            for (int a = 0; a < 3; ++a) g[a] += 2.0 * coef * (-2.0 * M_PI * k[a]) * cimag(z);
+        }
+        f += -2.0 * alpha / sqpi * q[i] - M_PI / (V * alpha * alpha) * Q;
+        phi[t] = f;
+        for (int a = 0; a < 3; ++a) grad[3 * t + a] = g[a];
+    }
+    free(kv);
+    free(Sk);
+    free(cstart);
+    free(cidx);
+    free(fill);
+    free(cellof);
+    free(spos);
+    free(sq);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */

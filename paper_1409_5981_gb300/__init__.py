@@ -27,7 +27,8 @@ EXPORT_PERM, EXPORT_SORTED_CELL, EXPORT_CELL_START = 1, 2, 3
 EXPORT_MULTIPOLE, EXPORT_LOCAL, EXPORT_CORR, EXPORT_FAR = 4, 5, 6, 7
 INFO_K, INFO_C, INFO_CG, INFO_KH, INFO_N, INFO_WORKSPACE_BYTES, INFO_LAUNCHES = 1, 2, 3, 4, 5, 6, 7
 INFO_SYSTEMS = 8
-INFO_TUNED_NEAR, INFO_M2L_TILE, INFO_REFINE = 9, 10, 11
+INFO_TUNED_NEAR, INFO_M2L_TILE, INFO_REFINE, INFO_M2L_ARITH = 9, 10, 11, 12
+M2L_ARITH_FP64_SIMT, M2L_ARITH_FP32_SIMT, M2L_ARITH_SPLITBF16_TC = 0, 1, 2
 MAX_SYSTEMS = 65535
 SUR_PARAMS, SUR_ADAM_M, SUR_ADAM_V, SUR_IN_SCALE, SUR_OUT_SCALE = 1, 2, 3, 4, 5
 SUR_INFO_STEP, SUR_INFO_FALLBACK, SUR_INFO_CLOW, SUR_INFO_CHIGH, SUR_INFO_ROWS = 1, 2, 3, 4, 5
@@ -108,6 +109,7 @@ _SIGS = {
                                                 ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "pmmm_surrogate_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                  ctypes.c_float, ctypes.POINTER(ctypes.c_double)]),
+    "pmmm_probe_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "pmmm_surrogate_compute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
 }
@@ -144,16 +146,48 @@ STATIC_SORT_MAX_N = 65536
 
 def bin_sort_static(cfg: Config, pos, perm, cell_start, stream=None) -> int:
     """Binning and stable cell sort with no device allocation (pmmm_bin_sort_static):
-    pos (n, 3) CUDA tensor in the precision's dtype; perm int32 (n,) and cell_start
-    int32 (K+1,) CUDA tensors receive the results.  Returns the status code."""
+    pos (n, 3) CUDA tensor in the precision's dtype; perm int32 (>= n elements) and
+    cell_start int32 (>= K+1 elements) CUDA tensors receive the results.  All three
+    must be contiguous and on the current device; anything else raises ValueError
+    before the library is called.  Returns the status code."""
     import torch
+    dt = torch.float64 if int(cfg.precision) == FP64 else torch.float32
+    dev = torch.cuda.current_device()
+    K = int(cfg.mesh[0]) * int(cfg.mesh[1]) * int(cfg.mesh[2])
+    for t, nm in ((pos, "pos"), (perm, "perm"), (cell_start, "cell_start")):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError(f"{nm} must be a contiguous CUDA tensor")
+        if t.device.index != dev:
+            raise ValueError(f"{nm} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+    if pos.dtype != dt:
+        raise ValueError(f"pos must be {dt} for this precision")
+    if pos.dim() != 2 or pos.shape[1] != 3:
+        raise ValueError("pos must have shape (n, 3)")
+    n = int(pos.shape[0])
+    if perm.dtype != torch.int32 or perm.numel() < n:
+        raise ValueError("perm must be an int32 tensor of at least n elements")
+    if cell_start.dtype != torch.int32 or cell_start.numel() < K + 1:
+        raise ValueError("cell_start must be an int32 tensor of at least K + 1 elements")
     c = cfg.to_c()
     if stream is None:
         stream = torch.cuda.current_stream()
-    n = int(pos.shape[0])
     return int(_lib().pmmm_bin_sort_static(ctypes.byref(c), n, ctypes.c_void_p(pos.data_ptr()),
                                            ctypes.c_void_p(perm.data_ptr()), ctypes.c_void_p(cell_start.data_ptr()),
                                            ctypes.c_void_p(stream.cuda_stream)))
+
+
+PROBE_FP32_FMA, PROBE_FP32X2_FMA, PROBE_FP64_FMA = 0, 1, 2
+
+
+def probe_peak(what: int, stream=None) -> float:
+    """pmmm_probe_peak: measured FMA rate of the current GPU in flop/s (2 x FMAs/s)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    v = ctypes.c_double(0.0)
+    _check(_lib().pmmm_probe_peak(int(what), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(v)),
+           "pmmm_probe_peak")
+    return float(v.value)
 
 
 def selftest_wait_timeout(polls: int = 1 << 16, stream=None) -> int:

@@ -15,7 +15,7 @@ OUTDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUTDIR, "libpmmm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["pmmm.cu", "hier.cu", "sort.cu", "p2m_l2p.cu", "fft.cu", "m2l.cu", "green.cu", "pp.cu", "reduce.cu", "static_sort.cu", "batch.cu",
-           "m2l_tc.cu", "fft_fused.cu", "mlp.cu", "surrogate.cu"]
+           "m2l_tc.cu", "fft_fused.cu", "mlp.cu", "surrogate.cu", "probe.cu"]
 HEADERS = ["common.cuh", "harmonics.cuh", "translations.cuh", "fft.cuh", "internal.cuh", "binning.cuh",
            "m2l_table.cuh", "tcgen05.cuh", "plan.cuh"]
 

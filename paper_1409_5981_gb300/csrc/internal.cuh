@@ -43,6 +43,35 @@ struct Geo {
   float loh[3], lol[3], invh[3], invl[3], csf[3];
 };
 
+// The binning geometry of a configuration (box, cells, cell-size units and the
+// float splits of the FP32 binning path).  Plan creation and the allocation-free
+// sort both take it from here, so their cell ids cannot drift apart.  V, alpha
+// and sign are left for the caller.
+inline Geo binning_geo(const pmmm_config& cfg) {
+  Geo g{};
+  for (int a = 0; a < 3; ++a) {
+    g.lo[a] = cfg.box_lo[a];
+    g.len[a] = cfg.box_len[a];
+    g.n[a] = cfg.mesh[a];
+    g.inv[a] = (double)cfg.mesh[a] / cfg.box_len[a];
+    g.h[a] = cfg.box_len[a] / cfg.mesh[a];
+  }
+  g.hs = (g.h[0] == g.h[1] && g.h[1] == g.h[2]) ? g.h[0] : cbrt(g.h[0] * g.h[1] * g.h[2]);
+  g.ihs = 1.0 / g.hs;
+  for (int a = 0; a < 3; ++a) {
+    g.cs[a] = g.h[a] / g.hs;
+    g.hh[a] = 0.5 * g.h[a];
+    g.loh[a] = (float)g.lo[a];
+    g.lol[a] = (float)(g.lo[a] - (double)g.loh[a]);
+    g.invh[a] = (float)g.inv[a];
+    g.invl[a] = (float)(g.inv[a] - (double)g.invh[a]);
+    g.csf[a] = (float)g.cs[a];
+  }
+  g.periodic = cfg.boundary == PMMM_PERIODIC ? 1 : 0;
+  g.c = cfg.cutoff;
+  return g;
+}
+
 enum ErrBits { ERRBIT_OUT_OF_BOX = 1, ERRBIT_NONFINITE = 2, ERRBIT_TIMEOUT = 4 };
 
 // Device error flag helpers

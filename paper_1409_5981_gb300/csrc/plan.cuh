@@ -61,6 +61,7 @@ struct pmmm_plan {
   int* m2l_tab = nullptr;             // batched M2L entry table, 4 ints per entry
   uint32_t* m2l_tab_tc = nullptr;     // packed entry table of the tensor-core M2L
   bool m2l_tc = false;                // batched M2L on the tensor cores (split BF16)
+  int m2l_arith = -1;                 // PMMM_M2L_ARITH_* of the last compute's M2L
   std::unordered_map<void*, size_t> sizes;
   // CUDA graph of one evaluation, and what it was captured for: the systems'
   // offsets, the caller's pointers, the workspace generation and the tuning

@@ -372,6 +372,8 @@ cudaError_t mesh_stage(pmmm_plan* pl, int B, int* nl) {
   if (e != cudaSuccess) return e;
   mark(pl, ST_M2L);
   const int64_t R = (int64_t)pl->C * B;
+  const int simt = fp64 ? PMMM_M2L_ARITH_FP64_SIMT : PMMM_M2L_ARITH_FP32_SIMT;
+  pl->m2l_arith = (B > 1 && pl->m2l_tc) ? PMMM_M2L_ARITH_SPLITBF16_TC : simt;
   if (B == 1) {
     e = launch_m2l(pl->p, fp64, pl->specM, pl->G, pl->specL, pl->d.Kh, s, nl);
   } else if (pl->m2l_tc || m2l_batched_gemm(fp64, pl->p, B)) {
@@ -417,6 +419,8 @@ cudaError_t hier_stage(pmmm_plan* pl, int* nl) {
   if (e == cudaSuccess) e = launch_hier_forward(h, pl->C, fp64, pl->M, pl->hspecM, bp->twx, s, nl);
   if (e != cudaSuccess) return e;
   mark(pl, ST_M2L);
+  pl->m2l_arith = (h.wavemajor && pl->m2l_tc) ? PMMM_M2L_ARITH_SPLITBF16_TC
+                                              : (fp64 ? PMMM_M2L_ARITH_FP64_SIMT : PMMM_M2L_ARITH_FP32_SIMT);
   if (!h.wavemajor)
     e = launch_m2l_systems(pl->p, fp64, pl->hspecM, bp->G, pl->hspecL, Khh, (int)Kc, s, nl);
   else if (pl->m2l_tc)
@@ -834,32 +838,11 @@ int pmmm_plan_create(const pmmm_config* cfg, void* stream, pmmm_plan** out) {
   d.Kt = (int64_t)d.Lx * d.Ly * d.Lz;
   d.Kh = (int64_t)d.Lz * d.Ly * d.hx;
   Geo& g = pl->g;
-  double hmin = 1e300;
-  for (int a = 0; a < 3; ++a) {
-    g.lo[a] = cfg->box_lo[a];
-    g.len[a] = cfg->box_len[a];
-    g.n[a] = cfg->mesh[a];
-    g.inv[a] = (double)cfg->mesh[a] / cfg->box_len[a];
-    g.h[a] = cfg->box_len[a] / cfg->mesh[a];
-    hmin = fmin(hmin, g.h[a]);
-  }
-  g.hs = (g.h[0] == g.h[1] && g.h[1] == g.h[2]) ? g.h[0] : cbrt(g.h[0] * g.h[1] * g.h[2]);
-  g.ihs = 1.0 / g.hs;
-  for (int a = 0; a < 3; ++a) {
-    g.cs[a] = g.h[a] / g.hs;
-    g.hh[a] = 0.5 * g.h[a];
-    g.loh[a] = (float)g.lo[a];
-    g.lol[a] = (float)(g.lo[a] - (double)g.loh[a]);
-    g.invh[a] = (float)g.inv[a];
-    g.invl[a] = (float)(g.inv[a] - (double)g.invh[a]);
-    g.csf[a] = (float)g.cs[a];
-  }
+  g = binning_geo(*cfg);
   g.V = cfg->box_len[0] * cfg->box_len[1] * cfg->box_len[2];
   g.alpha = cfg->ewald_alpha > 0.0 ? cfg->ewald_alpha
                                    : 1.5 / fmin(cfg->box_len[0], fmin(cfg->box_len[1], cfg->box_len[2]));
   g.sign = cfg->sign;
-  g.periodic = per ? 1 : 0;
-  g.c = cfg->cutoff;
   pl->nmax = cfg->ewald_nmax > 0 ? cfg->ewald_nmax : 5;
 
   const size_t T = pl->tsize;
@@ -1139,6 +1122,7 @@ int pmmm_plan_info(pmmm_plan* pl, int what, int64_t* value) {
     case PMMM_INFO_TUNED_NEAR: *value = pl->tuned_near; break;
     case PMMM_INFO_M2L_TILE: *value = pl->m2l_tile; break;
     case PMMM_INFO_REFINE: *value = pl->hier ? pl->hg.r : 1; break;
+    case PMMM_INFO_M2L_ARITH: *value = pl->m2l_arith; break;
     default: return PMMM_ERR_INVALID_ARG;
   }
   return PMMM_OK;

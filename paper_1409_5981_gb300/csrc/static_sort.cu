@@ -1,23 +1,24 @@
 // pmmm_bin_sort_static: binning and stable sort of the particles by cell, with
 // no device allocation at all.
 //
-// Some callers cannot call cudaMalloc: code that runs where the allocator is
-// off limits (inside a CUDA-graph capture that must not allocate, under a
-// memory pool that forbids growth, in a real-time loop that must never block
-// in the allocator, or in a host framework that owns all device memory).  They
-// still get the first step of the force evaluation -- the cell ids, the stable
-// permutation and the cell offsets -- through this entry point.  Its scratch
-// (key and index double buffers, particle records, radix histograms, the error
-// flag) is one file-scope device array, so the caller only passes the input and
-// output buffers.
+// Some callers cannot call cudaMalloc: a host framework or memory pool that owns
+// all device memory and forbids allocations behind its back, or a real-time
+// loop that must never block in the allocator (cudaMalloc may synchronise the
+// device and take an unbounded time).  They still get the first step of the
+// force evaluation -- the cell ids, the stable permutation and the cell offsets
+// -- through this entry point.  Its scratch (key and index double buffers,
+// particle records, radix histograms, the error flag) is one file-scope device
+// array, so the caller only passes the input and output buffers.
 //
 // The array is resident on every device that loads this library until the
 // process exits.  Its device address is looked up once per device (with that
 // device current) on the first call there; make that first call before any
-// stream capture.  Every call shares the array and it keeps the last call's
-// contents: the error flag is cleared at the start of each call and everything
-// else is fully rewritten before it is read.  Calls that overlap on the GPU
-// (other streams, other host threads) race on the array and must not be made.
+// stream capture.  Every call waits for its stream to finish, because it reads
+// the device-side status back.  Every call shares the array and it keeps the
+// last call's contents: the error flag is cleared at the start of each call and
+// everything else is fully rewritten before it is read.  Calls that overlap on
+// the GPU (other streams, other host threads) race on the array and must not be
+// made.
 #include <mutex>
 
 #include "internal.cuh"
@@ -58,7 +59,8 @@ int scratch_address(void** out) {
   return PMMM_OK;
 }
 
-bool pow2_or_any(int v) { return v >= 1; }
+// any positive cell count per axis (the sort itself has no power-of-two rule)
+bool mesh_dim_ok(int v) { return v >= 1; }
 
 }  // namespace
 
@@ -67,7 +69,7 @@ extern "C" int pmmm_bin_sort_static(const pmmm_config* cfg, int64_t n, const voi
   if (!cfg || n < 0 || !cell_start || (n > 0 && (!pos || !perm))) return PMMM_ERR_INVALID_ARG;
   for (int a = 0; a < 3; ++a) {
     if (!(cfg->box_len[a] > 0.0) || !isfinite(cfg->box_len[a]) || !isfinite(cfg->box_lo[a])) return PMMM_ERR_INVALID_ARG;
-    if (!pow2_or_any(cfg->mesh[a])) return PMMM_ERR_INVALID_ARG;
+    if (!mesh_dim_ok(cfg->mesh[a])) return PMMM_ERR_INVALID_ARG;
   }
   if (cfg->boundary != PMMM_OPEN && cfg->boundary != PMMM_PERIODIC) return PMMM_ERR_INVALID_ARG;
   if (cfg->precision < PMMM_FP64 || cfg->precision > PMMM_FP32_SPLITBF16_M2L) return PMMM_ERR_INVALID_ARG;
@@ -89,27 +91,7 @@ extern "C" int pmmm_bin_sort_static(const pmmm_config* cfg, int64_t n, const voi
   w.cap = kMaxN;
 
   // geometry exactly as a plan derives it (the cell ids depend on lo, len and n / len)
-  Geo g{};
-  for (int a = 0; a < 3; ++a) {
-    g.lo[a] = cfg->box_lo[a];
-    g.len[a] = cfg->box_len[a];
-    g.n[a] = cfg->mesh[a];
-    g.inv[a] = (double)cfg->mesh[a] / cfg->box_len[a];
-    g.h[a] = cfg->box_len[a] / cfg->mesh[a];
-  }
-  g.hs = (g.h[0] == g.h[1] && g.h[1] == g.h[2]) ? g.h[0] : cbrt(g.h[0] * g.h[1] * g.h[2]);
-  g.ihs = 1.0 / g.hs;
-  for (int a = 0; a < 3; ++a) {
-    g.cs[a] = g.h[a] / g.hs;
-    g.hh[a] = 0.5 * g.h[a];
-    g.loh[a] = (float)g.lo[a];
-    g.lol[a] = (float)(g.lo[a] - (double)g.loh[a]);
-    g.invh[a] = (float)g.inv[a];
-    g.invl[a] = (float)(g.inv[a] - (double)g.invh[a]);
-    g.csf[a] = (float)g.cs[a];
-  }
-  g.periodic = cfg->boundary == PMMM_PERIODIC ? 1 : 0;
-  g.c = cfg->cutoff;
+  const Geo g = binning_geo(*cfg);
   const bool fp64 = cfg->precision == PMMM_FP64;
 
   cudaStream_t s = (cudaStream_t)cuda_stream;

@@ -13,12 +13,18 @@ import pytest
 
 import oracle
 import synth
+from parity_util import force_errors, green, sample_cells
 
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
 BATCH_VS_SINGLE_FP64 = 1e-12
 FP32_TOL = {p: 3e-6 * (1 + 0.25 * p) for p in range(0, 13)}
+# relative RMS force / potential error bound of the split-BF16 tensor-core M2L against
+# the FP32 path: each M2L product carries <= 3 * 2^-18 relative error (hi + lo
+# representation of both operands, lo * lo dropped), i.e. ~1.1e-5 per term; the
+# far field is a fraction of each force, so the force error stays below 2e-5
+SPLITBF16_TOL = 2e-5
 
 
 @pytest.fixture(scope="module")
@@ -231,15 +237,77 @@ def test_batched_config4_sampled(pk):
         print(f"config4 system {s} (N={b - a}) batched vs single: force {ef:.2e} phi {ep:.2e}")
         assert ef < FP32_TOL[7] and ep < FP32_TOL[7]
         assert abs(energies[s] - se) < 1e-5 * abs(se)
+    G = green(cfg.box_lo, cfg.box_len, cfg.mesh, cfg.p, cfg.cutoff, True)
     a, b = off[smallest], off[smallest + 1]
-    cells = synth.rng(208).choice(32 ** 3, size=4, replace=False)
+    counts = np.bincount(_cells_of(pos[a:b], cfg), minlength=32 ** 3)
+    cells = sample_cells(counts, cfg.mesh, 208)
     ref = oracle.pmmm(pos[a:b], q[a:b], cfg.box_lo, cfg.box_len, cfg.mesh, cfg.p, cfg.cutoff, True,
-                      target_cells=cells)
+                      target_cells=cells, green=G)
     sel = ~np.isnan(ref["phi"])
-    ef = _rel(force[a:b][sel], -(q[a:b][sel, None] * ref["grad"][sel]))
+    ef, emax, e99 = force_errors(force[a:b][sel], -(q[a:b][sel, None] * ref["grad"][sel]))
     ep = _rel(phi[a:b][sel], ref["phi"][sel])
-    print(f"config4 system {smallest} sampled {sel.sum()} particles vs oracle: force {ef:.2e} phi {ep:.2e}")
+    print(f"config4 system {smallest} sampled {len(cells)} cells, {sel.sum()} particles vs oracle: force rms {ef:.2e} "
+          f"(per particle max {emax:.2e}, p99 {e99:.2e}) phi {ep:.2e}")
     assert ef < FP32_TOL[7] and ep < FP32_TOL[7]
+
+
+def _cells_of(pos, cfg):
+    """Cell id of each particle (for choosing sampled cells only: oracle binning)."""
+    st, cell, *_ = oracle.bin_particles(pos, cfg.box_lo, cfg.box_len, cfg.mesh, cfg.boundary == 1)
+    assert st == 0
+    return cell
+
+
+def test_batched_config4_splitbf16_sampled_vs_oracle(pk):
+    """The benchmarked batched workload with the tensor-core M2L: 64 periodic systems, N
+    log-uniform in [2^14, 2^18], mesh 32^3, p = 7, split BF16 (PMMM_INFO_M2L_ARITH says
+    the tensor cores ran).  The smallest and the largest system against the oracle PMMM
+    on 32 sampled cells each (the four most crowded, eight on the box faces, the rest
+    random), within SPLITBF16_TOL."""
+    import torch
+    sizes = synth.batched_sizes(64, synth.seed(4, 0))
+    cfg = pk.Config(mesh=(32, 32, 32), p=7, boundary=pk.PERIODIC, precision=pk.FP32_SPLITBF16_M2L)
+    pos, q, off = _systems(pk, cfg, sizes, 4)
+    plan, phi, force, energies = _batched(pk, cfg, pos, q, off)
+    assert plan.info(pk.INFO_M2L_ARITH) == pk.M2L_ARITH_SPLITBF16_TC
+    plan.close()
+    G = green(cfg.box_lo, cfg.box_len, cfg.mesh, cfg.p, cfg.cutoff, True)
+    for s_ in (int(np.argmin(sizes)), int(np.argmax(sizes))):
+        a, b = off[s_], off[s_ + 1]
+        counts = np.bincount(_cells_of(pos[a:b], cfg), minlength=32 ** 3)
+        cells = sample_cells(counts, cfg.mesh, 210 + s_)
+        ref = oracle.pmmm(pos[a:b], q[a:b], cfg.box_lo, cfg.box_len, cfg.mesh, cfg.p, cfg.cutoff, True,
+                          target_cells=cells, green=G)
+        sel = ~np.isnan(ref["phi"])
+        ef, emax, e99 = force_errors(force[a:b][sel], -(q[a:b][sel, None] * ref["grad"][sel]))
+        ep = _rel(phi[a:b][sel], ref["phi"][sel])
+        print(f"config4 split-BF16 system {s_} (N={b - a}) sampled {len(cells)} cells, {sel.sum()} particles vs "
+              f"oracle: force rms {ef:.2e} (per particle max {emax:.2e}, p99 {e99:.2e}) phi {ep:.2e}")
+        assert len(cells) == 32 and ef < SPLITBF16_TOL and ep < SPLITBF16_TOL
+
+
+def test_m2l_arithmetic_is_reported(pk):
+    """PMMM_INFO_M2L_ARITH names the M2L that ran: the tensor cores only for batched
+    split-BF16 evaluations with p <= 7; FP32 SIMT for one system or p > 7."""
+    import torch
+    sizes = [900, 1300, 700]
+    for p, prec, batched, want in ((3, pk.FP32_SPLITBF16_M2L, True, pk.M2L_ARITH_SPLITBF16_TC),
+                                   (3, pk.FP32_SPLITBF16_M2L, False, pk.M2L_ARITH_FP32_SIMT),
+                                   (8, pk.FP32_SPLITBF16_M2L, True, pk.M2L_ARITH_FP32_SIMT),
+                                   (3, pk.FP32, True, pk.M2L_ARITH_FP32_SIMT),
+                                   (3, pk.FP64, False, pk.M2L_ARITH_FP64_SIMT)):
+        cfg = pk.Config(mesh=(8, 8, 8), p=p, boundary=pk.PERIODIC, precision=prec, ewald_nmax=3)
+        pos, q, off = _systems(pk, cfg, sizes, 58)
+        dt = _dt(pk, cfg)
+        plan = pk.Plan(cfg)
+        assert plan.info(pk.INFO_M2L_ARITH) == -1
+        if batched:
+            plan.compute_batched(np.diff(off), _t(pos, dt), _t(q, dt))
+        else:
+            plan.compute(_t(pos[: off[1]], dt), _t(q[: off[1]], dt))
+        torch.cuda.synchronize()
+        assert plan.info(pk.INFO_M2L_ARITH) == want, (p, prec, batched)
+        plan.close()
 
 
 def test_batched_graph_replay(pk):
@@ -280,13 +348,6 @@ def test_batched_graph_replay(pk):
     ref.close()
     assert np.array_equal(phi.double().cpu().numpy(), rphi3) and np.array_equal(e3, re3)
     plan.close()
-
-
-# relative RMS force / potential error bound of the split-BF16 tensor-core M2L against
-# the FP32 path: each M2L product carries <= 3 * 2^-18 relative error (hi + lo
-# representation of both operands, lo * lo dropped), i.e. ~1.1e-5 per term; the
-# far field is a fraction of each force, so the force error stays below 2e-5
-SPLITBF16_TOL = 2e-5
 
 
 @pytest.mark.parametrize("p", [2, 5, 7])

@@ -81,3 +81,31 @@ def test_ewald_rectangular_box_dipole_pair():
     a2 = oracle.ewald(pos, q, box, 14.0, 0.5, 14.0 * 6.6 * 2.0 / np.pi)
     assert np.abs(a1[0] - a2[0]).max() < 1e-10
     assert np.abs(a1[1] - a2[1]).max() < 1e-9
+
+
+def test_ewald_targets_equals_ewald():
+    """The target-subset form (cell list, product phase factors) is the same sum as
+    ewald(): equal on every listed target, in a cubic and a rectangular box, with
+    sources outside the primary box (wrapped by the periodicity)."""
+    for box in ((1.0, 1.0, 1.0), (1.0, 1.5, 2.0)):
+        g = synth.rng(24)
+        pos, q = synth.uniform_pm1(700, 25, length=box)
+        pos[:50] += np.round(g.standard_normal((50, 3))) * np.asarray(box)
+        tg = g.choice(700, size=40, replace=False)
+        alpha, rcut = 14.0, 0.3
+        kmax = alpha * 5.1 * max(box) / np.pi
+        ref_phi, ref_g = oracle.ewald(pos, q, box, alpha, rcut, kmax, targets=tg)
+        phi, gr = oracle.ewald_targets(pos, q, box, tg, alpha=alpha, rcut=rcut, kmax=kmax)
+        assert np.abs(phi - ref_phi).max() < 1e-11 * np.abs(ref_phi).max()
+        assert np.abs(gr - ref_g).max() < 1e-10 * np.abs(ref_g).max()
+
+
+def test_ewald_targets_madelung_and_alpha():
+    """Rock salt: -+ M / d at the listed ions, for two splitting parameters."""
+    M = _madelung()
+    pos, q = synth.rock_salt(6)
+    tg = np.array([0, 1, 7, 100, 215])
+    for rc in (0.25, 0.4):
+        phi, gr = oracle.ewald_targets(pos, q, (1, 1, 1), tg, tol=1e-14, rcut=rc)
+        assert np.abs(phi * (1.0 / 6) + q[tg] * M).max() < 1e-11
+        assert np.abs(gr).max() < 1e-9

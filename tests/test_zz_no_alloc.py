@@ -78,3 +78,45 @@ def test_static_sort_limits(pk):
     assert st == pk.OK
     st = pk.bin_sort_static(cfg, pos[:0], perm, cs)
     assert st == pk.OK and int(cs.abs().sum()) == 0
+
+
+def test_static_sort_at_the_limit_matches_regular_path(pk):
+    """n = PMMM_STATIC_SORT_MAX_N fills every region of the static array to its sized
+    bound; a non-cubic mesh of 2048 cells, FP32 and FP64 inputs, two calls in a row."""
+    n = pk.STATIC_SORT_MAX_N
+    for precision, boundary, mesh in ((pk.FP32, pk.PERIODIC, (16, 8, 16)), (pk.FP64, pk.OPEN, (32, 4, 16))):
+        cfg = pk.Config(box_lo=(0.0, -1.0, 0.5), box_len=(2.0, 1.0, 1.5), mesh=mesh, p=1, boundary=boundary,
+                        precision=precision)
+        for rep in range(2):
+            g = synth.rng(9300 + 7 * precision + rep)
+            pos = np.asarray(cfg.box_lo) + g.random((n, 3)) * np.asarray(cfg.box_len)
+            if precision != pk.FP64:
+                pos = pos.astype(np.float32).astype(np.float64)
+            st, perm, cs = _static(pk, cfg, pos)
+            assert st == pk.OK
+            rperm, rcs = _regular(pk, cfg, pos, np.ones(n))
+            assert np.array_equal(perm, rperm)
+            assert np.array_equal(cs, rcs)
+
+
+def test_static_sort_wrapper_rejects_bad_tensors(pk):
+    """The binding checks dtype, shape, sizes, contiguity and device before any launch."""
+    import torch
+    cfg = pk.Config(mesh=(8, 8, 8), p=1, boundary=pk.PERIODIC, precision=pk.FP64)
+    n, K = 1000, 8 ** 3
+    pos = torch.rand((n, 3), dtype=torch.float64, device="cuda")
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    cs = torch.empty(K + 1, dtype=torch.int32, device="cuda")
+    bad = [
+        (pos.float(), perm, cs),                                   # FP32 positions under an FP64 config
+        (pos.reshape(-1)[: 2 * n].reshape(n, 2), perm, cs),       # wrong shape
+        (pos, perm[: n - 1], cs),                                  # short perm
+        (pos, perm.long(), cs),                                    # wrong index type
+        (pos, perm, cs[:K]),                                       # short cell_start
+        (pos.t().contiguous().t(), perm, cs),                      # not contiguous
+        (pos.cpu(), perm, cs),                                     # host tensor
+    ]
+    for a, b, c in bad:
+        with pytest.raises(ValueError):
+            pk.bin_sort_static(cfg, a, b, c)
+    assert pk.bin_sort_static(cfg, pos, perm, cs) == pk.OK
