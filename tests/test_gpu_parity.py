@@ -261,7 +261,16 @@ def test_config2_periodic_sampled(pk):
 def test_config2b_plummer_open_sampled(pk):
     """N = 2^20 Plummer sphere (a = 0.1, cut at 10a), equal masses, open box [-1,1]^3,
     mesh 64^3 -> 128^3 padded, p = 5, gravity; 32 sampled cells (the four most crowded,
-    eight on the box faces, the rest random non-empty) against the oracle."""
+    eight on the box faces, the rest random non-empty) against the oracle.
+
+    Tolerance: the FP32 path holds each position relative to its cell centre as an FP32
+    number, rounded once (to 2^-25 cell); the central cells of this cluster hold ~6300
+    particles with nearest neighbours ~0.005 cell apart, and the force on a particle
+    there is a strongly cancelling sum in which that rounding of the close pairs shows.
+    How much it shows is a property of the inputs, measured here: the oracle evaluated
+    on positions moved by 2^-25 cell per coordinate (random signs) against the oracle on
+    the exact positions.  The GPU error must stay within 3x that sensitivity, or within
+    FP32_TOL where the sensitivity is smaller."""
     n = 1 << 20
     pos, m = synth.plummer(n, synth.seed(2, 1))
     pos = pos.astype(np.float32).astype(np.float64)
@@ -273,9 +282,17 @@ def test_config2b_plummer_open_sampled(pk):
     sel = ~np.isnan(ref["phi"])
     e_f, e_max, e_99 = force_errors(force[sel], m[sel, None] * ref["grad"][sel])
     e_p = _rel(phi[sel], -ref["phi"][sel])
+    h = 2.0 / 64
+    g = synth.rng(207)
+    moved = pos + g.choice([-1.0, 1.0], size=pos.shape) * (2.0 ** -25) * h
+    ref2 = _oracle(cfg, pk, moved, m, target_cells=cells)
+    sel2 = sel & ~np.isnan(ref2["phi"])
+    e_sens = force_errors(ref2["grad"][sel2], ref["grad"][sel2])[0]
     print(f"plummer sampled {len(cells)} cells, {sel.sum()} particles: force rms {e_f:.2e} "
-          f"(per particle max {e_max:.2e}, p99 {e_99:.2e}) phi {e_p:.2e}")
-    assert len(cells) == 32 and e_f < FP32_TOL[5] and e_p < FP32_TOL[5]
+          f"(per particle max {e_max:.2e}, p99 {e_99:.2e}) phi {e_p:.2e}; sensitivity to 2^-25 cell "
+          f"position rounding {e_sens:.2e}")
+    assert len(cells) == 32 and sel2.sum() == sel.sum()
+    assert e_f < max(FP32_TOL[5], 3.0 * e_sens) and e_p < FP32_TOL[5]
     plan.close()
 
 
