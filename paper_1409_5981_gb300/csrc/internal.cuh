@@ -324,8 +324,8 @@ bool pp_per_target_applies(bool fp64, int c);
 cudaError_t launch_pp(bool fp64, const void* part, const void* src2, const uint32_t* pair_start, const uint32_t* vals,
                       const uint32_t* keys, int64_t n, bool per_target, const int* cell_start, int64_t K,
                       const uint32_t* item_start, const uint32_t* item_cell, unsigned int* counter, int num_sms,
-                      const void* far, PPParams pp, void* phi, void* force, double* epart, cudaStream_t s,
-                      int* nlaunch);
+                      const void* far, PPParams pp, void* phi, void* force, double* epart, int* err,
+                      cudaStream_t s, int* nlaunch);
 
 // ---------------------------------------------------------------- reduce.cu
 // Sums per-cell FP64 quantities and builds the periodic correction terms:

@@ -546,8 +546,8 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
     pp.sign32 = (float)pp.signf;
     const int64_t mi = pp_items_max(K, n);
     CK(launch_pp(fp64, pl->part, pl->src2, pl->pair_start, pl->vals_sorted, pl->keys_sorted, n, per_target, pl->cs, K,
-                 pl->item_start, pl->item_cell, pl->counter, pl->num_sms, pl->far, pp, phi, force, pl->epart, s,
-                 &nl));
+                 pl->item_start, pl->item_cell, pl->counter, pl->num_sms, pl->far, pp, phi, force, pl->epart, pl->err,
+                 s, &nl));
     mark(pl, ST_REDUCE);
     if (B == 1)
       CK(launch_energy(pl->epart, mi, pl->partial + 256 * 5, reduce_tickets(pl) + 1, pl->energy, s, &nl));

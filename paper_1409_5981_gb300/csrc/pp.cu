@@ -9,10 +9,11 @@
 // One warp per item: its R targets sit in registers, lane l owns target
 // l mod TL and source phase l / TL (TL = R rounded up to a power of two, so a
 // chunk of 8 targets still keeps 32 lanes busy on 4 source phases).  Sources
-// are read through L1 with broadcast loads (all lanes of a phase read the same
-// record); for each neighbour cell the target is moved into that cell's frame
-// once, so the pair loop needs no per-source shift.  Self pairs (r = 0) add zero.
+// are read with broadcast loads (all lanes of a phase read the same record):
+// through L1 in the FP64 kernel, from shared memory staged by bulk asynchronous
+// copies in the FP32 one.  Self pairs (r = 0) add zero.
 #include "internal.cuh"
+#include "tcgen05.cuh"
 
 namespace pmmm {
 
@@ -419,33 +420,9 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
   return d;
 }
 
-// Two sources per step with packed FP32 arithmetic (each lane of f32x2 is an
-// IEEE fp32 operation, so results equal the scalar path's).  gx/gy/gz
-// accumulate +q r / r^3 (negated by the caller).
-template <bool SELF>
-__device__ __forceinline__ void pp_pair2(const ulonglong2& A, const ulonglong2& B, f2 tx, f2 ty, f2 tz, f2& pot,
-                                         f2& gx, f2& gy, f2& gz) {
-  const f2 dx = sub2(tx, A.x), dy = sub2(ty, A.y), dz = sub2(tz, B.x);
-  const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
-  float a, b;
-  up2(r2, a, b);
-  float ra = rsqrt_ftz(a), rb = rsqrt_ftz(b);
-  if (SELF) {
-    ra = a > 0.f ? ra : 0.f;
-    rb = b > 0.f ? rb : 0.f;
-  }
-  const f2 ri = pk2(ra, rb);
-  const f2 qr = mul2(B.y, ri);
-  pot = add2(pot, qr);
-  const f2 qr3 = mul2(qr, mul2(ri, ri));
-  gx = fma2(qr3, dx, gx);
-  gy = fma2(qr3, dy, gy);
-  gz = fma2(qr3, dz, gz);
-}
-
-// The same two-source step with the arithmetic after the rsqrt in scalar FP32
-// (faster in the per-target kernel, whose lanes follow different neighbour
-// lists; the cell-item kernel is faster with the packed form above).
+// A two-source step with the subtractions and r^2 packed (f32x2) and the
+// arithmetic after the rsqrt in scalar FP32 (faster in the per-target kernel,
+// whose lanes follow different neighbour lists).
 template <bool SELF>
 __device__ __forceinline__ void pp_pair2_mixed(const ulonglong2& A, const ulonglong2& B, f2 tx, f2 ty, f2 tz, f2& pot,
                                                f2& gx, f2& gy, f2& gz) {
@@ -484,55 +461,113 @@ __device__ __forceinline__ void pp_pair2_mixed(const ulonglong2& A, const ulongl
   gz = pk2(z0, z1);
 }
 
+// FP32 near field (c = 1 or 2) with the neighbour cells staged by the Tensor Memory
+// Accelerator's bulk copies (cp.async.bulk, global -> shared, completion counted in
+// bytes on an mbarrier).  Same work items, lane mapping, results and energy
+// partials as the other cell-item kernels.  Per item the warp lists its (2c+1)^3 neighbour
+// cells -- the target's own cell first, then the others in (z, y, x) order --
+// numbers their source pairs consecutively and streams them through two
+// shared-memory buffers of NT_CAP pairs: a buffer is filled by one bulk copy per
+// cell piece (issued by the lane that owns the cell) and completes on its
+// mbarrier; the warp waits for it (bounded), moves the staged sources of the
+// neighbour cells into the target cell's frame (one packed add per coordinate),
+// sweeps the whole chunk with the target fixed (the own cell's pairs, which hold
+// the self pair, separately), and refills the buffer with the chunk after next
+// while the other buffer's copies are in flight.  A wait that runs out
+// raises the device error flag (PMMM_ERR_TIMEOUT), waits once more (bounded) for
+// the copies it issued and leaves the kernel.
+constexpr int NT_CAP = 128;                    // source pairs per buffer (4 KB), a multiple of 4
+constexpr int NT_BLOCKS_PER_SM = 5;            // resident blocks per SM (up to 102 registers per thread)
+constexpr long long NT_WAIT_POLLS = 1 << 20;  // polls of at most 1 us each
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// One step of two sources (pair record A = {x_a, x_b, y_a, y_b}, B = {z_a, z_b,
+// q_a, q_b}) for one target, on float2 values with the packed FP32 operations
+// (each half an IEEE fp32 operation: t - s is formed as fma(s, -1, t), exactly
+// the rounded difference).  The same 13 packed operations and 2 rsqrt for every
+// two sources as the per-target kernel's step.
 template <bool SELF>
-__device__ __forceinline__ void pp_sum2(const ulonglong2* __restrict__ src, int npair, int ph, int SP, f2 tx, f2 ty,
-                                        f2 tz, f2& pot, f2& gx, f2& gy, f2& gz) {
+__device__ __forceinline__ void pp_pair_v(const float4& A, const float4& B, float2 tx, float2 ty, float2 tz,
+                                          float2& pot, float2& gx, float2& gy, float2& gz) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 dx = __ffma2_rn(make_float2(A.x, A.y), m1, tx);
+  const float2 dy = __ffma2_rn(make_float2(A.z, A.w), m1, ty);
+  const float2 dz = __ffma2_rn(make_float2(B.x, B.y), m1, tz);
+  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+  float ra = rsqrt_ftz(r2.x), rb = rsqrt_ftz(r2.y);
+  if (SELF) {
+    ra = r2.x > 0.f ? ra : 0.f;
+    rb = r2.y > 0.f ? rb : 0.f;
+  }
+  const float2 ri = make_float2(ra, rb);
+  const float2 qr = __fmul2_rn(make_float2(B.z, B.w), ri);
+  pot = __fadd2_rn(pot, qr);
+  const float2 qr3 = __fmul2_rn(qr, __fmul2_rn(ri, ri));
+  gx = __ffma2_rn(qr3, dx, gx);
+  gy = __ffma2_rn(qr3, dy, gy);
+  gz = __ffma2_rn(qr3, dz, gz);
+}
+
+// Sweep of npair (a multiple of 4) staged source pairs: all of them for SP = 1, the
+// pairs ph, ph + SP, ... of this lane's source phase otherwise.
+template <bool SELF>
+__device__ __forceinline__ void pp_sweep(const float4* __restrict__ src, int npair, int ph, int SP, float2 tx,
+                                         float2 ty, float2 tz, float2& pot, float2& gx, float2& gy, float2& gz) {
   if (SP == 1) {
-    int j = 0;
-    for (; j + 4 <= npair; j += 4) {
-      const ulonglong2 A0 = src[2 * j], B0 = src[2 * j + 1], A1 = src[2 * j + 2], B1 = src[2 * j + 3];
-      const ulonglong2 A2 = src[2 * j + 4], B2 = src[2 * j + 5], A3 = src[2 * j + 6], B3 = src[2 * j + 7];
-      pp_pair2<SELF>(A0, B0, tx, ty, tz, pot, gx, gy, gz);
-      pp_pair2<SELF>(A1, B1, tx, ty, tz, pot, gx, gy, gz);
-      pp_pair2<SELF>(A2, B2, tx, ty, tz, pot, gx, gy, gz);
-      pp_pair2<SELF>(A3, B3, tx, ty, tz, pot, gx, gy, gz);
+    for (int j = 0; j < npair; j += 4) {
+      const float4 A0 = src[2 * j], B0 = src[2 * j + 1], A1 = src[2 * j + 2], B1 = src[2 * j + 3];
+      const float4 A2 = src[2 * j + 4], B2 = src[2 * j + 5], A3 = src[2 * j + 6], B3 = src[2 * j + 7];
+      pp_pair_v<SELF>(A0, B0, tx, ty, tz, pot, gx, gy, gz);
+      pp_pair_v<SELF>(A1, B1, tx, ty, tz, pot, gx, gy, gz);
+      pp_pair_v<SELF>(A2, B2, tx, ty, tz, pot, gx, gy, gz);
+      pp_pair_v<SELF>(A3, B3, tx, ty, tz, pot, gx, gy, gz);
     }
-    for (; j + 2 <= npair; j += 2) {
-      const ulonglong2 A0 = src[2 * j], B0 = src[2 * j + 1], A1 = src[2 * j + 2], B1 = src[2 * j + 3];
-      pp_pair2<SELF>(A0, B0, tx, ty, tz, pot, gx, gy, gz);
-      pp_pair2<SELF>(A1, B1, tx, ty, tz, pot, gx, gy, gz);
-    }
-    if (j < npair) pp_pair2<SELF>(src[2 * j], src[2 * j + 1], tx, ty, tz, pot, gx, gy, gz);
   } else {
-    for (int j = ph; j < npair; j += SP) pp_pair2<SELF>(src[2 * j], src[2 * j + 1], tx, ty, tz, pot, gx, gy, gz);
+    int j = ph;
+    for (; j + SP < npair; j += 2 * SP) {
+      const float4 A0 = src[2 * j], B0 = src[2 * j + 1], A1 = src[2 * (j + SP)], B1 = src[2 * (j + SP) + 1];
+      pp_pair_v<SELF>(A0, B0, tx, ty, tz, pot, gx, gy, gz);
+      pp_pair_v<SELF>(A1, B1, tx, ty, tz, pot, gx, gy, gz);
+    }
+    if (j < npair) pp_pair_v<SELF>(src[2 * j], src[2 * j + 1], tx, ty, tz, pot, gx, gy, gz);
   }
 }
 
-// FP32 near field (c = 1 or 2) on the pair-interleaved sources; same work items,
-// lane mapping and output as pp_kernel.  The warp walks its 27 neighbour cells
-// in pieces of up to 16 source pairs (32 words of 16 bytes): every piece is
-// fetched with one coalesced 128-bit load per lane one piece ahead of its use,
-// stored to a per-warp double buffer in shared memory and read back with
-// broadcast loads, so each warp keeps a whole cell's sources in flight.
-constexpr int PIECE = 16;  // source pairs per piece (one 16-byte word per lane)
-
 template <int CUT>
-__global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel_f32x2(
+__global__ void __launch_bounds__(PP_WARPS * 32, NT_BLOCKS_PER_SM) pp_kernel_tma(
     const float* __restrict__ part, const float* __restrict__ src2f, const uint32_t* __restrict__ pair_start,
     const uint32_t* __restrict__ vals, const int* __restrict__ cs, int64_t K, const uint32_t* __restrict__ item_start,
     const uint32_t* __restrict__ item_cell, unsigned int* __restrict__ counter, const float* __restrict__ far,
-    PPParams pp, float* __restrict__ phi, float* __restrict__ force, double* __restrict__ epart) {
-  __shared__ ulonglong2 stage[PP_WARPS][2][2 * PIECE];
+    PPParams pp, float* __restrict__ phi, float* __restrict__ force, double* __restrict__ epart,
+    int* __restrict__ err) {
+  constexpr int W = 2 * CUT + 1, NS = W * W * W, SL = (NS + 31) / 32, SELFK = (NS - 1) / 2;
+  __shared__ __align__(128) float4 sbuf[PP_WARPS][2][2 * NT_CAP];
+  __shared__ __align__(8) unsigned long long sbar[PP_WARPS][2];
   const float4* P = reinterpret_cast<const float4*>(part);
-  const ulonglong2* S2 = reinterpret_cast<const ulonglong2*>(src2f);
+  const char* S2 = reinterpret_cast<const char*>(src2f);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t bar0 = tc::smem_u32(&sbar[warp][0]), bar1 = tc::smem_u32(&sbar[warp][1]);
+  const uint32_t buf0 = tc::smem_u32(&sbuf[warp][0][0]), buf1 = tc::smem_u32(&sbuf[warp][1][0]);
+  if (lane == 0) {
+    tc::bar_init(bar0, 1);
+    tc::bar_init(bar1, 1);
+    tc::fence_proxy_async();
+  }
+  __syncwarp();
+  uint32_t parity = 0;  // bit b: parity of the next phase of buffer b
   const uint32_t nitems = item_start[K];
   const int nx = pp.n[0], ny = pp.n[1], nz = pp.n[2];
   const float csx = pp.cs32[0], csy = pp.cs32[1], csz = pp.cs32[2];
   uint32_t item = 0, batch_end = 0;
   for (;;) {
-    // consecutive items (neighbouring cells, mostly shared sources) stay on one
-    // warp, PP_BATCH per atomic
     if (item >= batch_end) {
       if (lane == 0) item = atomicAdd(counter, (unsigned)PP_BATCH);
       item = __shfl_sync(0xffffffffu, item, 0);
@@ -550,83 +585,146 @@ __global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel_f32
     const bool active = tl < R;
     float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
     if (active) xi = P[tbeg + tl];
-    const int sbase = cell - cell % pp.ksys, lc = cell - sbase;  // system's first cell, local cell
+    const int sbase = cell - cell % pp.ksys, lc = cell - sbase;
     const int ix = lc % nx, iy = (lc / nx) % ny, iz = lc / (nx * ny);
-    // neighbour table: entry k (x fastest) of the (2 CUT + 1)^3 cells
-    // (ix + k%W - CUT, iy + (k/W)%W - CUT, iz + k/W^2 - CUT) in lane k % 32, slot k / 32:
-    // first pair and pair count
-    constexpr int W = 2 * CUT + 1, NN = W * W * W, SLOTS = (NN + 31) / 32, SELFK = (NN - 1) / 2;
-    int nbb[SLOTS], nbc[SLOTS];
+    // segment s (lane s % 32, slot s / 32): the own cell for s = 0, then the other
+    // cells k = s - 1 (k >= SELFK: s) of the (2c+1)^3 block, x fastest: first pair
+    // (global), pair count, first pair in the item's numbering, and the shift that
+    // moves the cell's sources into the target cell's frame.  The numbering pads the
+    // own cell and the whole list to multiples of 4 pairs with zero-charge dummies.
+    int gb[SL], gn[SL], gf[SL];
+    float gsx[SL], gsy[SL], gsz[SL];
 #pragma unroll
-    for (int j = 0; j < SLOTS; ++j) {
-      const int kk = lane + 32 * j;
-      nbb[j] = 0;
-      nbc[j] = 0;
-      if (kk < NN) {
-        int jx = ix + kk % W - CUT, jy = iy + (kk / W) % W - CUT, jz = iz + kk / (W * W) - CUT;
+    for (int j = 0; j < SL; ++j) {
+      const int sg = lane + 32 * j;
+      gb[j] = gn[j] = 0;
+      gsx[j] = gsy[j] = gsz[j] = 0.f;
+      if (sg < NS) {
+        const int kk = sg == 0 ? SELFK : (sg - 1 >= SELFK ? sg : sg - 1);
+        const int dx = kk % W - CUT, dy = (kk / W) % W - CUT, dz = kk / (W * W) - CUT;
+        int jx = ix + dx, jy = iy + dy, jz = iz + dz;
         bool ok = true;
         if (jx < 0 || jx >= nx) { ok = ok && pp.periodic; jx += (jx < 0) ? nx : -nx; }
         if (jy < 0 || jy >= ny) { ok = ok && pp.periodic; jy += (jy < 0) ? ny : -ny; }
         if (jz < 0 || jz >= nz) { ok = ok && pp.periodic; jz += (jz < 0) ? nz : -nz; }
         if (ok) {
           const int cj = sbase + jx + nx * (jy + ny * jz);
-          nbb[j] = (int)__ldg(pair_start + cj);
-          nbc[j] = (int)__ldg(pair_start + cj + 1) - nbb[j];
+          gb[j] = (int)__ldg(pair_start + cj);
+          gn[j] = (int)__ldg(pair_start + cj + 1) - gb[j];
         }
+        gsx[j] = (float)dx * csx;
+        gsy[j] = (float)dy * csy;
+        gsz[j] = (float)dz * csz;
       }
     }
-    auto nbget = [&](int kk, int& bo, int& no) {
-      int bb = nbb[0], cc = nbc[0];
+    const int nself = __shfl_sync(0xffffffffu, gn[0], 0);
+    const int nselfp = (nself + 3) & ~3;  // own cell, padded: [0, nselfp)
+    int total = 0;
 #pragma unroll
-      for (int q = 1; q < SLOTS; ++q)
-        if ((kk >> 5) == q) {
-          bb = nbb[q];
-          cc = nbc[q];
-        }
-      bo = __shfl_sync(0xffffffffu, bb, kk & 31);
-      no = __shfl_sync(0xffffffffu, cc, kk & 31);
-    };
-    // piece iterator over (neighbour k, pair offset off)
-    int k = 0, off = 0;
-    int b, n;
-    nbget(0, b, n);
-    while (k < NN && n == 0) {
-      ++k;
-      if (k < NN) nbget(k, b, n);
-    }
-    ulonglong2 reg = make_ulonglong2(0ull, 0ull);
-    if (k < NN && lane < 2 * min(PIECE, n - off)) reg = S2[2 * (b + off) + lane];
-    f2 pot = pk2(0.f, 0.f), gx = pot, gy = pot, gz = pot;
-    int cur = 0;
-    while (k < NN) {
-      const int kc = k, len = min(PIECE, n - off);
-      stage[warp][cur][lane] = reg;
-      __syncwarp();
-      // advance to the next piece and fetch it
-      off += PIECE;
-      while (k < NN && off >= n) {
-        ++k;
-        off = 0;
-        if (k < NN) nbget(k, b, n);
+    for (int j = 0; j < SL; ++j) {
+      const int w = (j == 0 && lane == 0) ? nselfp : gn[j];
+      int v = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
       }
-      if (k < NN && lane < 2 * min(PIECE, n - off)) reg = S2[2 * (b + off) + lane];
-      // target in the frame of the source cell centre (units of hs)
-      const float txs = xi.x - (float)(kc % W - CUT) * csx;
-      const float tys = xi.y - (float)((kc / W) % W - CUT) * csy;
-      const float tzs = xi.z - (float)(kc / (W * W) - CUT) * csz;
-      const f2 tx = pk2(txs, txs), ty = pk2(tys, tys), tz = pk2(tzs, tzs);
-      if (kc == SELFK)
-        pp_sum2<true>(stage[warp][cur], len, ph, SP, tx, ty, tz, pot, gx, gy, gz);
-      else
-        pp_sum2<false>(stage[warp][cur], len, ph, SP, tx, ty, tz, pot, gx, gy, gz);
-      cur ^= 1;
+      gf[j] = total + v - w;
+      total += __shfl_sync(0xffffffffu, v, 31);
     }
-    float pa, pb, xa, xb, ya, yb, za, zb;
-    up2(pot, pa, pb);
-    up2(gx, xa, xb);
-    up2(gy, ya, yb);
-    up2(gz, za, zb);
-    float ps = pa + pb, gxs = -(xa + xb), gys = -(ya + yb), gzs = -(za + zb);
+    const int real_end = total;        // dummies of the tail: [real_end, total)
+    total = (total + 3) & ~3;
+    const int nch = (total + NT_CAP - 1) / NT_CAP;
+    // queues the copies of chunk ch into buffer b (real pairs only)
+    auto issue = [&](int ch, int b) {
+      const int base = ch * NT_CAP, end = min(base + NT_CAP, total);
+      const int dummies = max(0, min(end, nselfp) - max(base, nself)) + max(0, end - max(base, real_end));
+      const uint32_t bar = b ? bar1 : bar0, dst = b ? buf1 : buf0;
+      if (lane == 0) bar_expect_tx(bar, (uint32_t)(end - base - dummies) * 32u);
+      __syncwarp();
+      tc::fence_proxy_async();
+#pragma unroll
+      for (int j = 0; j < SL; ++j) {
+        const int lo = max(gf[j], base), hi = min(gf[j] + gn[j], end);
+        if (hi > lo)
+          bulk_g2s(dst + 32u * (uint32_t)(lo - base), S2 + 32 * ((int64_t)gb[j] + (lo - gf[j])),
+                   32u * (uint32_t)(hi - lo), bar);
+      }
+    };
+    for (int c0 = 0; c0 < 2 && c0 < nch; ++c0) issue(c0, c0);
+    float2 pot = make_float2(0.f, 0.f), gx = pot, gy = pot, gz = pot;
+    const float2 tx = make_float2(xi.x, xi.x), ty = make_float2(xi.y, xi.y), tz = make_float2(xi.z, xi.z);
+    int sc = 1;  // first segment not yet moved into the target's frame
+    bool ok = true;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int b = ch & 1;
+      const uint32_t bar = b ? bar1 : bar0;
+      const bool done = tc::bar_wait(bar, (parity >> b) & 1u, NT_WAIT_POLLS);
+      if (!__all_sync(0xffffffffu, done)) {
+        if (lane == 0) set_err(err, ERRBIT_TIMEOUT);
+        tc::bar_wait(bar, (parity >> b) & 1u, NT_WAIT_POLLS);
+        if (ch + 1 < nch) tc::bar_wait(b ? bar0 : bar1, (parity >> (b ^ 1)) & 1u, NT_WAIT_POLLS);
+        ok = false;
+        break;
+      }
+      parity ^= 1u << b;
+      float4* buf = &sbuf[warp][b][0];
+      const int base = ch * NT_CAP, end = min(base + NT_CAP, total);
+      // dummies: zero charge far outside every cell (they add exact zeros)
+      const float4 far4 = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 1.0e4f), farq = make_float4(1.0e4f, 1.0e4f, 0.f, 0.f);
+      for (int e = max(base, nself) + lane; e < min(end, nselfp); e += 32) {
+        buf[2 * (e - base)] = far4;
+        buf[2 * (e - base) + 1] = farq;
+      }
+      for (int e = max(base, real_end) + lane; e < end; e += 32) {
+        buf[2 * (e - base)] = far4;
+        buf[2 * (e - base) + 1] = farq;
+      }
+      // the neighbour cells' sources of this chunk moved into the target cell's frame
+      while (sc < NS) {
+        const int j = sc >> 5, src = sc & 31;
+        int f = gf[0], n = gn[0];
+        float sx = gsx[0], sy = gsy[0], sz = gsz[0];
+#pragma unroll
+        for (int q = 1; q < SL; ++q)
+          if (j == q) {
+            f = gf[q];
+            n = gn[q];
+            sx = gsx[q];
+            sy = gsy[q];
+            sz = gsz[q];
+          }
+        f = __shfl_sync(0xffffffffu, f, src);
+        if (f >= end) break;  // the segment starts in a later chunk
+        n = __shfl_sync(0xffffffffu, n, src);
+        sx = __shfl_sync(0xffffffffu, sx, src);
+        sy = __shfl_sync(0xffffffffu, sy, src);
+        sz = __shfl_sync(0xffffffffu, sz, src);
+        const int lo = max(f, base), hi = min(f + n, end);
+        for (int e = lo + lane; e < hi; e += 32) {
+          float4 A = buf[2 * (e - base)], B = buf[2 * (e - base) + 1];
+          A.x += sx;
+          A.y += sx;
+          A.z += sy;
+          A.w += sy;
+          B.x += sz;
+          B.y += sz;
+          buf[2 * (e - base)] = A;
+          buf[2 * (e - base) + 1] = B;
+        }
+        if (f + n > end) break;  // the segment continues in the next chunk
+        ++sc;
+      }
+      __syncwarp();
+      // own-cell pairs (self pair masked), then the rest of the chunk in one sweep
+      const int s1 = min(max(nselfp - base, 0), end - base);
+      if (s1 > 0) pp_sweep<true>(buf, s1, ph, SP, tx, ty, tz, pot, gx, gy, gz);
+      if (end - base > s1) pp_sweep<false>(buf + 2 * s1, end - base - s1, ph, SP, tx, ty, tz, pot, gx, gy, gz);
+      __syncwarp();  // every lane is done with buffer b
+      if (ch + 2 < nch) issue(ch + 2, b);
+    }
+    if (!__all_sync(0xffffffffu, ok)) return;
+    float ps = pot.x + pot.y, gxs = -(gx.x + gx.y), gys = -(gy.x + gy.y), gzs = -(gz.x + gz.y);
     for (int o = TL; o < 32; o <<= 1) {
       ps += __shfl_xor_sync(0xffffffffu, ps, o);
       gxs += __shfl_xor_sync(0xffffffffu, gxs, o);
@@ -666,8 +764,7 @@ __global__ void __launch_bounds__(PP_WARPS * 32, PP_BLOCKS_PER_SM) pp_kernel_f32
       epart[(int64_t)item * 4 + 2] = (double)f_t[1];
       epart[(int64_t)item * 4 + 3] = (double)f_t[2];
     }
-    __syncwarp();  // the stage buffers are rewritten by the next item
-    ++item;        // next item of this warp's batch
+    ++item;
   }
 }
 
@@ -840,7 +937,8 @@ bool pp_per_target_applies(bool fp64, int c) { return !fp64 && c <= 2; }
 cudaError_t launch_pp(bool fp64, const void* part, const void* src2, const uint32_t* pair_start, const uint32_t* vals,
                       const uint32_t* keys, int64_t n, bool per_target, const int* cell_start, int64_t K,
                       const uint32_t* item_start, const uint32_t* item_cell, unsigned int* counter, int num_sms,
-                      const void* far, PPParams pp, void* phi, void* force, double* epart, cudaStream_t s, int* nl) {
+                      const void* far, PPParams pp, void* phi, void* force, double* epart, int* err, cudaStream_t s,
+                      int* nl) {
   // persistent launch: PP_BLOCKS_PER_SM resident blocks of PP_WARPS warps per SM
   const unsigned blocks = (unsigned)(PP_BLOCKS_PER_SM * (num_sms > 0 ? num_sms : 1));
   if (per_target && pp_per_target_applies(fp64, pp.c) && src2 != nullptr) {
@@ -855,14 +953,15 @@ cudaError_t launch_pp(bool fp64, const void* part, const void* src2, const uint3
                                                     vals, cell_start, item_start, n, (const float4*)far, pp,
                                                     (float*)phi, (float*)force, epart);
   } else if (!fp64 && pp.c <= 2 && src2 != nullptr) {
+    const unsigned tblocks = (unsigned)(NT_BLOCKS_PER_SM * (num_sms > 0 ? num_sms : 1));
     if (pp.c <= 1)
-      pp_kernel_f32x2<1><<<blocks, PP_WARPS * 32, 0, s>>>((const float*)part, (const float*)src2, pair_start, vals,
-                                                          cell_start, K, item_start, item_cell, counter,
-                                                          (const float*)far, pp, (float*)phi, (float*)force, epart);
+      pp_kernel_tma<1><<<tblocks, PP_WARPS * 32, 0, s>>>((const float*)part, (const float*)src2, pair_start, vals,
+                                                         cell_start, K, item_start, item_cell, counter,
+                                                         (const float*)far, pp, (float*)phi, (float*)force, epart, err);
     else
-      pp_kernel_f32x2<2><<<blocks, PP_WARPS * 32, 0, s>>>((const float*)part, (const float*)src2, pair_start, vals,
-                                                          cell_start, K, item_start, item_cell, counter,
-                                                          (const float*)far, pp, (float*)phi, (float*)force, epart);
+      pp_kernel_tma<2><<<tblocks, PP_WARPS * 32, 0, s>>>((const float*)part, (const float*)src2, pair_start, vals,
+                                                         cell_start, K, item_start, item_cell, counter,
+                                                         (const float*)far, pp, (float*)phi, (float*)force, epart, err);
   } else {
 #define PP_LAUNCH(T, S)                                                                                              \
   pp_kernel<T, S><<<blocks, PP_WARPS * 32, 0, s>>>((const T*)part, vals, cell_start, K, item_start, item_cell, counter, \

@@ -103,7 +103,18 @@ def _check_against_single(pk, cfg, sizes, config, wrap=False):
         eu = abs(energies[s] - se) / max(abs(se), 1e-300)
         worst = max(worst, ef, ep)
         assert ef < tol and ep < tol, (s, ef, ep)
-        assert eu < (1e-12 if cfg.precision == pk.FP64 else 1e-5), (s, eu)
+        if cfg.precision == pk.FP64:
+            assert eu < 1e-12, (s, eu)
+        else:
+            # U = 1/2 sum q phi: by Cauchy-Schwarz the energies of two evaluations differ
+            # by at most 1/2 |q| |phi_a - phi_b| (the potentials checked above), plus the
+            # FP32 rounding of the per-item partial sums (~1e-6 of 1/2 sum |q phi|); the
+            # energy of a neutral system cancels strongly, so a relative bound on U alone
+            # would measure that cancellation rather than the arithmetic
+            du = abs(energies[s] - se)
+            bound = 0.5 * np.linalg.norm(q[a:b]) * np.linalg.norm(phi[a:b] - sphi) \
+                + 1e-6 * 0.5 * np.abs(q[a:b] * sphi).sum()
+            assert du <= bound, (s, du, bound, eu)
     print(f"batched vs single ({B} systems, p={cfg.p}, prec={cfg.precision}, bnd={cfg.boundary}): worst {worst:.2e}")
     plan.close()
 
@@ -236,7 +247,10 @@ def test_batched_config4_sampled(pk):
         ef, ep = _rel(force[a:b], sforce), _rel(phi[a:b], sphi)
         print(f"config4 system {s} (N={b - a}) batched vs single: force {ef:.2e} phi {ep:.2e}")
         assert ef < FP32_TOL[7] and ep < FP32_TOL[7]
-        assert abs(energies[s] - se) < 1e-5 * abs(se)
+        # the Cauchy-Schwarz energy bound of _check_against_single
+        bound = 0.5 * np.linalg.norm(q[a:b]) * np.linalg.norm(phi[a:b] - sphi) \
+            + 1e-6 * 0.5 * np.abs(q[a:b] * sphi).sum()
+        assert abs(energies[s] - se) <= bound
     G = green(cfg.box_lo, cfg.box_len, cfg.mesh, cfg.p, cfg.cutoff, True)
     a, b = off[smallest], off[smallest + 1]
     counts = np.bincount(_cells_of(pos[a:b], cfg), minlength=32 ** 3)
