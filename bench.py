@@ -60,6 +60,9 @@ WORKLOADS = {
                                                  "uniform_pm1", 1.0, 1, 4),
     "periodic_hier_n1048576_mesh32_r4_p7_splitbf16": (1 << 20, "periodic", 32, 7, "splitbf16", (0, 0, 0),
                                                       (1, 1, 1), "uniform_pm1", 1.0, 1, 4),
+    # the 64^3 mesh stage with few particles: the ncu profiling case of the large-mesh FFT and M2L kernels
+    "periodic_uniform_n1048576_mesh64_p7_fp32": (1 << 20, "periodic", 64, 7, "fp32", (0, 0, 0), (1, 1, 1),
+                                                  "uniform_pm1", 1.0),
     # same particle density as the default (32 per cell), 8x smaller: the ncu profiling case
     "periodic_uniform_n131072_mesh16_p7_fp32": (1 << 17, "periodic", 16, 7, "fp32", (0, 0, 0), (1, 1, 1),
                                                  "uniform_pm1", 1.0),

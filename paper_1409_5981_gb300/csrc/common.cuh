@@ -34,10 +34,12 @@ template <typename T> PMMM_HD cpx<T> operator*(T s, cpx<T> a) { return mk(s * a.
 template <typename T> PMMM_HD cpx<T> conjg(cpx<T> a) { return mk(a.x, -a.y); }
 // multiply by +i (s = +1) or -i (s = -1)
 template <typename T> PMMM_HD cpx<T> mul_si(cpx<T> a, int s) { return s > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x); }
-// a += b * c
+// a += b * c as four fused multiply-adds into the accumulator (one rounding each)
 template <typename T> PMMM_HD void cmac(cpx<T>& a, cpx<T> b, cpx<T> c) {
-  a.x += b.x * c.x - b.y * c.y;
-  a.y += b.x * c.y + b.y * c.x;
+  a.x = fma(b.x, c.x, a.x);
+  a.x = fma(-b.y, c.y, a.x);
+  a.y = fma(b.x, c.y, a.y);
+  a.y = fma(b.y, c.x, a.y);
 }
 
 // Real storage index of App. A.7: X[l(l+1)+m] = Re X_l^|m| (m >= 0), Im X_l^|m| (m < 0).

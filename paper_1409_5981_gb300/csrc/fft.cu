@@ -168,6 +168,204 @@ __global__ void __launch_bounds__(FFT_THREADS) cols_kernel(cpx<T>* __restrict__ 
   }
 }
 
+// Forward x and y passes of one plane (c, z < nz) in one block: the real rows
+// y < ny (two per complex transform) -> half-spectrum rows -> columns along y
+// (rows y >= ny zero) -> the plane [Ly][hx] of the spectrum, written contiguously.
+// One read of the moments and one write of the plane replace the separate x and
+// y passes (each a read and a write of the spectrum).  LX, LY > 0: transform
+// lengths known at compile time (indices fold; twiddles staged in shared memory);
+// 0: taken from d.
+template <typename T, int LX, int LY>
+__global__ void __launch_bounds__(FFT_THREADS) plane_fwd_kernel(const T* __restrict__ in, cpx<T>* __restrict__ out,
+                                                                Dims d, FftPlan1D plx, FftPlan1D ply,
+                                                                const cpx<T>* __restrict__ twx,
+                                                                const cpx<T>* __restrict__ twy, int64_t abuf) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* B = A + abuf;
+  const int Lx = LX > 0 ? LX : d.Lx, Ly = LY > 0 ? LY : d.Ly, hx = Lx / 2 + 1;
+  const cpx<T>* tx = twx;
+  const cpx<T>* ty = twy;
+  if constexpr (LX > 0) {
+    cpx<T>* st = B + abuf;
+    for (int t = threadIdx.x; t < LX; t += blockDim.x) st[t] = twx[t];
+    for (int t = threadIdx.x; t < LY; t += blockDim.x) st[LX + t] = twy[t];
+    tx = st;
+    ty = st + LX;
+  }
+  const int64_t c = blockIdx.x / d.nz;
+  const int z = (int)(blockIdx.x - c * d.nz);
+  const int npairs = (d.ny + 1) / 2;
+  const T* src = in + (c * d.nz + z) * (int64_t)d.ny * d.nx;
+  // x pass: row pair pr packs rows 2 pr (real part) and 2 pr + 1 (imaginary part)
+  for (int e = threadIdx.x; e < npairs * Lx; e += blockDim.x) {
+    const int pr = e / Lx, x = e - pr * Lx;
+    const int ya = 2 * pr, yb = ya + 1;
+    T a = T(0), b = T(0);
+    if (x < d.nx) {
+      a = src[(int64_t)ya * d.nx + x];
+      if (yb < d.ny) b = src[(int64_t)yb * d.nx + x];
+    }
+    A[e] = mk(a, b);
+  }
+  __syncthreads();
+  if constexpr (LX > 0)
+    run_stages_ct<T, true, LX, -1>(A, B, npairs, tx);
+  else
+    run_stages<T, true>(A, B, plx, npairs, tx, -1);
+  // half spectra of the rows into B as the plane [Ly][hx] (rows y >= ny zero)
+  for (int e = threadIdx.x; e < Ly * hx; e += blockDim.x) {
+    const int y = e / hx, k = e - y * hx;
+    cpx<T> v = mk(T(0), T(0));
+    if (y < d.ny) {
+      const int pr = y >> 1;
+      const cpx<T> Z = A[pr * Lx + k];
+      const cpx<T> Zm = conjg(A[pr * Lx + ((Lx - k) & (Lx - 1))]);
+      v = (y & 1) ? mk((Z.y - Zm.y) * T(0.5), -(Z.x - Zm.x) * T(0.5)) : mk((Z.x + Zm.x) * T(0.5), (Z.y + Zm.y) * T(0.5));
+    }
+    B[e] = v;
+  }
+  __syncthreads();
+  if constexpr (LY > 0)
+    run_stages_ct<T, false, LY, -1>(B, A, hx, ty);
+  else
+    run_stages<T, false>(B, A, ply, hx, ty, -1);
+  cpx<T>* dst = out + c * d.Kh + (int64_t)z * Ly * hx;
+  for (int e = threadIdx.x; e < Ly * hx; e += blockDim.x) dst[e] = B[e];
+}
+
+// Inverse y and x passes of one plane (c, z < nz): the plane [Ly][hx] of the
+// spectrum -> columns along y (only rows y < ny kept) -> row pairs -> real rows,
+// x < nx written.
+template <typename T, int LX, int LY>
+__global__ void __launch_bounds__(FFT_THREADS) plane_inv_kernel(const cpx<T>* __restrict__ in, T* __restrict__ out,
+                                                                Dims d, FftPlan1D plx, FftPlan1D ply,
+                                                                const cpx<T>* __restrict__ twx,
+                                                                const cpx<T>* __restrict__ twy, int64_t abuf) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* B = A + abuf;
+  const int Lx = LX > 0 ? LX : d.Lx, Ly = LY > 0 ? LY : d.Ly, hx = Lx / 2 + 1, half = Lx / 2;
+  const cpx<T>* tx = twx;
+  const cpx<T>* ty = twy;
+  if constexpr (LX > 0) {
+    cpx<T>* st = B + abuf;
+    for (int t = threadIdx.x; t < LX; t += blockDim.x) st[t] = twx[t];
+    for (int t = threadIdx.x; t < LY; t += blockDim.x) st[LX + t] = twy[t];
+    tx = st;
+    ty = st + LX;
+  }
+  const int64_t c = blockIdx.x / d.nz;
+  const int z = (int)(blockIdx.x - c * d.nz);
+  const int npairs = (d.ny + 1) / 2;
+  const cpx<T>* src = in + c * d.Kh + (int64_t)z * Ly * hx;
+  for (int e = threadIdx.x; e < Ly * hx; e += blockDim.x) A[e] = src[e];
+  __syncthreads();
+  if constexpr (LY > 0)
+    run_stages_ct<T, false, LY, +1>(A, B, hx, ty);
+  else
+    run_stages<T, false>(A, B, ply, hx, ty, +1);
+  // rows y < ny of the plane -> row pairs Z = X + i Y over the full length Lx in B
+  for (int e = threadIdx.x; e < npairs * Lx; e += blockDim.x) {
+    const int pr = e / Lx, k = e - pr * Lx;
+    cpx<T> v[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int y = 2 * pr + q;
+      v[q] = mk(T(0), T(0));
+      if (y < d.ny) {
+        const cpx<T>* row = A + y * hx;
+        if (k <= half) {
+          v[q] = row[k];
+          if (k == 0 || k == half) v[q].y = T(0);
+        } else {
+          v[q] = conjg(row[Lx - k]);
+        }
+      }
+    }
+    B[e] = mk(v[0].x - v[1].y, v[0].y + v[1].x);
+  }
+  __syncthreads();
+  if constexpr (LX > 0)
+    run_stages_ct<T, true, LX, +1>(B, A, npairs, tx);
+  else
+    run_stages<T, true>(B, A, plx, npairs, tx, +1);
+  T* dst = out + (c * d.nz + z) * (int64_t)d.ny * d.nx;
+  for (int e = threadIdx.x; e < d.ny * d.nx; e += blockDim.x) {
+    const int y = e / d.nx, x = e - y * d.nx;
+    const cpx<T> v = B[(y >> 1) * Lx + x];
+    dst[e] = (y & 1) ? v.y : v.x;
+  }
+}
+
+// Shared memory of the plane kernels: two buffers, each the larger of the row
+// pairs (npairs x Lx) and the plane (Ly x hx).
+template <typename T>
+int64_t plane_buf(const Dims& d) {
+  const int64_t a = (int64_t)((d.ny + 1) / 2) * d.Lx, b = (int64_t)d.Ly * d.hx;
+  return a > b ? a : b;
+}
+template <typename T>
+bool plane_applies(const Dims& d) {
+  return (2 * plane_buf<T>(d) + d.Lx + d.Ly) * (int64_t)sizeof(cpx<T>) <= 200 * 1024;
+}
+
+template <typename T, bool FWD, int LX, int LY>
+void launch_plane_l(const void* in, void* out, const Dims& d, int C, const FftTw& tw, cudaStream_t s) {
+  const int64_t ab = plane_buf<T>(d);
+  const size_t smem = (2 * (size_t)ab + (size_t)(LX + LY)) * sizeof(cpx<T>);
+  const unsigned grid = (unsigned)((int64_t)C * d.nz);
+  const FftPlan1D plx = make_fft_plan(d.Lx), ply = make_fft_plan(d.Ly);
+  if constexpr (FWD) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(plane_fwd_kernel<T, LX, LY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    plane_fwd_kernel<T, LX, LY><<<grid, FFT_THREADS, smem, s>>>((const T*)in, (cpx<T>*)out, d, plx, ply,
+                                                                (const cpx<T>*)tw.x, (const cpx<T>*)tw.y, ab);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(plane_inv_kernel<T, LX, LY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    plane_inv_kernel<T, LX, LY><<<grid, FFT_THREADS, smem, s>>>((const cpx<T>*)in, (T*)out, d, plx, ply,
+                                                                (const cpx<T>*)tw.x, (const cpx<T>*)tw.y, ab);
+  }
+}
+
+// Square planes of 32, 64 or 128 points take the compile-time-length kernels.
+template <typename T, bool FWD>
+void launch_plane(const void* in, void* out, const Dims& d, int C, const FftTw& tw, cudaStream_t s) {
+  if (d.Lx == d.Ly && d.Lx == 32) return launch_plane_l<T, FWD, 32, 32>(in, out, d, C, tw, s);
+  if (d.Lx == d.Ly && d.Lx == 64) return launch_plane_l<T, FWD, 64, 64>(in, out, d, C, tw, s);
+  if (d.Lx == d.Ly && d.Lx == 128) return launch_plane_l<T, FWD, 128, 128>(in, out, d, C, tw, s);
+  launch_plane_l<T, FWD, 0, 0>(in, out, d, C, tw, s);
+}
+
+// cols_kernel with the transform length L and the direction SGN known at compile
+// time (twiddles staged in shared memory after the two buffers).
+template <typename T, int L, int SGN>
+__global__ void __launch_bounds__(FFT_THREADS) cols_ct_kernel(cpx<T>* __restrict__ data, int64_t col_stride,
+                                                              int inner, int64_t bstride1, int nb1, int64_t bstride2,
+                                                              int TW, int nin, int nout,
+                                                              const cpx<T>* __restrict__ tw) {
+  extern __shared__ unsigned char smem_raw[];
+  cpx<T>* A = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* B = A + (size_t)L * TW;
+  cpx<T>* st = B + (size_t)L * TW;
+  for (int t = threadIdx.x; t < L; t += blockDim.x) st[t] = tw[t];
+  const int col0 = blockIdx.y * TW;
+  const int b1 = (int)(blockIdx.x % (unsigned)nb1), b2 = (int)(blockIdx.x / (unsigned)nb1);
+  cpx<T>* base = data + (int64_t)b2 * bstride2 + (int64_t)b1 * bstride1 + col0;
+  const int w = min(TW, inner - col0);
+  for (int e = threadIdx.x; e < L * TW; e += blockDim.x) {
+    const int row = e / TW, col = e - row * TW;
+    A[e] = (row < nin && col < w) ? base[row * col_stride + col] : mk(T(0), T(0));
+  }
+  __syncthreads();
+  run_stages_ct<T, false, L, SGN>(A, B, TW, st);
+  for (int e = threadIdx.x; e < L * TW; e += blockDim.x) {
+    const int row = e / TW, col = e - row * TW;
+    if (row < nout && col < w) base[row * col_stride + col] = A[e];
+  }
+}
+
 template <typename T>
 __global__ void twiddle_kernel(int L, cpx<T>* tw) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -197,6 +395,25 @@ cudaError_t cols(cpx<T>* data, int64_t col_stride, int inner, int64_t bs1, int n
   const size_t smem = 2 * (size_t)L * TW * sizeof(cpx<T>);
   // batches on x (up to 2^31 - 1), column tiles on y (inner / TW <= 65535 for L <= 512)
   dim3 grid((unsigned)(nb1 * nb2), (unsigned)((inner + TW - 1) / TW));
+#define PMMM_COLS_CT(LL)                                                                                        \
+  if (L == LL) {                                                                                              \
+    const size_t sm2 = smem + LL * sizeof(cpx<T>);                                                            \
+    if (sgn < 0) {                                                                                            \
+      if (sm2 > 48 * 1024)                                                                                    \
+        cudaFuncSetAttribute(cols_ct_kernel<T, LL, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2); \
+      cols_ct_kernel<T, LL, -1><<<grid, FFT_THREADS, sm2, s>>>(data, col_stride, inner, bs1, nb1, bs2, TW, nin, nout, tw); \
+    } else {                                                                                                  \
+      if (sm2 > 48 * 1024)                                                                                    \
+        cudaFuncSetAttribute(cols_ct_kernel<T, LL, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2); \
+      cols_ct_kernel<T, LL, 1><<<grid, FFT_THREADS, sm2, s>>>(data, col_stride, inner, bs1, nb1, bs2, TW, nin, nout, tw); \
+    }                                                                                                         \
+    return cudaGetLastError();                                                                                \
+  }
+  PMMM_COLS_CT(32)
+  PMMM_COLS_CT(64)
+  PMMM_COLS_CT(128)
+  PMMM_COLS_CT(256)
+#undef PMMM_COLS_CT
   if (smem > 48 * 1024) cudaFuncSetAttribute(cols_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cols_kernel<T><<<grid, FFT_THREADS, smem, s>>>(data, col_stride, inner, bs1, nb1, bs2, TW, nin, nout, sgn, pl, tw);
   return cudaGetLastError();
@@ -204,29 +421,37 @@ cudaError_t cols(cpx<T>* data, int64_t col_stride, int inner, int64_t bs1, int n
 
 template <typename T>
 cudaError_t forward(const T* in, cpx<T>* spec, const Dims& d, int C, const FftTw& tw, cudaStream_t s, int* nl) {
-  // x pass
-  {
-    const FftPlan1D pl = make_fft_plan(d.Lx);
-    const int ppb = pick_ppb(d.Lx);
-    const int64_t nrows = (int64_t)C * d.nz * d.ny;
-    const int64_t npairs = (nrows + 1) / 2;
-    const size_t smem = 2 * (size_t)ppb * d.Lx * sizeof(cpx<T>);
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(r2c_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    r2c_rows_kernel<T><<<(int)((npairs + ppb - 1) / ppb), FFT_THREADS, smem, s>>>(in, spec, d, C, pl,
-                                                                                 (const cpx<T>*)tw.x, ppb);
+  if (plane_applies<T>(d)) {
+    // x and y passes together, one block per plane (c, z < nz)
+    launch_plane<T, true>((const void*)in, (void*)spec, d, C, tw, s);
     ++*nl;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+  } else {
+    // x pass
+    {
+      const FftPlan1D pl = make_fft_plan(d.Lx);
+      const int ppb = pick_ppb(d.Lx);
+      const int64_t nrows = (int64_t)C * d.nz * d.ny;
+      const int64_t npairs = (nrows + 1) / 2;
+      const size_t smem = 2 * (size_t)ppb * d.Lx * sizeof(cpx<T>);
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(r2c_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      r2c_rows_kernel<T><<<(int)((npairs + ppb - 1) / ppb), FFT_THREADS, smem, s>>>(in, spec, d, C, pl,
+                                                                                   (const cpx<T>*)tw.x, ppb);
+      ++*nl;
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    // y pass over (c, z < nz): rows y >= ny are zero
+    cudaError_t e = cols<T>(spec, d.hx, d.hx, (int64_t)d.Ly * d.hx, d.nz, d.Kh, C, d.ny, d.Ly, -1, d.Ly,
+                            (const cpx<T>*)tw.y, s);
+    ++*nl;
+    if (e != cudaSuccess) return e;
   }
-  // y pass over (c, z < nz): rows y >= ny are zero
-  cudaError_t e = cols<T>(spec, d.hx, d.hx, (int64_t)d.Ly * d.hx, d.nz, d.Kh, C, d.ny, d.Ly, -1, d.Ly,
-                          (const cpx<T>*)tw.y, s);
-  ++*nl;
-  if (e != cudaSuccess) return e;
   // z pass over c: planes z >= nz are zero
-  e = cols<T>(spec, (int64_t)d.Ly * d.hx, (int)((int64_t)d.Ly * d.hx), 0, 1, d.Kh, C, d.nz, d.Lz, -1, d.Lz,
-              (const cpx<T>*)tw.z, s);
+  cudaError_t e = cols<T>(spec, (int64_t)d.Ly * d.hx, (int)((int64_t)d.Ly * d.hx), 0, 1, d.Kh, C, d.nz, d.Lz, -1,
+                          d.Lz, (const cpx<T>*)tw.z, s);
   ++*nl;
   return e;
 }
@@ -238,6 +463,12 @@ cudaError_t inverse(cpx<T>* spec, T* out, const Dims& d, int C, const FftTw& tw,
                           d.Lz, (const cpx<T>*)tw.z, s);
   ++*nl;
   if (e != cudaSuccess) return e;
+  if (plane_applies<T>(d)) {
+    // y and x passes together, one block per plane (c, z < nz)
+    launch_plane<T, false>((const void*)spec, (void*)out, d, C, tw, s);
+    ++*nl;
+    return cudaGetLastError();
+  }
   // y pass over (c, z < nz): only rows y < ny needed
   e = cols<T>(spec, d.hx, d.hx, (int64_t)d.Ly * d.hx, d.nz, d.Kh, C, d.Ly, d.ny, +1, d.Ly, (const cpx<T>*)tw.y, s);
   ++*nl;

@@ -106,3 +106,94 @@ PMMM_HD void stockham_bf_any(int R, const cpx<T>* in, cpx<T>* out, int L, int Ns
 }
 
 }  // namespace pmmm
+
+namespace pmmm {
+
+// ---------------------------------------------------------------------------
+// The same Stockham stages with the length, the stage radices and the direction
+// known at compile time (lengths 8 ... 512), so that every index and twiddle
+// step folds into constants.  Radix of stage st of a length-L transform: 8 while
+// the remaining length is a multiple of 8, then 4, then 2 (as make_fft_plan).
+constexpr int ct_radix(int L, int st) {
+  int rem = L, r = 2;
+  for (int i = 0; i <= st; ++i) {
+    r = (rem % 8 == 0) ? 8 : (rem % 4 == 0 ? 4 : 2);
+    rem /= r;
+  }
+  return r;
+}
+constexpr int ct_nstages(int L) {
+  int n = 0, rem = L;
+  while (rem > 1) {
+    rem /= (rem % 8 == 0) ? 8 : (rem % 4 == 0 ? 4 : 2);
+    ++n;
+  }
+  return n;
+}
+constexpr int ct_ns(int L, int st) {
+  int ns = 1;
+  for (int i = 0; i < st; ++i) ns *= ct_radix(L, i);
+  return ns;
+}
+
+// One butterfly of stage (R, NS) of a length-L transform, elements at in[t * es];
+// tw[t] = exp(-2 pi i t / L) (the inverse, SGN = +1, uses the conjugates).
+template <typename T, int L, int R, int NS, int SGN>
+__device__ __forceinline__ void stockham_bf_ct(const cpx<T>* in, cpx<T>* out, int j, int es, const cpx<T>* tw) {
+  constexpr int q = L / R;
+  const int k = j & (NS - 1);
+  cpx<T> v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = in[(j + r * q) * es];
+  if constexpr (NS > 1) {
+    constexpr int step = L / (NS * R);
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      cpx<T> w = tw[r * k * step];
+      if constexpr (SGN > 0) w.y = -w.y;
+      v[r] = v[r] * w;
+    }
+  }
+  if constexpr (R == 2) dft2(v);
+  if constexpr (R == 4) dft4(v, SGN);
+  if constexpr (R == 8) dft8(v, SGN);
+  const int base = (j - k) * R + k;
+#pragma unroll
+  for (int r = 0; r < R; ++r) out[(base + r * NS) * es] = v[r];
+}
+
+// Every stage of `ntrans` length-L transforms held in shared memory (A -> B ->
+// ..., the result ends in A on return, pointers swapped as in run_stages).
+// ROWS: transform tr at A[tr L ...] (stride 1); else element t of transform tr at
+// A[t ntrans + tr].  Block-wide: ends with __syncthreads().
+template <typename T, bool ROWS, int L, int SGN, int ST = 0>
+__device__ __forceinline__ void run_stages_ct(cpx<T>*& A, cpx<T>*& B, int ntrans, const cpx<T>* tw) {
+  if constexpr (ST < ct_nstages(L)) {
+    constexpr int R = ct_radix(L, ST), NS = ct_ns(L, ST), nb = L / R;
+    if constexpr (ROWS) {
+      for (int t = threadIdx.x; t < nb * ntrans; t += blockDim.x) {
+        const int tr = t / nb, j = t % nb;
+        stockham_bf_ct<T, L, R, NS, SGN>(A + tr * L, B + tr * L, j, 1, tw);
+      }
+    } else {
+      // t = j ntrans + tr, walked with an incremental (tr, j) to avoid a division per task
+      const int dq = (int)blockDim.x / ntrans, dr = (int)blockDim.x - dq * ntrans;
+      int tr = (int)threadIdx.x % ntrans, j = (int)threadIdx.x / ntrans;
+      for (; j < nb; j += dq) {
+        stockham_bf_ct<T, L, R, NS, SGN>(A + tr, B + tr, j, ntrans, tw);
+        tr += dr;
+        if (tr >= ntrans) {
+          tr -= ntrans;
+          ++j;
+        }
+      }
+    }
+    __syncthreads();
+    cpx<T>* tmp = A;
+    A = B;
+    B = tmp;
+    run_stages_ct<T, ROWS, L, SGN, ST + 1>(A, B, ntrans, tw);
+  }
+}
+
+}  // namespace pmmm
