@@ -84,7 +84,10 @@ typedef struct pmmm_config {
   int32_t near_field;  /* pmmm_near_field: near-field kernel (results agree to rounding) */
   double sign;         /* +1 Coulomb, -1 gravity */
   double ewald_alpha;  /* periodic splitting parameter; 0 -> 1.5 / min(box_len) (App. B.1 example) */
-  int32_t ewald_nmax;  /* periodic lattice sums over |n|_2 <= nmax (both sums); 0 -> 5 */
+  int32_t ewald_nmax;  /* periodic lattice sums over |n|_2 <= nmax (both sums); 0 -> 5.  The
+                        * M2L uses the parity of the converged kernel; a small nmax leaves an
+                        * asymmetry of about erfc(alpha b nmax) (2e-10 at nmax = 3 with
+                        * alpha b = 1.5, below 1e-25 at 5) */
   int32_t refine;      /* two-level PMMM (Sec. 5, hierarchical treatment): 0 or 1 -> one level;
                         * r = 2, 4, 8 or 16 -> mesh is the fine mesh, every r^3 block of fine cells
                         * one coarse cell (mesh divisible by r; the coarse mesh obeys the mesh rules

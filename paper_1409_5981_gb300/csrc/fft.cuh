@@ -107,6 +107,7 @@ PMMM_HD void stockham_bf_any(int R, const cpx<T>* in, cpx<T>* out, int L, int Ns
 
 }  // namespace pmmm
 
+#if defined(__CUDACC__)
 namespace pmmm {
 
 // ---------------------------------------------------------------------------
@@ -197,3 +198,4 @@ __device__ __forceinline__ void run_stages_ct(cpx<T>*& A, cpx<T>*& B, int ntrans
 }
 
 }  // namespace pmmm
+#endif  // __CUDACC__

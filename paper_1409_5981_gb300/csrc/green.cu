@@ -228,14 +228,46 @@ __global__ void green_recip_table_kernel(double2* __restrict__ rtab, const int4*
 
 template <typename T>
 __global__ void green_finish_kernel(const double2* __restrict__ in, cpx<T>* __restrict__ out, int64_t count,
-                                    double scale) {
+                                    int64_t Kh, double scale) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
+  // the spectrum of a component of order j is real (even j) or imaginary (odd j):
+  // the other part, rounding noise of the transform (or the asymmetry of an
+  // under-converged lattice sum), is set to zero
+  const int s = (int)(i / Kh);
+  int j = 0;
+  while ((j + 1) * (j + 1) <= s) ++j;
   const double2 v = in[i];
-  out[i] = mk((T)(v.x * scale), (T)(v.y * scale));
+  out[i] = (j & 1) ? mk((T)0, (T)(v.y * scale)) : mk((T)(v.x * scale), (T)0);
+}
+
+// The one real number per kernel spectrum value that the parity leaves (component
+// s = sidx(j, a) of order j: the real part for even j, the imaginary part for odd
+// j; the other part vanishes up to rounding), scaled as the complex spectra.
+template <typename T>
+__global__ void green_parity_kernel(const double2* __restrict__ in, T* __restrict__ out, int CG, int64_t Kh,
+                                    double scale) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)CG * Kh) return;
+  const int s = (int)(i / Kh);
+  int j = 0;
+  while ((j + 1) * (j + 1) <= s) ++j;
+  const double2 v = in[i];
+  out[i] = (T)(((j & 1) ? v.y : v.x) * scale);
 }
 
 }  // namespace
+
+cudaError_t launch_green_parity(const void* specd, void* outr, bool fp64, int CG, int64_t Kh, double scale,
+                                cudaStream_t st) {
+  const int64_t count = (int64_t)CG * Kh;
+  const unsigned blocks = (unsigned)((count + 255) / 256);
+  if (fp64)
+    green_parity_kernel<double><<<blocks, 256, 0, st>>>((const double2*)specd, (double*)outr, CG, Kh, scale);
+  else
+    green_parity_kernel<float><<<blocks, 256, 0, st>>>((const double2*)specd, (float*)outr, CG, Kh, scale);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_green_open(double* G, const Dims& d, int p, int c, const double cs[3], cudaStream_t st) {
   green_open_kernel<<<(unsigned)((d.Kt + 127) / 128), 128, 0, st>>>(G, d, 2 * p, c, cs[0], cs[1], cs[2]);
@@ -284,13 +316,13 @@ cudaError_t launch_green_periodic(double* G, const Dims& d, int p, int c, const 
   return e != cudaSuccess ? e : e2;
 }
 
-cudaError_t launch_green_finish(const void* specd, void* out, bool fp64, int64_t count, double scale,
+cudaError_t launch_green_finish(const void* specd, void* out, bool fp64, int64_t count, int64_t Kh, double scale,
                                 cudaStream_t st) {
   const unsigned blocks = (unsigned)((count + 255) / 256);
   if (fp64)
-    green_finish_kernel<double><<<blocks, 256, 0, st>>>((const double2*)specd, (cpx<double>*)out, count, scale);
+    green_finish_kernel<double><<<blocks, 256, 0, st>>>((const double2*)specd, (cpx<double>*)out, count, Kh, scale);
   else
-    green_finish_kernel<float><<<blocks, 256, 0, st>>>((const double2*)specd, (cpx<float>*)out, count, scale);
+    green_finish_kernel<float><<<blocks, 256, 0, st>>>((const double2*)specd, (cpx<float>*)out, count, Kh, scale);
   return cudaGetLastError();
 }
 

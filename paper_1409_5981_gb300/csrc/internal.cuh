@@ -190,10 +190,12 @@ cudaError_t launch_fft_fused_inverse(const void* spec, void* out, const Dims& d,
                                      int* nlaunch);
 
 // ---------------------------------------------------------------- m2l.cu
-cudaError_t launch_m2l(int p, bool fp64, const void* Mt, const void* Gt, void* Lt, int64_t Kh, cudaStream_t s,
+cudaError_t launch_m2l(int p, bool fp64, const void* Mt, const void* Gt, const void* Gr, void* Lt, int64_t Kh,
+                       cudaStream_t s,
                        int* nlaunch);
 // nsys systems sharing Gt, spectra laid out [c][system][k] (thread per (k, l, system))
-cudaError_t launch_m2l_systems(int p, bool fp64, const void* Mt, const void* Gt, void* Lt, int64_t Kh, int nsys,
+cudaError_t launch_m2l_systems(int p, bool fp64, const void* Mt, const void* Gt, const void* Gr, void* Lt, int64_t Kh,
+                               int nsys,
                                cudaStream_t s, int* nlaunch);
 
 // ---------------------------------------------------------------- batch.cu
@@ -282,7 +284,11 @@ cudaError_t launch_green_open(double* G, const Dims& d, int p, int c, const doub
 cudaError_t launch_green_periodic(double* G, const Dims& d, int p, int c, const double cs[3], double alpha_s,
                                   int nmax, cudaStream_t st);
 // spectrum (FP64, [CG][Kh]) scaled by 1/Kt -> T
-cudaError_t launch_green_finish(const void* specd, void* out, bool fp64, int64_t count, double scale,
+// Parity-reduced kernel spectra: one real number per component and wavevector
+// (real part for even order, imaginary part for odd order), scaled.
+cudaError_t launch_green_parity(const void* specd, void* outr, bool fp64, int CG, int64_t Kh, double scale,
+                                cudaStream_t st);
+cudaError_t launch_green_finish(const void* specd, void* out, bool fp64, int64_t count, int64_t Kh, double scale,
                                 cudaStream_t st);
 
 // ---------------------------------------------------------------- pp.cu

@@ -42,46 +42,49 @@ __global__ void __launch_bounds__(128, (P <= 7 ? 4 : 1)) m2l_kernel(const cpx<T>
 }
 
 // Tile form: one block per tile of M2L_TILE consecutive wavevectors (of one
-// system), holding the tile's spectra of all C moment channels and all C_G kernel
-// components in shared memory (one coalesced asynchronous copy of each row), so
-// that every spectrum value is read from memory once however many output orders
-// use it.  Warp w takes the output orders w and P - w for the 32 wavevectors of
-// the tile (lane = wavevector): each warp then has the same number of terms, (P +
-// 2) (lam + 1) per source order lam.  Stores are coalesced rows of the tile.
+// system), holding the tile's spectra of all C moment channels and the
+// parity-reduced kernel spectra (one real number per component, m2l_order_par) in
+// shared memory (one coalesced asynchronous copy of each row), so that every
+// spectrum value is read from memory once however many output orders use it.
+// Warp w takes the output orders w and P - w for the 32 wavevectors of the tile
+// (lane = wavevector): each warp then has the same number of terms, (P + 2)
+// (lam + 1) per source order lam.  Stores are coalesced rows of the tile.
 constexpr int M2L_TILE = 32;
 
 template <int P, typename T>
 constexpr int m2l_tile_threads() { return 32 * ((P + 2) / 2); }
 template <int P, typename T>
-constexpr size_t m2l_tile_smem() { return (size_t)((P + 1) * (P + 1) + (2 * P + 1) * (2 * P + 1)) * M2L_TILE * sizeof(cpx<T>); }
+constexpr size_t m2l_tile_smem() {
+  return ((size_t)(P + 1) * (P + 1) * sizeof(cpx<T>) + (size_t)(2 * P + 1) * (2 * P + 1) * sizeof(T)) * M2L_TILE;
+}
 
-template <typename T>
-__device__ __forceinline__ void cp_async_cpx(cpx<T>* dst, const cpx<T>* src, bool valid) {
+// 4-, 8- or 16-byte asynchronous copy global -> shared; zero fill when !valid
+template <int BYTES>
+__device__ __forceinline__ void cp_async_n(void* dst, const void* src, bool valid) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-  const int n = valid ? (int)sizeof(cpx<T>) : 0;  // zero fill past the last wavevector
-  if constexpr (sizeof(cpx<T>) == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+  const int n = valid ? BYTES : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(BYTES), "r"(n) : "memory");
 }
 
 template <int P, typename T>
 __global__ void __launch_bounds__(m2l_tile_threads<P, T>()) m2l_tile_kernel(const cpx<T>* __restrict__ Mt,
-                                                                           const cpx<T>* __restrict__ Gt,
+                                                                           const T* __restrict__ Gr,
                                                                            cpx<T>* __restrict__ Lt, int64_t Kh,
                                                                            int nsys) {
   constexpr int C = (P + 1) * (P + 1), CG = (2 * P + 1) * (2 * P + 1);
   extern __shared__ __align__(16) unsigned char m2l_smem[];
   cpx<T>* Ms = reinterpret_cast<cpx<T>*>(m2l_smem);
-  cpx<T>* Gs = Ms + C * M2L_TILE;
+  T* Gs = reinterpret_cast<T*>(Ms + C * M2L_TILE);
   const int64_t k0 = (int64_t)blockIdx.x * M2L_TILE;
   const int64_t cstride = (int64_t)nsys * Kh, mk0 = (int64_t)blockIdx.y * Kh + k0;
   for (int i = threadIdx.x; i < (C + CG) * M2L_TILE; i += blockDim.x) {
     const int row = i / M2L_TILE, tk = i - row * M2L_TILE;
     const bool valid = k0 + tk < Kh;
-    const cpx<T>* src = row < C ? Mt + row * cstride + mk0 + (valid ? tk : 0)
-                                : Gt + (int64_t)(row - C) * Kh + k0 + (valid ? tk : 0);
-    cp_async_cpx<T>(Ms + i, src, valid);
+    const int t = valid ? tk : 0;
+    if (row < C)
+      cp_async_n<sizeof(cpx<T>)>(Ms + i, Mt + row * cstride + mk0 + t, valid);
+    else
+      cp_async_n<sizeof(T)>(Gs + (i - C * M2L_TILE), Gr + (int64_t)(row - C) * Kh + k0 + t, valid);
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
@@ -93,20 +96,20 @@ __global__ void __launch_bounds__(m2l_tile_threads<P, T>()) m2l_tile_kernel(cons
   auto St = [&](int c, cpx<T> v) {
     if (store) Lo[c * cstride] = v;
   };
-  m2l_order<P, T>(w, P, Mk, Gk, St);
-  if (P - w != w) m2l_order<P, T>(P - w, P, Mk, Gk, St);
+  m2l_order_par<P, T>(w, P, Mk, Gk, St);
+  if (P - w != w) m2l_order_par<P, T>(P - w, P, Mk, Gk, St);
 }
 
 template <int P, typename T>
 bool m2l_tile_fits() { return m2l_tile_smem<P, T>() <= 200 * 1024; }
 
 template <int P, typename T>
-cudaError_t run_tile(const void* Mt, const void* Gt, void* Lt, int64_t Kh, int nsys, cudaStream_t s) {
+cudaError_t run_tile(const void* Mt, const void* Gr, void* Lt, int64_t Kh, int nsys, cudaStream_t s) {
   const size_t smem = m2l_tile_smem<P, T>();
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(m2l_tile_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((unsigned)((Kh + M2L_TILE - 1) / M2L_TILE), (unsigned)nsys);
-  m2l_tile_kernel<P, T><<<grid, m2l_tile_threads<P, T>(), smem, s>>>((const cpx<T>*)Mt, (const cpx<T>*)Gt,
+  m2l_tile_kernel<P, T><<<grid, m2l_tile_threads<P, T>(), smem, s>>>((const cpx<T>*)Mt, (const T*)Gr,
                                                                       (cpx<T>*)Lt, Kh, nsys);
   return cudaGetLastError();
 }
@@ -115,8 +118,8 @@ cudaError_t run_tile(const void* Mt, const void* Gt, void* Lt, int64_t Kh, int n
 constexpr int64_t M2L_CT_MIN_BLOCKS = 1024;
 
 template <int P, typename T>
-cudaError_t run(const void* Mt, const void* Gt, void* Lt, int64_t Kh, int nsys, cudaStream_t s) {
-  if (m2l_tile_fits<P, T>()) return run_tile<P, T>(Mt, Gt, Lt, Kh, nsys, s);
+cudaError_t run(const void* Mt, const void* Gt, const void* Gr, void* Lt, int64_t Kh, int nsys, cudaStream_t s) {
+  if (Gr && m2l_tile_fits<P, T>()) return run_tile<P, T>(Mt, Gr, Lt, Kh, nsys, s);
   dim3 grid((unsigned)((Kh + 127) / 128), P + 1, (unsigned)nsys);
   const bool ct = sizeof(T) == 4 && P <= 8 && (int64_t)grid.x * nsys >= M2L_CT_MIN_BLOCKS;
   if constexpr (sizeof(T) == 4 && P <= 8) {
@@ -130,26 +133,27 @@ cudaError_t run(const void* Mt, const void* Gt, void* Lt, int64_t Kh, int nsys, 
 }
 
 template <int P>
-cudaError_t dispatch(int p, bool fp64, const void* Mt, const void* Gt, void* Lt, int64_t Kh, int nsys,
+cudaError_t dispatch(int p, bool fp64, const void* Mt, const void* Gt, const void* Gr, void* Lt, int64_t Kh, int nsys,
                      cudaStream_t s) {
-  if (p == P) return fp64 ? run<P, double>(Mt, Gt, Lt, Kh, nsys, s) : run<P, float>(Mt, Gt, Lt, Kh, nsys, s);
-  if constexpr (P < PMMM_PMAX) return dispatch<P + 1>(p, fp64, Mt, Gt, Lt, Kh, nsys, s);
+  if (p == P)
+    return fp64 ? run<P, double>(Mt, Gt, Gr, Lt, Kh, nsys, s) : run<P, float>(Mt, Gt, Gr, Lt, Kh, nsys, s);
+  if constexpr (P < PMMM_PMAX) return dispatch<P + 1>(p, fp64, Mt, Gt, Gr, Lt, Kh, nsys, s);
   return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-cudaError_t launch_m2l(int p, bool fp64, const void* Mt, const void* Gt, void* Lt, int64_t Kh, cudaStream_t s,
-                       int* nl) {
+cudaError_t launch_m2l(int p, bool fp64, const void* Mt, const void* Gt, const void* Gr, void* Lt, int64_t Kh,
+                       cudaStream_t s, int* nl) {
   ++*nl;
-  return dispatch<0>(p, fp64, Mt, Gt, Lt, Kh, 1, s);
+  return dispatch<0>(p, fp64, Mt, Gt, Gr, Lt, Kh, 1, s);
 }
 
-cudaError_t launch_m2l_systems(int p, bool fp64, const void* Mt, const void* Gt, void* Lt, int64_t Kh, int nsys,
-                               cudaStream_t s, int* nl) {
+cudaError_t launch_m2l_systems(int p, bool fp64, const void* Mt, const void* Gt, const void* Gr, void* Lt, int64_t Kh,
+                               int nsys, cudaStream_t s, int* nl) {
   if (nsys < 1 || nsys > 65535) return cudaErrorInvalidValue;
   ++*nl;
-  return dispatch<0>(p, fp64, Mt, Gt, Lt, Kh, nsys, s);
+  return dispatch<0>(p, fp64, Mt, Gt, Gr, Lt, Kh, nsys, s);
 }
 
 }  // namespace pmmm

@@ -34,6 +34,7 @@ struct pmmm_plan {
   size_t tsize = 8;  // sizeof(T)
   // mesh workspace
   void *M = nullptr, *L = nullptr, *specM = nullptr, *specL = nullptr, *G = nullptr;
+  void* Gr = nullptr;  // parity-reduced kernel spectra [C_G][Kh]: one real number per value
   void *twx = nullptr, *twy = nullptr, *twz = nullptr;
   double* cellsum = nullptr;  // [5][K]: sum q, sum q u_x, sum q u_y, sum q u_z, sum q |u|^2
   int* cs = nullptr;          // [K+1]

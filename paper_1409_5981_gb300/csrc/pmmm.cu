@@ -96,6 +96,7 @@ void free_all(pmmm_plan* pl) {
   free_particles(pl);
   free_mesh(pl);
   dfree(pl, pl->G);
+  dfree(pl, pl->Gr);
   dfree(pl, pl->twx); dfree(pl, pl->twy); dfree(pl, pl->twz);
   dfree(pl, pl->partial);
   dfree(pl, pl->counter);
@@ -275,7 +276,9 @@ int build_green(pmmm_plan* pl) {
     e = launch_fft_forward(true, Gd, Sd, gd, pl->CG, tw, pl->stream, &nl);
   }
   if (e == cudaSuccess)
-    e = launch_green_finish(Sd, pl->G, pl->fp64, (int64_t)pl->CG * d.Kh, 1.0 / (double)d.Kt, pl->stream);
+    e = launch_green_finish(Sd, pl->G, pl->fp64, (int64_t)pl->CG * d.Kh, d.Kh, 1.0 / (double)d.Kt, pl->stream);
+  if (e == cudaSuccess) e = dalloc(pl, &pl->Gr, pl->tsize * pl->CG * (size_t)d.Kh);
+  if (e == cudaSuccess) e = launch_green_parity(Sd, pl->Gr, pl->fp64, pl->CG, d.Kh, 1.0 / (double)d.Kt, pl->stream);
   cudaError_t e2 = cudaStreamSynchronize(pl->stream);
   if (e == cudaSuccess) e = e2;
   if (Gd) cudaFree(Gd);
@@ -375,7 +378,7 @@ cudaError_t mesh_stage(pmmm_plan* pl, int B, int* nl) {
   const int simt = fp64 ? PMMM_M2L_ARITH_FP64_SIMT : PMMM_M2L_ARITH_FP32_SIMT;
   pl->m2l_arith = (B > 1 && pl->m2l_tc) ? PMMM_M2L_ARITH_SPLITBF16_TC : simt;
   if (B == 1) {
-    e = launch_m2l(pl->p, fp64, pl->specM, pl->G, pl->specL, pl->d.Kh, s, nl);
+    e = launch_m2l(pl->p, fp64, pl->specM, pl->G, pl->Gr, pl->specL, pl->d.Kh, s, nl);
   } else if (pl->m2l_tc || m2l_batched_gemm(fp64, pl->p, B)) {
     // matrix products per wavevector on wavevector-major spectra:
     // specM -> specL (transposed) -> M2L -> specM -> specL (channel-major)
@@ -386,7 +389,7 @@ cudaError_t mesh_stage(pmmm_plan* pl, int B, int* nl) {
                      : launch_m2l_batched(fp64, pl->specL, pl->G, pl->specM, pl->m2l_tab, pl->p, B, pl->d.Kh, s, nl);
     if (e == cudaSuccess) e = launch_transpose(fp64, pl->specM, pl->specL, pl->d.Kh, R, s, nl);
   } else {
-    e = launch_m2l_systems(pl->p, fp64, pl->specM, pl->G, pl->specL, pl->d.Kh, B, s, nl);
+    e = launch_m2l_systems(pl->p, fp64, pl->specM, pl->G, pl->Gr, pl->specL, pl->d.Kh, B, s, nl);
   }
   if (e != cudaSuccess) return e;
   mark(pl, ST_FFT_INV);
@@ -422,7 +425,7 @@ cudaError_t hier_stage(pmmm_plan* pl, int* nl) {
   pl->m2l_arith = (h.wavemajor && pl->m2l_tc) ? PMMM_M2L_ARITH_SPLITBF16_TC
                                               : (fp64 ? PMMM_M2L_ARITH_FP64_SIMT : PMMM_M2L_ARITH_FP32_SIMT);
   if (!h.wavemajor)
-    e = launch_m2l_systems(pl->p, fp64, pl->hspecM, bp->G, pl->hspecL, Khh, (int)Kc, s, nl);
+    e = launch_m2l_systems(pl->p, fp64, pl->hspecM, bp->G, bp->Gr, pl->hspecL, Khh, (int)Kc, s, nl);
   else if (pl->m2l_tc)
     e = launch_m2l_tc(pl->hspecM, bp->G, pl->hspecL, pl->m2l_tab_tc, pl->p, (int)Kc, Khh, pl->num_sms, pl->m2l_tile,
                       pl->err, s, nl);

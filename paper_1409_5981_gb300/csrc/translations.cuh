@@ -183,6 +183,127 @@ PMMM_HD void m2l_order(int l, int p, LM&& Mk, LG&& Gk, ST&& St) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same M2L with the parity of the kernel spectra used.  Every stored kernel
+// component of order j is a real function of the cell offset with
+// G(-d) = (-1)^j G(d) (the solid harmonic S_j is homogeneous of parity (-1)^j,
+// and the masks, the zero padding and the periodic image sums are symmetric), so
+// its spectrum is real for even j and imaginary for odd j.  Gr(s) returns that
+// one real number of component s (Re for even j, Im for odd j).  Each
+// kernel-spectrum factor of a term is then a real scalar times eps_j (1 or i), and
+// eps_j is applied to the moment spectra once per source order (M' = eps_j M): a
+// complex product becomes a real scalar times a complex number, half the
+// multiply-adds of the complex form, with the kernel spectra half the size.
+template <typename T, int KAP>
+PMMM_HD T s_re_r(const T* sre, const T* sim) {
+  (void)sim;
+  if (KAP >= 0) return sre[KAP];
+  return ((-KAP) & 1) ? -sre[-KAP] : sre[-KAP];
+}
+template <typename T, int KAP>
+PMMM_HD T s_im_r(const T* sre, const T* sim) {
+  (void)sre;
+  if (KAP == 0) return T(0);
+  if (KAP > 0) return sim[KAP];
+  return ((-KAP) & 1) ? sim[-KAP] : -sim[-KAP];
+}
+// a += s v, s real: two multiply-adds
+template <typename T>
+PMMM_HD void rmac(cpx<T>& a, T s, cpx<T> v) {
+  a.x = fma(s, v.x, a.x);
+  a.y = fma(s, v.y, a.y);
+}
+
+// Term (m, mu) of Eq. realmatrix with real kernel scalars and M' = eps_j M.
+template <int P, typename T, int M, int MU>
+PMMM_HD void m2l_term_par(const T* sre, const T* sim, const cpx<T>* mre, const cpx<T>* mim, cpx<T>* Lre,
+                          cpx<T>* Lim) {
+  const T A = s_re_r<T, -(M + MU)>(sre, sim);
+  const T B = s_im_r<T, -(M + MU)>(sre, sim);
+  if constexpr (MU == 0) {
+    rmac(Lre[M], A, mre[0]);
+    if constexpr (M != 0) rmac(Lim[M], B, mre[0]);
+  } else {
+    T C = s_re_r<T, MU - M>(sre, sim);
+    T D = s_im_r<T, MU - M>(sre, sim);
+    if constexpr (MU & 1) {
+      C = -C;
+      D = -D;
+    }
+    rmac(Lre[M], A + C, mre[MU]);
+    rmac(Lre[M], D - B, mim[MU]);
+    rmac(Lim[M], B + D, mre[MU]);
+    rmac(Lim[M], A - C, mim[MU]);
+  }
+}
+
+template <int P, typename T, int M, int MU>
+struct M2LColPar {
+  PMMM_HD static void apply(int l, const T* sre, const T* sim, const cpx<T>* mre, const cpx<T>* mim, cpx<T>* Lre,
+                            cpx<T>* Lim) {
+    if (M > l) return;
+    m2l_term_par<P, T, M, MU>(sre, sim, mre, mim, Lre, Lim);
+    if constexpr (M < P) M2LColPar<P, T, M + 1, MU>::apply(l, sre, sim, mre, mim, Lre, Lim);
+  }
+};
+template <int P, typename T, int MU>
+struct M2LColsPar {
+  PMMM_HD static void apply(int l, int lam, const T* sre, const T* sim, const cpx<T>* mre, const cpx<T>* mim,
+                            cpx<T>* Lre, cpx<T>* Lim) {
+    if (MU > lam) return;
+    M2LColPar<P, T, 0, MU>::apply(l, sre, sim, mre, mim, Lre, Lim);
+    if constexpr (MU < P) M2LColsPar<P, T, MU + 1>::apply(l, lam, sre, sim, mre, mim, Lre, Lim);
+  }
+};
+
+// One output order l of the M2L at one wavevector from the parity-reduced kernel
+// spectra: Mk(c) as in m2l_order, Gr(s) the real number of component s, St(c, v).
+template <int P, typename T, class LM, class LG, class ST>
+PMMM_HD void m2l_order_par(int l, int p, LM&& Mk, LG&& Gr, ST&& St) {
+  cpx<T> Lre[P + 1], Lim[P + 1];
+#pragma unroll
+  for (int m = 0; m <= P; ++m) {
+    Lre[m] = mk(T(0), T(0));
+    Lim[m] = mk(T(0), T(0));
+  }
+  for (int lam = 0; lam <= p; ++lam) {
+    const int j = l + lam;
+    const bool odd = (j & 1) != 0;
+    cpx<T> mre[P + 1], mim[P + 1];
+#pragma unroll
+    for (int mu = 0; mu <= P; ++mu) {
+      mre[mu] = mk(T(0), T(0));
+      mim[mu] = mk(T(0), T(0));
+      if (mu <= lam) {
+        cpx<T> v = Mk(sidx(lam, mu));
+        mre[mu] = odd ? mk(-v.y, v.x) : v;
+        if (mu > 0) {
+          v = Mk(sidx(lam, -mu));
+          mim[mu] = odd ? mk(-v.y, v.x) : v;
+        }
+      }
+    }
+    T sre[2 * P + 1], sim[2 * P + 1];
+#pragma unroll
+    for (int a = 0; a <= 2 * P; ++a) {
+      sre[a] = T(0);
+      sim[a] = T(0);
+      if (a <= j) {
+        sre[a] = Gr(sidx(j, a));
+        if (a > 0) sim[a] = Gr(sidx(j, -a));
+      }
+    }
+    M2LColsPar<P, T, 0>::apply(l, lam, sre, sim, mre, mim, Lre, Lim);
+  }
+#pragma unroll
+  for (int m = 0; m <= P; ++m) {
+    if (m <= l) {
+      St(sidx(l, m), Lre[m]);
+      if (m > 0) St(sidx(l, -m), Lim[m]);
+    }
+  }
+}
+
 // L2P of Eq. L2P and the gradient through the order-one L2L of Eq. L2L
 // (Eq. phigrad: dPhi/dx = -Re L'_1^1, dPhi/dy = Im L'_1^1, dPhi/dz = L'_1^0).
 //   L(c) -> real channel c of the local expansion; R: real storage of R(r - r_L).

@@ -34,6 +34,19 @@ static void m2l_dispatch(int p, const double* M, const double* G, double* L) {
 }
 
 template <int P>
+static void m2l_par_dispatch(int p, const double* M, const double* Gr, double* L) {
+  if (p == P) {
+    const cpx<double>* Mc = reinterpret_cast<const cpx<double>*>(M);
+    cpx<double>* Lc = reinterpret_cast<cpx<double>*>(L);
+    for (int l = 0; l <= p; ++l)
+      m2l_order_par<P, double>(l, p, [&](int c) { return Mc[c]; }, [&](int s) { return Gr[s]; },
+                               [&](int c, cpx<double> v) { Lc[c] = v; });
+    return;
+  }
+  if constexpr (P < PMMM_PMAX) m2l_par_dispatch<P + 1>(p, M, Gr, L);
+}
+
+template <int P>
 static void l2p_dispatch(int p, const double* L, const double* u, double* out) {
   if (p == P) {
     double R[(P + 1) * (P + 1)];
@@ -93,6 +106,8 @@ static void fft_run(int L, int inverse, double* data) {
 }
 
 extern "C" {
+// M2L of one wavevector from the parity-reduced kernel spectra (one real number per component)
+void h_m2l_k_par(int p, const double* M, const double* Gr, double* L) { m2l_par_dispatch<0>(p, M, Gr, L); }
 int h_pmax() { return PMMM_PMAX; }
 void h_regular_real(int p, double x, double y, double z, double* out) { reg_dispatch<0>(p, x, y, z, out); }
 void h_singular_real(int J, double x, double y, double z, double* out) {

@@ -354,16 +354,16 @@ def test_config3_sampled_vs_oracle(pk, p):
     """N = 2^24 uniform +-1, periodic, mesh 64^3 (the multi-pass FFT and, in FP32, the
     compile-time-order M2L at the size they run at): the FP32 and the FP64 GPU paths
     against the oracle PMMM (all-cell-pair convolution of Eq. pmmm) on 32 sampled cells
-    (the four most crowded, eight on the box faces, the rest random).  ewald_nmax = 3 on
-    both sides keeps the oracle's Green table quick: the image sums at nmax = 3 already
-    converge far below rounding (erfc(4.5) ~ 2e-10 real space, exp(-39) reciprocal), and
-    the table is a set-up input of both paths, not a step under test."""
+    (the four most crowded, eight on the box faces, the rest random), with the default
+    Ewald truncation (nmax = 5, real-space terms below erfc(7.5) ~ 3e-26): the GPU's M2L
+    uses the parity of the converged kernel (its spectra real or imaginary by order), which
+    a truncation at nmax = 3 would break at the 2e-10 level (erfc(4.5))."""
     import torch
     n = 1 << 24
     pos, q = synth.uniform_pm1(n, synth.seed(3, 0))
     pos32 = pos.astype(np.float32).astype(np.float64)
     for prec in (pk.FP32, pk.FP64):
-        cfg = pk.Config(mesh=(64, 64, 64), p=p, boundary=pk.PERIODIC, precision=prec, ewald_nmax=3)
+        cfg = pk.Config(mesh=(64, 64, 64), p=p, boundary=pk.PERIODIC, precision=prec)
         dt = torch.float64 if prec == pk.FP64 else torch.float32
         plan = pk.Plan(cfg)
         phi, force, _ = plan.compute(torch.tensor(pos32, dtype=dt, device="cuda"),

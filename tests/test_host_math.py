@@ -34,6 +34,7 @@ def lib():
     L.h_singular_real.argtypes = [i, d, d, d, vp]
     L.h_fft.argtypes = [i, i, i, vp]
     L.h_m2l_k.argtypes = [i, vp, vp, vp]
+    L.h_m2l_k_par.argtypes = [i, vp, vp, vp]
     L.h_l2p.argtypes = [i, vp, vp, vp]
     L.h_m2l_table.argtypes = [i, vp, vp, vp]
     L.h_l2p_stream.argtypes = [i, vp, vp, vp]
@@ -197,3 +198,23 @@ def test_m2l_entry_table_matches_per_k_m2l(lib):
         lib.h_m2l_k(p, P(M), P(G), P(a))
         lib.h_m2l_table(p, P(M), P(G), P(b))
         assert np.abs(a - b).max() < 1e-12 * max(1.0, np.abs(a).max()), p
+
+
+def test_parity_m2l_equals_complex_form(lib):
+    """The M2L on parity-reduced kernel spectra (component s of order j: real spectrum
+    for even j, imaginary for odd j, one real number stored) equals the real-matrix
+    form on the full complex spectra with that structure, for every p."""
+    g = synth.rng(107)
+    for p in range(0, lib.h_pmax() + 1):
+        C, CG = (p + 1) ** 2, (2 * p + 1) ** 2
+        Mc = g.standard_normal(2 * C)
+        Gr = g.standard_normal(CG)
+        Gc = np.zeros(2 * CG)
+        for s in range(CG):
+            j = int(np.floor(np.sqrt(s)))
+            Gc[2 * s + (j & 1)] = Gr[s]
+        L1 = np.zeros(2 * C)
+        L2 = np.zeros(2 * C)
+        lib.h_m2l_k(p, P(Mc), P(Gc), P(L1))
+        lib.h_m2l_k_par(p, P(Mc), P(Gr), P(L2))
+        assert np.abs(L1 - L2).max() <= 1e-13 * max(1.0, np.abs(L1).max()), p
