@@ -305,9 +305,10 @@ def _probe_alu(pk):
 
 def _mesh_bytes(C, CG, K, Kh, esz):
     """(bytes of the mesh stages fft_forward + m2l + fft_inverse: M read, each spectrum
-    written and read, G~ read, L written; the same plus the P2M write of M and the L2P
-    read of L, the ideal-pass model 16CK + 32CKh + 8C_G Kh for FP32)."""
-    own = esz * (2 * C * K + 8 * C * Kh + 2 * CG * Kh)
+    written and read, the parity-reduced kernel spectra read (one real number per
+    value), L written; the ideal-pass model 16CK + 32CKh + 8C_G Kh for FP32, which adds
+    the P2M write of M and the L2P read of L and counts complex kernel spectra)."""
+    own = esz * (2 * C * K + 8 * C * Kh + CG * Kh)
     full = esz * (4 * C * K + 8 * C * Kh + 2 * CG * Kh)
     return own, full
 
@@ -349,8 +350,8 @@ def _mesh_roofline_64(pk, torch, dev, hbm, flush, steps=6):
             "stage_ms": {k: med[k] for k in ("p2m", "fft_forward", "m2l", "fft_inverse", "l2p")},
             "eval_ms": statistics.median(tot),
             "achieved": own / (ms * 1e-3) / 1e9, "frac": own / (ms * 1e-3) / 1e9 / hbm,
-            "bytes": own, "bytes_model": "4B*(2CK + 8CKh + 2C_G Kh): M read, spectra written and read, G~ read, "
-                                          "L written",
+            "bytes": own, "bytes_model": "4B*(2CK + 8CKh + C_G Kh): M read, spectra written and read, parity-reduced "
+                                          "G~ read (one real number per value), L written",
             "frac_survey_model": full / (ms * 1e-3) / 1e9 / hbm,
             "survey_model": "16CK + 32CKh + 8C_G Kh (adds the P2M write of M and the L2P read of L, whose "
                             "time is not in the stages timed)"}
@@ -588,8 +589,9 @@ def run_ours(args, rank, world, local_rank):
     C, CG, Kh, K = plan.info(pk.INFO_C), plan.info(pk.INFO_CG), plan.info(pk.INFO_KH), plan.info(pk.INFO_K)
     pp_ms = statistics.median(stage_acc.get("near_field", [float("nan")]))
     mesh_ms = sum(statistics.median(stage_acc.get(s, [0.0])) for s in ("fft_forward", "m2l", "fft_inverse"))
-    mesh_bytes = esz * (2 * C * K + 4 * 2 * C * Kh + 2 * CG * Kh)
-    bytes_model = "4B*(2CK + 8CKh + 2C_G Kh): M read, spectra written/read, G~ read, L written"
+    mesh_bytes, _ = _mesh_bytes(C, CG, K, Kh, esz)
+    bytes_model = ("4B*(2CK + 8CKh + C_G Kh): M read, spectra written/read, parity-reduced G~ read (one real "
+                   "number per value), L written")
     if refine > 1:
         # two levels: fine M read twice (M2M, block transform), the coarse mesh stage, block spectra
         # written and read twice, the block kernel spectra, kept outputs written and read, fine L written
@@ -600,10 +602,10 @@ def run_ours(args, rank, world, local_rank):
             mb *= 2
         Khh, W = mb * mb * (mb // 2 + 1), (2 * cut + 1) * refine
         mesh_bytes = esz * (3 * C * K + 2 * C * Kc + 8 * C * Kc * Khh + 2 * CG * Khh + 2 * C * Kc * W ** 3
-                            + 8 * C * Khc + 2 * CG * Khc)
-        bytes_model = ("4B*(3CK + 2CKc + 8CKcKhh + 2C_G Khh + 2CKcW^3 + 8CKhc + 2C_G Khc): fine M read twice, "
+                            + 8 * C * Khc + CG * Khc)
+        bytes_model = ("4B*(3CK + 2CKc + 8CKcKhh + 2C_G Khh + 2CKcW^3 + 8CKhc + C_G Khc): fine M read twice, "
                        "coarse M written/read, block spectra written/read twice, block kernel spectra, kept "
-                       "outputs written/read, coarse spectra and kernel, fine L written")
+                       "outputs written/read, coarse spectra and parity-reduced kernel, fine L written")
     hbm, sm_max, peak_kind = _peaks()
     alu_derived = 2.0 * FP32_LANES_PER_SM * NUM_SMS * sm_max * 1e6 / 1e12
     alu_peak = alu_meas / 1e12

@@ -272,8 +272,6 @@ PMMM_HD void m2l_order_par(int l, int p, LM&& Mk, LG&& Gr, ST&& St) {
     cpx<T> mre[P + 1], mim[P + 1];
 #pragma unroll
     for (int mu = 0; mu <= P; ++mu) {
-      mre[mu] = mk(T(0), T(0));
-      mim[mu] = mk(T(0), T(0));
       if (mu <= lam) {
         cpx<T> v = Mk(sidx(lam, mu));
         mre[mu] = odd ? mk(-v.y, v.x) : v;
@@ -286,8 +284,6 @@ PMMM_HD void m2l_order_par(int l, int p, LM&& Mk, LG&& Gr, ST&& St) {
     T sre[2 * P + 1], sim[2 * P + 1];
 #pragma unroll
     for (int a = 0; a <= 2 * P; ++a) {
-      sre[a] = T(0);
-      sim[a] = T(0);
       if (a <= j) {
         sre[a] = Gr(sidx(j, a));
         if (a > 0) sim[a] = Gr(sidx(j, -a));
