@@ -168,6 +168,21 @@ __global__ void __launch_bounds__(FFT_THREADS) cols_kernel(cpx<T>* __restrict__ 
   }
 }
 
+// Block-wide copy of n complex values (plane of the spectrum <-> shared memory):
+// 16-byte words (two FP32 complex values) when both ends are 16-byte aligned.
+template <typename T>
+__device__ __forceinline__ void copy_plane(cpx<T>* dst, const cpx<T>* src, int n) {
+  if (sizeof(T) == 4 && ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll 4
+    for (int e = threadIdx.x; e < n / 2; e += blockDim.x) d4[e] = s4[e];
+    if ((n & 1) && threadIdx.x == 0) dst[n - 1] = src[n - 1];
+  } else {
+    for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
+  }
+}
+
 // Forward x and y passes of one plane (c, z < nz) in one block: the real rows
 // y < ny (two per complex transform) -> half-spectrum rows -> columns along y
 // (rows y >= ny zero) -> the plane [Ly][hx] of the spectrum, written contiguously.
@@ -198,15 +213,35 @@ __global__ void __launch_bounds__(FFT_THREADS) plane_fwd_kernel(const T* __restr
   const int npairs = (d.ny + 1) / 2;
   const T* src = in + (c * d.nz + z) * (int64_t)d.ny * d.nx;
   // x pass: row pair pr packs rows 2 pr (real part) and 2 pr + 1 (imaginary part)
-  for (int e = threadIdx.x; e < npairs * Lx; e += blockDim.x) {
-    const int pr = e / Lx, x = e - pr * Lx;
-    const int ya = 2 * pr, yb = ya + 1;
-    T a = T(0), b = T(0);
-    if (x < d.nx) {
-      a = src[(int64_t)ya * d.nx + x];
-      if (yb < d.ny) b = src[(int64_t)yb * d.nx + x];
+  if (sizeof(T) == 4 && (d.nx & 3) == 0) {
+    // FP32 rows read as 16-byte vectors, four loads in flight per thread
+    const int q4 = Lx / 4, nq = d.nx / 4;
+#pragma unroll 4
+    for (int v = threadIdx.x; v < npairs * q4; v += blockDim.x) {
+      const int pr = v / q4, x4 = v - pr * q4;
+      const int ya = 2 * pr, yb = ya + 1;
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+      if (x4 < nq) {
+        a = reinterpret_cast<const float4*>(src + (int64_t)ya * d.nx)[x4];
+        if (yb < d.ny) b = reinterpret_cast<const float4*>(src + (int64_t)yb * d.nx)[x4];
+      }
+      cpx<T>* o = A + pr * Lx + 4 * x4;
+      o[0] = mk((T)a.x, (T)b.x);
+      o[1] = mk((T)a.y, (T)b.y);
+      o[2] = mk((T)a.z, (T)b.z);
+      o[3] = mk((T)a.w, (T)b.w);
     }
-    A[e] = mk(a, b);
+  } else {
+    for (int e = threadIdx.x; e < npairs * Lx; e += blockDim.x) {
+      const int pr = e / Lx, x = e - pr * Lx;
+      const int ya = 2 * pr, yb = ya + 1;
+      T a = T(0), b = T(0);
+      if (x < d.nx) {
+        a = src[(int64_t)ya * d.nx + x];
+        if (yb < d.ny) b = src[(int64_t)yb * d.nx + x];
+      }
+      A[e] = mk(a, b);
+    }
   }
   __syncthreads();
   if constexpr (LX > 0)
@@ -231,7 +266,7 @@ __global__ void __launch_bounds__(FFT_THREADS) plane_fwd_kernel(const T* __restr
   else
     run_stages<T, false>(B, A, ply, hx, ty, -1);
   cpx<T>* dst = out + c * d.Kh + (int64_t)z * Ly * hx;
-  for (int e = threadIdx.x; e < Ly * hx; e += blockDim.x) dst[e] = B[e];
+  copy_plane<T>(dst, B, Ly * hx);
 }
 
 // Inverse y and x passes of one plane (c, z < nz): the plane [Ly][hx] of the
@@ -259,7 +294,7 @@ __global__ void __launch_bounds__(FFT_THREADS) plane_inv_kernel(const cpx<T>* __
   const int z = (int)(blockIdx.x - c * d.nz);
   const int npairs = (d.ny + 1) / 2;
   const cpx<T>* src = in + c * d.Kh + (int64_t)z * Ly * hx;
-  for (int e = threadIdx.x; e < Ly * hx; e += blockDim.x) A[e] = src[e];
+  copy_plane<T>(A, src, Ly * hx);
   __syncthreads();
   if constexpr (LY > 0)
     run_stages_ct<T, false, LY, +1>(A, B, hx, ty);
@@ -291,10 +326,25 @@ __global__ void __launch_bounds__(FFT_THREADS) plane_inv_kernel(const cpx<T>* __
   else
     run_stages<T, true>(B, A, plx, npairs, tx, +1);
   T* dst = out + (c * d.nz + z) * (int64_t)d.ny * d.nx;
-  for (int e = threadIdx.x; e < d.ny * d.nx; e += blockDim.x) {
-    const int y = e / d.nx, x = e - y * d.nx;
-    const cpx<T> v = B[(y >> 1) * Lx + x];
-    dst[e] = (y & 1) ? v.y : v.x;
+  if (sizeof(T) == 4 && (d.nx & 3) == 0) {
+    const int nq = d.nx / 4;
+#pragma unroll 4
+    for (int v = threadIdx.x; v < d.ny * nq; v += blockDim.x) {
+      const int y = v / nq, x = 4 * (v - y * nq);
+      const cpx<T>* r = B + (y >> 1) * Lx + x;
+      float4 o;
+      if (y & 1)
+        o = make_float4((float)r[0].y, (float)r[1].y, (float)r[2].y, (float)r[3].y);
+      else
+        o = make_float4((float)r[0].x, (float)r[1].x, (float)r[2].x, (float)r[3].x);
+      reinterpret_cast<float4*>(dst)[v] = o;
+    }
+  } else {
+    for (int e = threadIdx.x; e < d.ny * d.nx; e += blockDim.x) {
+      const int y = e / d.nx, x = e - y * d.nx;
+      const cpx<T> v = B[(y >> 1) * Lx + x];
+      dst[e] = (y & 1) ? v.y : v.x;
+    }
   }
 }
 
@@ -354,15 +404,38 @@ __global__ void __launch_bounds__(FFT_THREADS) cols_ct_kernel(cpx<T>* __restrict
   const int b1 = (int)(blockIdx.x % (unsigned)nb1), b2 = (int)(blockIdx.x / (unsigned)nb1);
   cpx<T>* base = data + (int64_t)b2 * bstride2 + (int64_t)b1 * bstride1 + col0;
   const int w = min(TW, inner - col0);
-  for (int e = threadIdx.x; e < L * TW; e += blockDim.x) {
-    const int row = e / TW, col = e - row * TW;
-    A[e] = (row < nin && col < w) ? base[row * col_stride + col] : mk(T(0), T(0));
+  // FP32 full tiles with 16-byte aligned rows: two complex values per load / store
+  const bool vec = sizeof(T) == 4 && w == TW && (TW & 1) == 0 && (col_stride & 1) == 0 &&
+                   ((reinterpret_cast<uintptr_t>(base)) & 15) == 0;
+  if (vec) {
+    const int h = TW / 2;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < L * h; e += blockDim.x) {
+      const int row = e / h, c2 = e - row * h;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (row < nin) v = reinterpret_cast<const float4*>(base + row * col_stride)[c2];
+      reinterpret_cast<float4*>(A)[e] = v;
+    }
+  } else {
+    for (int e = threadIdx.x; e < L * TW; e += blockDim.x) {
+      const int row = e / TW, col = e - row * TW;
+      A[e] = (row < nin && col < w) ? base[row * col_stride + col] : mk(T(0), T(0));
+    }
   }
   __syncthreads();
   run_stages_ct<T, false, L, SGN>(A, B, TW, st);
-  for (int e = threadIdx.x; e < L * TW; e += blockDim.x) {
-    const int row = e / TW, col = e - row * TW;
-    if (row < nout && col < w) base[row * col_stride + col] = A[e];
+  if (vec) {
+    const int h = TW / 2;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < nout * h; e += blockDim.x) {
+      const int row = e / h, c2 = e - row * h;
+      reinterpret_cast<float4*>(base + row * col_stride)[c2] = reinterpret_cast<const float4*>(A)[e];
+    }
+  } else {
+    for (int e = threadIdx.x; e < L * TW; e += blockDim.x) {
+      const int row = e / TW, col = e - row * TW;
+      if (row < nout && col < w) base[row * col_stride + col] = A[e];
+    }
   }
 }
 
