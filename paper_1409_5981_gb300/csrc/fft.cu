@@ -212,7 +212,11 @@ __global__ void __launch_bounds__(FFT_THREADS) plane_fwd_kernel(const T* __restr
   const int z = (int)(blockIdx.x - c * d.nz);
   const int npairs = (d.ny + 1) / 2;
   const T* src = in + (c * d.nz + z) * (int64_t)d.ny * d.nx;
-  // x pass: row pair pr packs rows 2 pr (real part) and 2 pr + 1 (imaginary part)
+  // x pass: row pair pr packs rows 2 pr (real part) and 2 pr + 1 (imaginary part).
+  // Compile-time lengths keep the pairs as columns (element x of pair pr at
+  // A[x ES + pr], ES = npairs + 1 odd: bank-conflict-free butterflies); else rows.
+  const int ES = LX > 0 ? npairs + 1 : 0;
+  auto xat = [&](int pr, int x) { return LX > 0 ? x * ES + pr : pr * Lx + x; };
   if (sizeof(T) == 4 && (d.nx & 3) == 0) {
     // FP32 rows read as 16-byte vectors, four loads in flight per thread
     const int q4 = Lx / 4, nq = d.nx / 4;
@@ -225,11 +229,10 @@ __global__ void __launch_bounds__(FFT_THREADS) plane_fwd_kernel(const T* __restr
         a = reinterpret_cast<const float4*>(src + (int64_t)ya * d.nx)[x4];
         if (yb < d.ny) b = reinterpret_cast<const float4*>(src + (int64_t)yb * d.nx)[x4];
       }
-      cpx<T>* o = A + pr * Lx + 4 * x4;
-      o[0] = mk((T)a.x, (T)b.x);
-      o[1] = mk((T)a.y, (T)b.y);
-      o[2] = mk((T)a.z, (T)b.z);
-      o[3] = mk((T)a.w, (T)b.w);
+      A[xat(pr, 4 * x4 + 0)] = mk((T)a.x, (T)b.x);
+      A[xat(pr, 4 * x4 + 1)] = mk((T)a.y, (T)b.y);
+      A[xat(pr, 4 * x4 + 2)] = mk((T)a.z, (T)b.z);
+      A[xat(pr, 4 * x4 + 3)] = mk((T)a.w, (T)b.w);
     }
   } else {
     for (int e = threadIdx.x; e < npairs * Lx; e += blockDim.x) {
@@ -240,12 +243,12 @@ __global__ void __launch_bounds__(FFT_THREADS) plane_fwd_kernel(const T* __restr
         a = src[(int64_t)ya * d.nx + x];
         if (yb < d.ny) b = src[(int64_t)yb * d.nx + x];
       }
-      A[e] = mk(a, b);
+      A[xat(pr, x)] = mk(a, b);
     }
   }
   __syncthreads();
   if constexpr (LX > 0)
-    run_stages_ct<T, true, LX, -1>(A, B, npairs, tx);
+    run_stages_ct<T, false, LX, -1>(A, B, npairs, tx, ES);
   else
     run_stages<T, true>(A, B, plx, npairs, tx, -1);
   // half spectra of the rows into B as the plane [Ly][hx] (rows y >= ny zero)
@@ -254,8 +257,8 @@ __global__ void __launch_bounds__(FFT_THREADS) plane_fwd_kernel(const T* __restr
     cpx<T> v = mk(T(0), T(0));
     if (y < d.ny) {
       const int pr = y >> 1;
-      const cpx<T> Z = A[pr * Lx + k];
-      const cpx<T> Zm = conjg(A[pr * Lx + ((Lx - k) & (Lx - 1))]);
+      const cpx<T> Z = A[xat(pr, k)];
+      const cpx<T> Zm = conjg(A[xat(pr, (Lx - k) & (Lx - 1))]);
       v = (y & 1) ? mk((Z.y - Zm.y) * T(0.5), -(Z.x - Zm.x) * T(0.5)) : mk((Z.x + Zm.x) * T(0.5), (Z.y + Zm.y) * T(0.5));
     }
     B[e] = v;
@@ -301,6 +304,9 @@ __global__ void __launch_bounds__(FFT_THREADS) plane_inv_kernel(const cpx<T>* __
   else
     run_stages<T, false>(A, B, ply, hx, ty, +1);
   // rows y < ny of the plane -> row pairs Z = X + i Y over the full length Lx in B
+  // (columns with the odd stride ES for compile-time lengths, as the forward pass)
+  const int ES = LX > 0 ? npairs + 1 : 0;
+  auto xat = [&](int pr, int x) { return LX > 0 ? x * ES + pr : pr * Lx + x; };
   for (int e = threadIdx.x; e < npairs * Lx; e += blockDim.x) {
     const int pr = e / Lx, k = e - pr * Lx;
     cpx<T> v[2];
@@ -318,11 +324,11 @@ __global__ void __launch_bounds__(FFT_THREADS) plane_inv_kernel(const cpx<T>* __
         }
       }
     }
-    B[e] = mk(v[0].x - v[1].y, v[0].y + v[1].x);
+    B[xat(pr, k)] = mk(v[0].x - v[1].y, v[0].y + v[1].x);
   }
   __syncthreads();
   if constexpr (LX > 0)
-    run_stages_ct<T, true, LX, +1>(B, A, npairs, tx);
+    run_stages_ct<T, false, LX, +1>(B, A, npairs, tx, ES);
   else
     run_stages<T, true>(B, A, plx, npairs, tx, +1);
   T* dst = out + (c * d.nz + z) * (int64_t)d.ny * d.nx;
@@ -330,19 +336,19 @@ __global__ void __launch_bounds__(FFT_THREADS) plane_inv_kernel(const cpx<T>* __
     const int nq = d.nx / 4;
 #pragma unroll 4
     for (int v = threadIdx.x; v < d.ny * nq; v += blockDim.x) {
-      const int y = v / nq, x = 4 * (v - y * nq);
-      const cpx<T>* r = B + (y >> 1) * Lx + x;
+      const int y = v / nq, x = 4 * (v - y * nq), pr = y >> 1;
+      const cpx<T> r0 = B[xat(pr, x)], r1 = B[xat(pr, x + 1)], r2 = B[xat(pr, x + 2)], r3 = B[xat(pr, x + 3)];
       float4 o;
       if (y & 1)
-        o = make_float4((float)r[0].y, (float)r[1].y, (float)r[2].y, (float)r[3].y);
+        o = make_float4((float)r0.y, (float)r1.y, (float)r2.y, (float)r3.y);
       else
-        o = make_float4((float)r[0].x, (float)r[1].x, (float)r[2].x, (float)r[3].x);
+        o = make_float4((float)r0.x, (float)r1.x, (float)r2.x, (float)r3.x);
       reinterpret_cast<float4*>(dst)[v] = o;
     }
   } else {
     for (int e = threadIdx.x; e < d.ny * d.nx; e += blockDim.x) {
       const int y = e / d.nx, x = e - y * d.nx;
-      const cpx<T> v = B[(y >> 1) * Lx + x];
+      const cpx<T> v = B[xat(y >> 1, x)];
       dst[e] = (y & 1) ? v.y : v.x;
     }
   }
@@ -352,7 +358,7 @@ __global__ void __launch_bounds__(FFT_THREADS) plane_inv_kernel(const cpx<T>* __
 // pairs (npairs x Lx) and the plane (Ly x hx).
 template <typename T>
 int64_t plane_buf(const Dims& d) {
-  const int64_t a = (int64_t)((d.ny + 1) / 2) * d.Lx, b = (int64_t)d.Ly * d.hx;
+  const int64_t a = (int64_t)((d.ny + 1) / 2 + 1) * d.Lx, b = (int64_t)d.Ly * d.hx;
   return a > b ? a : b;
 }
 template <typename T>
@@ -454,8 +460,9 @@ int pick_ppb(int L) {
 }
 
 int pick_tw(int inner, int L, size_t elem) {
-  // whole rows of up to 40 columns (e.g. the 17 or 33 points of a half spectrum), else 16
-  int TW = inner <= 40 ? inner : 16;
+  // whole rows of up to 40 columns (e.g. the 17 or 33 points of a half spectrum), else 32
+  // (256-byte row segments of FP32 complex values)
+  int TW = inner <= 40 ? inner : 32;
   while (TW > 1 && 2 * (size_t)L * TW * elem > 96 * 1024) TW /= 2;
   return TW;
 }

@@ -166,9 +166,12 @@ __device__ __forceinline__ void stockham_bf_ct(const cpx<T>* in, cpx<T>* out, in
 // Every stage of `ntrans` length-L transforms held in shared memory (A -> B ->
 // ..., the result ends in A on return, pointers swapped as in run_stages).
 // ROWS: transform tr at A[tr L ...] (stride 1); else element t of transform tr at
-// A[t ntrans + tr].  Block-wide: ends with __syncthreads().
+// A[t es + tr], es = ntrans unless given (a larger, odd stride keeps the lanes of
+// a warp on distinct banks when ntrans is a power of two).  Block-wide: ends
+// with __syncthreads().
 template <typename T, bool ROWS, int L, int SGN, int ST = 0>
-__device__ __forceinline__ void run_stages_ct(cpx<T>*& A, cpx<T>*& B, int ntrans, const cpx<T>* tw) {
+__device__ __forceinline__ void run_stages_ct(cpx<T>*& A, cpx<T>*& B, int ntrans, const cpx<T>* tw, int es = 0) {
+  if (es == 0) es = ntrans;
   if constexpr (ST < ct_nstages(L)) {
     constexpr int R = ct_radix(L, ST), NS = ct_ns(L, ST), nb = L / R;
     if constexpr (ROWS) {
@@ -181,7 +184,7 @@ __device__ __forceinline__ void run_stages_ct(cpx<T>*& A, cpx<T>*& B, int ntrans
       const int dq = (int)blockDim.x / ntrans, dr = (int)blockDim.x - dq * ntrans;
       int tr = (int)threadIdx.x % ntrans, j = (int)threadIdx.x / ntrans;
       for (; j < nb; j += dq) {
-        stockham_bf_ct<T, L, R, NS, SGN>(A + tr, B + tr, j, ntrans, tw);
+        stockham_bf_ct<T, L, R, NS, SGN>(A + tr, B + tr, j, es, tw);
         tr += dr;
         if (tr >= ntrans) {
           tr -= ntrans;
@@ -193,7 +196,7 @@ __device__ __forceinline__ void run_stages_ct(cpx<T>*& A, cpx<T>*& B, int ntrans
     cpx<T>* tmp = A;
     A = B;
     B = tmp;
-    run_stages_ct<T, ROWS, L, SGN, ST + 1>(A, B, ntrans, tw);
+    run_stages_ct<T, ROWS, L, SGN, ST + 1>(A, B, ntrans, tw, es);
   }
 }
 
