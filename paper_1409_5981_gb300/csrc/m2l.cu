@@ -41,10 +41,127 @@ __global__ void __launch_bounds__(128, (P <= 7 ? 4 : 1)) m2l_kernel(const cpx<T>
     m2l_order<P, T>(l, p, Mk, Gk, St);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 packed form of m2l_order_par: the real and imaginary parts of every
+// spectrum value travel together as a float2, each kernel scalar g is used as the
+// pair (g, g), and the sums and multiply-adds run as packed f32x2 operations, so a
+// term (m, mu > 0) issues 4 packed additions and 4 packed multiply-adds instead of
+// 4 additions and 8 multiply-adds.  Same operations per component, same order.
+__device__ __forceinline__ float2 pk_neg(float2 a) { return make_float2(-a.x, -a.y); }
+// SA X + SB Y for compile-time signs
+template <int SA, int SB>
+__device__ __forceinline__ float2 pk_comb(float2 X, float2 Y) {
+  if constexpr (SA > 0 && SB > 0) return __fadd2_rn(X, Y);
+  if constexpr (SA > 0 && SB < 0) return __fadd2_rn(X, pk_neg(Y));
+  if constexpr (SA < 0 && SB > 0) return __fadd2_rn(Y, pk_neg(X));
+  return pk_neg(__fadd2_rn(X, Y));
+}
+// spectrum scalar of Re S_j^KAP (SRe) or Im S_j^KAP (SIm) as (index into the stored
+// components, sign), from sre[a] = X[sidx(j, a)], sim[a] = X[sidx(j, -a)], a >= 0
+template <int KAP> struct SRe { static constexpr int idx = KAP >= 0 ? KAP : -KAP, sgn = (KAP < 0 && ((-KAP) & 1)) ? -1 : 1; };
+template <int KAP> struct SIm { static constexpr int idx = KAP >= 0 ? KAP : -KAP, sgn = (KAP < 0 && !((-KAP) & 1)) ? -1 : 1, zero = KAP == 0; };
+template <int P, int M, int MU>
+__device__ __forceinline__ void m2l_term_pk(const float2* sre, const float2* sim, const float2* mre, const float2* mim,
+                                            float2* Lre, float2* Lim) {
+  using A = SRe<-(M + MU)>;
+  using B = SIm<-(M + MU)>;
+  if constexpr (MU == 0) {
+    Lre[M] = __ffma2_rn(A::sgn > 0 ? sre[A::idx] : pk_neg(sre[A::idx]), mre[0], Lre[M]);
+    if constexpr (!B::zero) Lim[M] = __ffma2_rn(B::sgn > 0 ? sim[B::idx] : pk_neg(sim[B::idx]), mre[0], Lim[M]);
+  } else {
+    using Cc = SRe<MU - M>;
+    using Dd = SIm<MU - M>;
+    constexpr int cs = (MU & 1) ? -Cc::sgn : Cc::sgn, ds = (MU & 1) ? -Dd::sgn : Dd::sgn;
+    const float2 a = sre[A::idx], c = sre[Cc::idx];
+    const float2 u1 = pk_comb<A::sgn, cs>(a, c);
+    const float2 u4 = pk_comb<A::sgn, -cs>(a, c);
+    float2 u2, u3;
+    if constexpr (B::zero && Dd::zero) {
+      u2 = make_float2(0.f, 0.f);
+      u3 = u2;
+    } else if constexpr (B::zero) {
+      u2 = ds > 0 ? sim[Dd::idx] : pk_neg(sim[Dd::idx]);
+      u3 = u2;
+    } else if constexpr (Dd::zero) {
+      u2 = B::sgn > 0 ? pk_neg(sim[B::idx]) : sim[B::idx];
+      u3 = B::sgn > 0 ? sim[B::idx] : pk_neg(sim[B::idx]);
+    } else {
+      u2 = pk_comb<ds, -B::sgn>(sim[Dd::idx], sim[B::idx]);
+      u3 = pk_comb<B::sgn, ds>(sim[B::idx], sim[Dd::idx]);
+    }
+    Lre[M] = __ffma2_rn(u1, mre[MU], Lre[M]);
+    if constexpr (!(B::zero && Dd::zero)) Lre[M] = __ffma2_rn(u2, mim[MU], Lre[M]);
+    if constexpr (!(B::zero && Dd::zero)) Lim[M] = __ffma2_rn(u3, mre[MU], Lim[M]);
+    Lim[M] = __ffma2_rn(u4, mim[MU], Lim[M]);
+  }
+}
+template <int P, int M, int MU>
+struct M2LColPk {
+  __device__ __forceinline__ static void apply(int l, const float2* sre, const float2* sim, const float2* mre,
+                                               const float2* mim, float2* Lre, float2* Lim) {
+    if (M > l) return;
+    m2l_term_pk<P, M, MU>(sre, sim, mre, mim, Lre, Lim);
+    if constexpr (M < P) M2LColPk<P, M + 1, MU>::apply(l, sre, sim, mre, mim, Lre, Lim);
+  }
+};
+template <int P, int MU>
+struct M2LColsPk {
+  __device__ __forceinline__ static void apply(int l, int lam, const float2* sre, const float2* sim,
+                                               const float2* mre, const float2* mim, float2* Lre, float2* Lim) {
+    if (MU > lam) return;
+    M2LColPk<P, 0, MU>::apply(l, sre, sim, mre, mim, Lre, Lim);
+    if constexpr (MU < P) M2LColsPk<P, MU + 1>::apply(l, lam, sre, sim, mre, mim, Lre, Lim);
+  }
+};
+// One output order l at one wavevector: Mk(c) -> float2 spectrum of channel c,
+// Gs1(s) -> the parity-reduced kernel scalar of component s, St(c, float2).
+template <int P, class LM, class LG, class ST>
+__device__ __forceinline__ void m2l_order_pk(int l, int p, LM&& Mk, LG&& Gs1, ST&& St) {
+  float2 Lre[P + 1], Lim[P + 1];
+#pragma unroll
+  for (int m = 0; m <= P; ++m) Lre[m] = Lim[m] = make_float2(0.f, 0.f);
+  for (int lam = 0; lam <= p; ++lam) {
+    const int j = l + lam;
+    const bool odd = (j & 1) != 0;
+    float2 mre[P + 1], mim[P + 1];
+#pragma unroll
+    for (int mu = 0; mu <= P; ++mu) {
+      if (mu <= lam) {
+        float2 v = Mk(sidx(lam, mu));
+        mre[mu] = odd ? make_float2(-v.y, v.x) : v;
+        if (mu > 0) {
+          v = Mk(sidx(lam, -mu));
+          mim[mu] = odd ? make_float2(-v.y, v.x) : v;
+        }
+      }
+    }
+    float2 sre[2 * P + 1], sim[2 * P + 1];
+#pragma unroll
+    for (int a = 0; a <= 2 * P; ++a) {
+      if (a <= j) {
+        const float g = Gs1(sidx(j, a));
+        sre[a] = make_float2(g, g);
+        if (a > 0) {
+          const float h = Gs1(sidx(j, -a));
+          sim[a] = make_float2(h, h);
+        }
+      }
+    }
+    M2LColsPk<P, 0>::apply(l, lam, sre, sim, mre, mim, Lre, Lim);
+  }
+#pragma unroll
+  for (int m = 0; m <= P; ++m) {
+    if (m <= l) {
+      St(sidx(l, m), Lre[m]);
+      if (m > 0) St(sidx(l, -m), Lim[m]);
+    }
+  }
+}
+
 // Tile form: one block per tile of M2L_TILE consecutive wavevectors (of one
 // system), holding the tile's spectra of all C moment channels and the
-// parity-reduced kernel spectra (one real number per component, m2l_order_par) in
-// shared memory (one coalesced asynchronous copy of each row), so that every
+// parity-reduced kernel spectra (one real number per component; m2l_order_pk in
+// FP32, m2l_order_par in FP64) in shared memory (one coalesced asynchronous copy of each row), so that every
 // spectrum value is read from memory once however many output orders use it.
 // Warp w takes the output orders w and P - w for the 32 wavevectors of the tile
 // (lane = wavevector): each warp then has the same number of terms, (P + 2)
@@ -67,7 +184,7 @@ __device__ __forceinline__ void cp_async_n(void* dst, const void* src, bool vali
 }
 
 template <int P, typename T>
-__global__ void __launch_bounds__(m2l_tile_threads<P, T>()) m2l_tile_kernel(const cpx<T>* __restrict__ Mt,
+__global__ void __launch_bounds__(m2l_tile_threads<P, T>(), (sizeof(T) == 4 ? 4 : 1)) m2l_tile_kernel(const cpx<T>* __restrict__ Mt,
                                                                            const T* __restrict__ Gr,
                                                                            cpx<T>* __restrict__ Lt, int64_t Kh,
                                                                            int nsys) {
@@ -91,13 +208,24 @@ __global__ void __launch_bounds__(m2l_tile_threads<P, T>()) m2l_tile_kernel(cons
   const int tk = threadIdx.x & 31, w = threadIdx.x >> 5;
   const bool store = k0 + tk < Kh;
   cpx<T>* Lo = Lt + mk0 + tk;
-  auto Mk = [&](int c) { return Ms[c * M2L_TILE + tk]; };
-  auto Gk = [&](int s) { return Gs[s * M2L_TILE + tk]; };
-  auto St = [&](int c, cpx<T> v) {
-    if (store) Lo[c * cstride] = v;
-  };
-  m2l_order_par<P, T>(w, P, Mk, Gk, St);
-  if (P - w != w) m2l_order_par<P, T>(P - w, P, Mk, Gk, St);
+  if constexpr (sizeof(T) == 4) {
+    const float2* M2 = reinterpret_cast<const float2*>(Ms);
+    auto Mk = [&](int c) { return M2[c * M2L_TILE + tk]; };
+    auto Gk = [&](int s) { return (float)Gs[s * M2L_TILE + tk]; };
+    auto St = [&](int c, float2 v) {
+      if (store) Lo[c * cstride] = mk((T)v.x, (T)v.y);
+    };
+    m2l_order_pk<P>(w, P, Mk, Gk, St);
+    if (P - w != w) m2l_order_pk<P>(P - w, P, Mk, Gk, St);
+  } else {
+    auto Mk = [&](int c) { return Ms[c * M2L_TILE + tk]; };
+    auto Gk = [&](int s) { return Gs[s * M2L_TILE + tk]; };
+    auto St = [&](int c, cpx<T> v) {
+      if (store) Lo[c * cstride] = v;
+    };
+    m2l_order_par<P, T>(w, P, Mk, Gk, St);
+    if (P - w != w) m2l_order_par<P, T>(P - w, P, Mk, Gk, St);
+  }
 }
 
 template <int P, typename T>
