@@ -251,8 +251,16 @@ enum {
   PMMM_INFO_TUNED_NEAR = 9, /* near-field kernel chosen by pmmm_plan_autotune (0: none, from the config) */
   PMMM_INFO_M2L_TILE = 10,  /* systems per CTA of the tensor-core batched M2L (32 or 64; default 64) */
   PMMM_INFO_REFINE = 11,    /* refinement of a two-level plan (1: one level) */
-  PMMM_INFO_M2L_ARITH = 12  /* arithmetic of the last compute's M2L: PMMM_M2L_ARITH_* (-1 before any) */
+  PMMM_INFO_M2L_ARITH = 12, /* arithmetic of the last compute's M2L: PMMM_M2L_ARITH_* (-1 before any) */
+  PMMM_INFO_SPLIT = 13      /* 1 if the last compute ran the far field beside the near field (below) */
 };
+/* Split evaluation (FP32 plans whose near field runs on cell items, i.e. not the
+ * per-target kernel of sparse cells): after the sort, the far field (P2M, mesh
+ * stage, periodic corrections, L2P) runs on a second stream of the plan, created
+ * with the highest priority, beside the near field, whose sums go to a workspace
+ * buffer; one more launch adds the two.  The results equal those of the plain
+ * sequence bit for bit.  Off while stage timing is on and for surrogate
+ * evaluations. */
 /* The M2L arithmetic that actually ran.  PMMM_FP32_SPLITBF16_M2L asks for the
  * tensor cores, but they serve only where the per-wavevector M2L is a true matrix
  * product: batched evaluations of more than one system, and the fine-level block

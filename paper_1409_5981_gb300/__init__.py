@@ -27,7 +27,7 @@ EXPORT_PERM, EXPORT_SORTED_CELL, EXPORT_CELL_START = 1, 2, 3
 EXPORT_MULTIPOLE, EXPORT_LOCAL, EXPORT_CORR, EXPORT_FAR = 4, 5, 6, 7
 INFO_K, INFO_C, INFO_CG, INFO_KH, INFO_N, INFO_WORKSPACE_BYTES, INFO_LAUNCHES = 1, 2, 3, 4, 5, 6, 7
 INFO_SYSTEMS = 8
-INFO_TUNED_NEAR, INFO_M2L_TILE, INFO_REFINE, INFO_M2L_ARITH = 9, 10, 11, 12
+INFO_TUNED_NEAR, INFO_M2L_TILE, INFO_REFINE, INFO_M2L_ARITH, INFO_SPLIT = 9, 10, 11, 12, 13
 M2L_ARITH_FP64_SIMT, M2L_ARITH_FP32_SIMT, M2L_ARITH_SPLITBF16_TC = 0, 1, 2
 MAX_SYSTEMS = 65535
 SUR_PARAMS, SUR_ADAM_M, SUR_ADAM_V, SUR_IN_SCALE, SUR_OUT_SCALE = 1, 2, 3, 4, 5

@@ -326,12 +326,20 @@ cudaError_t launch_gather_lists(const void* rec, bool fp64, const uint32_t* vals
 // (epart[max_items][4]).  Persistent warps fetch items from *counter.  With
 // FP32, c = 1 and src2 given, the packed-FP32 kernel on the pair layout is used.
 // per_target (FP32, c = 1 only): one thread per sorted target (keys = sorted cell ids), for sparse cells.
+// near_out (split evaluation; only where pp_tma_applies): the near sums of every
+// sorted target go to near_out[s] = (phi, grad) / (hs, hs^2) instead of being
+// combined, and launch_pp_combine adds the far field afterwards.
 bool pp_per_target_applies(bool fp64, int c);
+bool pp_tma_applies(bool fp64, int c, bool per_target);
 cudaError_t launch_pp(bool fp64, const void* part, const void* src2, const uint32_t* pair_start, const uint32_t* vals,
                       const uint32_t* keys, int64_t n, bool per_target, const int* cell_start, int64_t K,
                       const uint32_t* item_start, const uint32_t* item_cell, unsigned int* counter, int num_sms,
-                      const void* far, PPParams pp, void* phi, void* force, double* epart, int* err,
+                      const void* far, PPParams pp, void* phi, void* force, double* epart, int* err, void* near_out,
                       cudaStream_t s, int* nlaunch);
+cudaError_t launch_pp_combine(const void* part, const uint32_t* vals, const int* cell_start, int64_t K,
+                              const uint32_t* item_start, const uint32_t* item_cell, int64_t max_items,
+                              const void* far, const void* nearv, PPParams pp, void* phi, void* force, double* epart,
+                              int num_sms, cudaStream_t s, int* nlaunch);
 
 // ---------------------------------------------------------------- reduce.cu
 // Sums per-cell FP64 quantities and builds the periodic correction terms:

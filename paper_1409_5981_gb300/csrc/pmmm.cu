@@ -69,6 +69,7 @@ void free_particles(pmmm_plan* pl) {
   dfree(pl, pl->src2);
   dfree(pl, pl->epart);
   dfree(pl, pl->bpartial);
+  dfree(pl, pl->nearv);
   pl->bchunks = 0;
   pl->max_items = 0;
   pl->cap = 0;
@@ -113,6 +114,14 @@ void free_all(pmmm_plan* pl) {
   pl->gexec = nullptr;
   if (pl->cstream) cudaStreamDestroy(pl->cstream);
   pl->cstream = nullptr;
+  if (pl->aux) {
+    cudaStreamSynchronize(pl->aux);
+    cudaStreamDestroy(pl->aux);
+  }
+  pl->aux = nullptr;
+  if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+  if (pl->ev_join) cudaEventDestroy(pl->ev_join);
+  pl->ev_fork = pl->ev_join = nullptr;
   for (int i = 0; i <= ST_COUNT; ++i)
     if (pl->ev[i]) cudaEventDestroy(pl->ev[i]);
 }
@@ -149,6 +158,7 @@ cudaError_t alloc_mesh(pmmm_plan* pl, int B) {
 
 int ensure_particles(pmmm_plan* pl, int64_t n);
 int ensure_m2l_tables(pmmm_plan* pl);
+void set_streams(pmmm_plan* pl, cudaStream_t s);
 
 // Grows the mesh workspace to B systems (the particle workspace, sized by the
 // cell count, is rebuilt with it).
@@ -230,6 +240,7 @@ int ensure_particles(pmmm_plan* pl, int64_t n) {
   if (e == cudaSuccess) e = dalloc(pl, &v, sizeof(double) * 4 * (size_t)mi);
   if (e == cudaSuccess) pl->epart = (double*)v;
   if (e == cudaSuccess && !pl->fp64) e = dalloc(pl, &pl->src2, 32 * (size_t)pp_pairs_max(Kb, cap));
+  if (e == cudaSuccess && !pl->fp64 && pl->split) e = dalloc(pl, &pl->nearv, 16 * (size_t)cap);
   // items of one system: at most its cells + cap / 32 + 1
   const int bch = reduce_batched_chunks(pl->d.K, pp_items_max(pl->d.K, cap));
   if (e == cudaSuccess) e = dalloc(pl, &v, sizeof(double) * 5 * (size_t)pl->bcap * bch);
@@ -369,7 +380,9 @@ cudaError_t mesh_stage(pmmm_plan* pl, int B, int* nl) {
   const bool fp64 = pl->fp64;
   cudaError_t e = cudaSuccess;
   FftTw tw{pl->twx, pl->twy, pl->twz};
-  const bool fused = fft_fused_applies(fp64, pl->d);
+  // one CTA per channel only when the channels fill the GPU; otherwise the plane
+  // kernels (a CTA per channel and z plane) and the column pass
+  const bool fused = fft_fused_applies(fp64, pl->d) && (int64_t)pl->C * B >= pl->num_sms;
   e = fused ? launch_fft_fused_forward(pl->M, pl->specM, pl->d, pl->C * B, tw, s, nl)
             : launch_fft_forward(fp64, pl->M, pl->specM, pl->d, pl->C * B, tw, s, nl);
   if (e != cudaSuccess) return e;
@@ -456,6 +469,8 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
   const int near = pl->tuned_near ? pl->tuned_near : pl->cfg.near_field;
   const bool per_target = pp_per_target_applies(fp64, pl->g.c) &&
                           (near == PMMM_NEAR_PER_TARGET || (near == PMMM_NEAR_AUTO && sparse));
+  bool split = false;
+  cudaStream_t fs = s;
 #define CK(x)                    \
   do {                           \
     e = (x);                     \
@@ -478,8 +493,21 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
                            K, pl->part, fp64 ? nullptr : pl->src2, pl->item_cell, pl->epart, pp_items_max(K, n),
                            per_target, s, &nl));
   }
+  // Split evaluation: the far field (P2M .. L2P) goes to the plan's second stream
+  // and runs beside the near field, which then leaves its sums in nearv; a
+  // combination launch follows both.  Not with stage timing (stages queued one
+  // by one) nor with a far-field hook (the surrogate's own plans).
+  split = pl->split && pl->aux && pl->nearv && !pl->timing && !pl->hook && pl->src2 &&
+          pp_tma_applies(fp64, pl->g.c, per_target);
+  fs = s;
+  if (split) {
+    CK(cudaEventRecord(pl->ev_fork, s));
+    CK(cudaStreamWaitEvent(pl->aux, pl->ev_fork, 0));
+    fs = pl->aux;
+    set_streams(pl, fs);
+  }
   mark(pl, ST_P2M);
-  CK(launch_p2m(pl->p, fp64, pl->part, pl->cs, K, pl->M, pl->cellsum, pl->cellsum + K, sparse, s, &nl));
+  CK(launch_p2m(pl->p, fp64, pl->part, pl->cs, K, pl->M, pl->cellsum, pl->cellsum + K, sparse, fs, &nl));
   mark(pl, ST_FFT_FWD);
   CK(pl->hier ? hier_stage(pl, &nl) : mesh_stage(pl, B, &nl));
   mark(pl, ST_L2P);
@@ -489,12 +517,12 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
       // the coarse per-cell sums come from the coarse P2M)
       pmmm_plan* cp = pl->coarse;
       CK(launch_corrections(cp->cellsum, cp->cellsum + cp->d.K, cp->d.K, cp->g.hs, pl->g.V, pl->partial,
-                            reduce_tickets(pl), pl->corr, s, &nl));
+                            reduce_tickets(pl), pl->corr, fs, &nl));
     } else if (B == 1) {
       CK(launch_corrections(pl->cellsum, pl->cellsum + K, K, pl->g.hs, pl->g.V, pl->partial, reduce_tickets(pl),
-                            pl->corr, s, &nl));
+                            pl->corr, fs, &nl));
     } else {
-      CK(launch_corrections_batched(pl->cellsum, K, Ks, B, pl->g.hs, pl->g.V, pl->bpartial, pl->corr, s, &nl));
+      CK(launch_corrections_batched(pl->cellsum, K, Ks, B, pl->g.hs, pl->g.V, pl->bpartial, pl->corr, fs, &nl));
     }
   }
   {
@@ -528,7 +556,11 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
       Luse = pl->hook->L;
       puse = pl->hook->p_l2p;
     }
-    CK(launch_l2p(puse, fp64, pl->part, pl->keys_sorted, n, Luse, K, pl->corr, cellq, cp, pl->far, s, &nl));
+    CK(launch_l2p(puse, fp64, pl->part, pl->keys_sorted, n, Luse, K, pl->corr, cellq, cp, pl->far, fs, &nl));
+  }
+  if (split) {
+    set_streams(pl, s);
+    CK(cudaEventRecord(pl->ev_join, fs));
   }
   mark(pl, ST_PP);
   {
@@ -550,7 +582,12 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
     const int64_t mi = pp_items_max(K, n);
     CK(launch_pp(fp64, pl->part, pl->src2, pl->pair_start, pl->vals_sorted, pl->keys_sorted, n, per_target, pl->cs, K,
                  pl->item_start, pl->item_cell, pl->counter, pl->num_sms, pl->far, pp, phi, force, pl->epart, pl->err,
-                 s, &nl));
+                 split ? pl->nearv : nullptr, s, &nl));
+    if (split) {
+      CK(cudaStreamWaitEvent(s, pl->ev_join, 0));
+      CK(launch_pp_combine(pl->part, pl->vals_sorted, pl->cs, K, pl->item_start, pl->item_cell, mi, pl->far,
+                           pl->nearv, pp, phi, force, pl->epart, pl->num_sms, s, &nl));
+    }
     mark(pl, ST_REDUCE);
     if (B == 1)
       CK(launch_energy(pl->epart, mi, pl->partial + 256 * 5, reduce_tickets(pl) + 1, pl->energy, s, &nl));
@@ -560,6 +597,8 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
   mark(pl, ST_COUNT);
 #undef CK
 done:
+  if (split) set_streams(pl, s);
+  pl->split_last = split && e == cudaSuccess;
   pl->launches = nl;
   pl->n_last = n;
   pl->nsys_last = B;
@@ -687,7 +726,9 @@ int graph_eval(pmmm_plan* pl, int B, int64_t n, const int64_t* off, const void* 
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(pl->cstream, &graph);
     set_streams(pl, user);
-    if (e == cudaSuccess && rc == PMMM_OK) e = cudaGraphInstantiate(&pl->gexec, graph, 0);
+    // node priorities as captured (the far-field stream's launches first)
+    if (e == cudaSuccess && rc == PMMM_OK)
+      e = cudaGraphInstantiateWithFlags(&pl->gexec, graph, cudaGraphInstantiateFlagUseNodePriority);
     if (graph) cudaGraphDestroy(graph);
     if (rc != PMMM_OK || e != cudaSuccess) {
       if (pl->gexec && e != cudaSuccess) cudaGraphExecDestroy(pl->gexec);
@@ -826,6 +867,7 @@ int pmmm_plan_create(const pmmm_config* cfg, void* stream, pmmm_plan** out) {
   pl->C = (cfg->p + 1) * (cfg->p + 1);
   pl->CG = (2 * cfg->p + 1) * (2 * cfg->p + 1);
   pl->fp64 = cfg->precision == PMMM_FP64;
+  pl->split = !pl->fp64;
   pl->m2l_tc = cfg->precision == PMMM_FP32_SPLITBF16_M2L && m2l_tc_supported(cfg->p);
   pl->tsize = pl->fp64 ? sizeof(double) : sizeof(float);
   const bool per = cfg->boundary == PMMM_PERIODIC;
@@ -870,6 +912,15 @@ int pmmm_plan_create(const pmmm_config* cfg, void* stream, pmmm_plan** out) {
   if (e == cudaSuccess) e = launch_twiddles(pl->fp64, d.Ly, pl->twy, pl->stream);
   if (e == cudaSuccess) e = launch_twiddles(pl->fp64, d.Lz, pl->twz, pl->stream);
   for (int i = 0; i <= ST_COUNT && e == cudaSuccess; ++i) e = cudaEventCreate(&pl->ev[i]);
+  if (e == cudaSuccess && pl->split) {
+    // the far field's stream takes the highest priority, so that its blocks are
+    // placed ahead of queued near-field blocks
+    int lo = 0, hi = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&pl->aux, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     rc = map_cuda(e);
     free_all(pl);
@@ -1126,6 +1177,7 @@ int pmmm_plan_info(pmmm_plan* pl, int what, int64_t* value) {
     case PMMM_INFO_M2L_TILE: *value = pl->m2l_tile; break;
     case PMMM_INFO_REFINE: *value = pl->hier ? pl->hg.r : 1; break;
     case PMMM_INFO_M2L_ARITH: *value = pl->m2l_arith; break;
+    case PMMM_INFO_SPLIT: *value = pl->split_last ? 1 : 0; break;
     default: return PMMM_ERR_INVALID_ARG;
   }
   return PMMM_OK;

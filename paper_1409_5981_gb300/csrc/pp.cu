@@ -399,11 +399,6 @@ __device__ __forceinline__ f2 pk2(float a, float b) {
   return r;
 }
 __device__ __forceinline__ void up2(f2 r, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
-__device__ __forceinline__ f2 add2(f2 a, f2 b) {
-  f2 d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
 __device__ __forceinline__ f2 sub2(f2 a, f2 b) {
   f2 d;
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
@@ -522,7 +517,18 @@ template <bool SELF>
 __device__ __forceinline__ void pp_sweep(const float4* __restrict__ src, int npair, int ph, int SP, float2 tx,
                                          float2 ty, float2 tz, float2& pot, float2& gx, float2& gy, float2& gz) {
   if (SP == 1) {
-    for (int j = 0; j < npair; j += 4) {
+    int j = 0;
+    for (; j + 8 <= npair; j += 8) {
+      float4 A[8], B[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        A[u] = src[2 * (j + u)];
+        B[u] = src[2 * (j + u) + 1];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) pp_pair_v<SELF>(A[u], B[u], tx, ty, tz, pot, gx, gy, gz);
+    }
+    for (; j < npair; j += 4) {
       const float4 A0 = src[2 * j], B0 = src[2 * j + 1], A1 = src[2 * j + 2], B1 = src[2 * j + 3];
       const float4 A2 = src[2 * j + 4], B2 = src[2 * j + 5], A3 = src[2 * j + 6], B3 = src[2 * j + 7];
       pp_pair_v<SELF>(A0, B0, tx, ty, tz, pot, gx, gy, gz);
@@ -532,6 +538,16 @@ __device__ __forceinline__ void pp_sweep(const float4* __restrict__ src, int npa
     }
   } else {
     int j = ph;
+    for (; j + 3 * SP < npair; j += 4 * SP) {
+      float4 A[4], B[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        A[u] = src[2 * (j + u * SP)];
+        B[u] = src[2 * (j + u * SP) + 1];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pp_pair_v<SELF>(A[u], B[u], tx, ty, tz, pot, gx, gy, gz);
+    }
     for (; j + SP < npair; j += 2 * SP) {
       const float4 A0 = src[2 * j], B0 = src[2 * j + 1], A1 = src[2 * (j + SP)], B1 = src[2 * (j + SP) + 1];
       pp_pair_v<SELF>(A0, B0, tx, ty, tz, pot, gx, gy, gz);
@@ -547,7 +563,7 @@ __global__ void __launch_bounds__(PP_WARPS * 32, NT_BLOCKS_PER_SM) pp_kernel_tma
     const uint32_t* __restrict__ vals, const int* __restrict__ cs, int64_t K, const uint32_t* __restrict__ item_start,
     const uint32_t* __restrict__ item_cell, unsigned int* __restrict__ counter, const float* __restrict__ far,
     PPParams pp, float* __restrict__ phi, float* __restrict__ force, double* __restrict__ epart,
-    int* __restrict__ err) {
+    int* __restrict__ err, float4* __restrict__ near_out) {
   constexpr int W = 2 * CUT + 1, NS = W * W * W, SL = (NS + 31) / 32, SELFK = (NS - 1) / 2;
   __shared__ __align__(128) float4 sbuf[PP_WARPS][2][2 * NT_CAP];
   __shared__ __align__(8) unsigned long long sbar[PP_WARPS][2];
@@ -731,13 +747,23 @@ __global__ void __launch_bounds__(PP_WARPS * 32, NT_BLOCKS_PER_SM) pp_kernel_tma
       gys += __shfl_xor_sync(0xffffffffu, gys, o);
       gzs += __shfl_xor_sync(0xffffffffu, gzs, o);
     }
+    // near sums in units of 1 / hs and 1 / hs^2, each product rounded on its own
+    // (no contraction with the far-field addition), so that the split evaluation,
+    // which stores them and adds the far field later, gives the same results
+    const float np0 = __fmul_rn(ps, pp.ih32), np1 = __fmul_rn(gxs, pp.ih2_32), np2 = __fmul_rn(gys, pp.ih2_32),
+                np3 = __fmul_rn(gzs, pp.ih2_32);
+    if (near_out) {  // split evaluation: the near sums only, combined later by pp_combine_kernel
+      if (active && ph == 0) near_out[tbeg + tl] = make_float4(np0, np1, np2, np3);
+      ++item;
+      continue;
+    }
     float e_t = 0.f, f_t[3] = {0.f, 0.f, 0.f};
     if (active && ph == 0) {
       const int s = tbeg + tl;
       const float4 fr = reinterpret_cast<const float4*>(far)[s];
-      const float ih = pp.ih32, ih2 = pp.ih2_32, sg = pp.sign32;
-      const float pt = sg * (fr.x + ps * ih);
-      const float g0 = sg * (fr.y + gxs * ih2), g1 = sg * (fr.z + gys * ih2), g2 = sg * (fr.w + gzs * ih2);
+      const float sg = pp.sign32;
+      const float pt = sg * (fr.x + np0);
+      const float g0 = sg * (fr.y + np1), g1 = sg * (fr.z + np2), g2 = sg * (fr.w + np3);
       const uint32_t o = vals[s];
       const float q = xi.w;
       if (phi) phi[o] = pt;
@@ -765,6 +791,62 @@ __global__ void __launch_bounds__(PP_WARPS * 32, NT_BLOCKS_PER_SM) pp_kernel_tma
       epart[(int64_t)item * 4 + 3] = (double)f_t[2];
     }
     ++item;
+  }
+}
+
+// Combination of a split FP32 evaluation, where the near field ran beside the far
+// field and left its sums (potential, gradient, in units of 1 / hs and 1 / hs^2)
+// in near_out: one warp per work item, lane = target, the same combination,
+// caller-order stores and per-item energy and net-force partials as the
+// epilogue of pp_kernel_tma.
+__global__ void __launch_bounds__(256) pp_combine_kernel(const float4* __restrict__ part,
+                                                         const uint32_t* __restrict__ vals, const int* __restrict__ cs,
+                                                         int64_t K, const uint32_t* __restrict__ item_start,
+                                                         const uint32_t* __restrict__ item_cell,
+                                                         const float4* __restrict__ far,
+                                                         const float4* __restrict__ nearv, PPParams pp,
+                                                         float* __restrict__ phi, float* __restrict__ force,
+                                                         double* __restrict__ epart) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nitems = item_start[K];
+  const uint32_t wstride = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < nitems; item += wstride) {
+    const int cell = (int)item_cell[item];
+    const int tbeg = cs[cell] + (int)(item - item_start[cell]) * CHUNK;
+    const int R = min(CHUNK, cs[cell + 1] - tbeg);
+    float e_t = 0.f, f_t[3] = {0.f, 0.f, 0.f};
+    if (lane < R) {
+      const int s = tbeg + lane;
+      const float4 fr = far[s], nr = nearv[s];
+      const float sg = pp.sign32;
+      const float pt = sg * (fr.x + nr.x);
+      const float g0 = sg * (fr.y + nr.y), g1 = sg * (fr.z + nr.z), g2 = sg * (fr.w + nr.w);
+      const uint32_t o = vals[s];
+      const float q = part[s].w;
+      if (phi) phi[o] = pt;
+      if (force) {
+        force[3 * (int64_t)o + 0] = -q * g0;
+        force[3 * (int64_t)o + 1] = -q * g1;
+        force[3 * (int64_t)o + 2] = -q * g2;
+      }
+      e_t = 0.5f * q * pt;
+      f_t[0] = -q * g0;
+      f_t[1] = -q * g1;
+      f_t[2] = -q * g2;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e_t += __shfl_xor_sync(0xffffffffu, e_t, o);
+      f_t[0] += __shfl_xor_sync(0xffffffffu, f_t[0], o);
+      f_t[1] += __shfl_xor_sync(0xffffffffu, f_t[1], o);
+      f_t[2] += __shfl_xor_sync(0xffffffffu, f_t[2], o);
+    }
+    if (lane == 0) {
+      epart[(int64_t)item * 4 + 0] = (double)e_t;
+      epart[(int64_t)item * 4 + 1] = (double)f_t[0];
+      epart[(int64_t)item * 4 + 2] = (double)f_t[1];
+      epart[(int64_t)item * 4 + 3] = (double)f_t[2];
+    }
   }
 }
 
@@ -933,12 +1015,28 @@ cudaError_t launch_gather_lists(const void* rec, bool fp64, const uint32_t* vals
 }
 
 bool pp_per_target_applies(bool fp64, int c) { return !fp64 && c <= 2; }
+bool pp_tma_applies(bool fp64, int c, bool per_target) { return !fp64 && c <= 2 && !per_target; }
+
+cudaError_t launch_pp_combine(const void* part, const uint32_t* vals, const int* cell_start, int64_t K,
+                              const uint32_t* item_start, const uint32_t* item_cell, int64_t max_items,
+                              const void* far, const void* nearv, PPParams pp, void* phi, void* force, double* epart,
+                              int num_sms, cudaStream_t s, int* nl) {
+  if (max_items <= 0) return cudaSuccess;
+  int64_t blocks = (max_items + 7) / 8;  // 8 warps (items) per block
+  const int64_t cap = 8 * (int64_t)(num_sms > 0 ? num_sms : 1);
+  if (blocks > cap) blocks = cap;
+  pp_combine_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float4*)part, vals, cell_start, K, item_start, item_cell,
+                                                     (const float4*)far, (const float4*)nearv, pp, (float*)phi,
+                                                     (float*)force, epart);
+  ++*nl;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pp(bool fp64, const void* part, const void* src2, const uint32_t* pair_start, const uint32_t* vals,
                       const uint32_t* keys, int64_t n, bool per_target, const int* cell_start, int64_t K,
                       const uint32_t* item_start, const uint32_t* item_cell, unsigned int* counter, int num_sms,
-                      const void* far, PPParams pp, void* phi, void* force, double* epart, int* err, cudaStream_t s,
-                      int* nl) {
+                      const void* far, PPParams pp, void* phi, void* force, double* epart, int* err, void* near_out,
+                      cudaStream_t s, int* nl) {
   // persistent launch: PP_BLOCKS_PER_SM resident blocks of PP_WARPS warps per SM
   const unsigned blocks = (unsigned)(PP_BLOCKS_PER_SM * (num_sms > 0 ? num_sms : 1));
   if (per_target && pp_per_target_applies(fp64, pp.c) && src2 != nullptr) {
@@ -952,17 +1050,20 @@ cudaError_t launch_pp(bool fp64, const void* part, const void* src2, const uint3
       pp_target_kernel<2><<<g, PPS_THREADS, 0, s>>>((const float4*)part, (const ulonglong2*)src2, pair_start, keys,
                                                     vals, cell_start, item_start, n, (const float4*)far, pp,
                                                     (float*)phi, (float*)force, epart);
-  } else if (!fp64 && pp.c <= 2 && src2 != nullptr) {
+  } else if (pp_tma_applies(fp64, pp.c, false) && src2 != nullptr) {
     const unsigned tblocks = (unsigned)(NT_BLOCKS_PER_SM * (num_sms > 0 ? num_sms : 1));
     if (pp.c <= 1)
       pp_kernel_tma<1><<<tblocks, PP_WARPS * 32, 0, s>>>((const float*)part, (const float*)src2, pair_start, vals,
                                                          cell_start, K, item_start, item_cell, counter,
-                                                         (const float*)far, pp, (float*)phi, (float*)force, epart, err);
+                                                         (const float*)far, pp, (float*)phi, (float*)force, epart, err,
+                                                         (float4*)near_out);
     else
       pp_kernel_tma<2><<<tblocks, PP_WARPS * 32, 0, s>>>((const float*)part, (const float*)src2, pair_start, vals,
                                                          cell_start, K, item_start, item_cell, counter,
-                                                         (const float*)far, pp, (float*)phi, (float*)force, epart, err);
+                                                         (const float*)far, pp, (float*)phi, (float*)force, epart, err,
+                                                         (float4*)near_out);
   } else {
+    if (near_out) return cudaErrorInvalidValue;  // only the cell-item FP32 kernel splits
 #define PP_LAUNCH(T, S)                                                                                              \
   pp_kernel<T, S><<<blocks, PP_WARPS * 32, 0, s>>>((const T*)part, vals, cell_start, K, item_start, item_cell, counter, \
                                                    (const T*)far, pp, (T*)phi, (T*)force, epart)

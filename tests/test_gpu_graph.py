@@ -99,3 +99,42 @@ def test_batched_graph_default_stream(pk):
         assert np.array_equal(phi.cpu().numpy(), rphi) and np.array_equal(force.cpu().numpy(), rforce)
         assert np.array_equal(e, re)
     plan.close()
+
+
+@pytest.mark.parametrize("boundary,cutoff", [("periodic", 1), ("periodic", 2), ("open", 1)])
+def test_split_evaluation_matches_plain_sequence(pk, boundary, cutoff):
+    """FP32 cell-item near field: the far field runs on the plan's second stream
+    beside the near field (PMMM_INFO_SPLIT = 1), plain and graph-launched, and
+    gives the results of the one-stream sequence (stage timing on) bit for bit,
+    energies included; the batched form too."""
+    import torch
+    bc = pk.PERIODIC if boundary == "periodic" else pk.OPEN
+    cfg = pk.Config(mesh=(8, 8, 8), p=4, boundary=bc, precision=pk.FP32, cutoff=cutoff)
+    n = 32 * 8 ** 3  # 32 per cell: cell items, not the per-target kernel
+    pos, q = synth.uniform_pm1(n, synth.seed(7, 10 + cutoff))
+    tp = torch.tensor(pos.astype(np.float32), device="cuda")
+    tq = torch.tensor(q.astype(np.float32), device="cuda")
+    ref = pk.Plan(cfg)
+    ref.set_timing(True)
+    rphi, rforce, re = ref.compute(tp, tq, energy=True)
+    assert ref.info(pk.INFO_SPLIT) == 0
+    rphi, rforce = rphi.cpu().numpy(), rforce.cpu().numpy()
+    counts = np.array([n // 2, 0, n - n // 2])
+    bphi, bforce, be = ref.compute_batched(counts, tp, tq, energies=True)
+    assert ref.info(pk.INFO_SPLIT) == 0
+    bphi, bforce = bphi.cpu().numpy(), bforce.cpu().numpy()
+    ref.close()
+
+    plan = pk.Plan(cfg)
+    phi = torch.empty(n, dtype=torch.float32, device="cuda")
+    force = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    for k in range(3):  # plain, capture + launch, replay
+        _, _, e = plan.compute(tp, tq, phi=phi, force=force, energy=True)
+        assert plan.info(pk.INFO_SPLIT) == 1
+        assert np.array_equal(phi.cpu().numpy(), rphi) and np.array_equal(force.cpu().numpy(), rforce), f"call {k}"
+        assert e == re, f"call {k}"
+    sphi, sforce, se = plan.compute_batched(counts, tp, tq, energies=True)
+    assert plan.info(pk.INFO_SPLIT) == 1
+    assert np.array_equal(sphi.cpu().numpy(), bphi) and np.array_equal(sforce.cpu().numpy(), bforce)
+    assert np.array_equal(se, be)
+    plan.close()
