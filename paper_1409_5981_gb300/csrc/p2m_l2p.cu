@@ -36,15 +36,16 @@ __device__ __forceinline__ void p2m_accumulate(T ux, T uy, T uz, T q, T* acc) {
 
 // Eight lanes per cell: each lane accumulates q R(r_M - r_i) = q R(-u) of every
 // eighth particle of its cell into (p+1)^2 registers, a 3-step butterfly sums the
-// eight lanes, and a shared-memory transpose writes the channel-major M of 32
+// eight lanes, and a shared-memory transpose writes the channel-major M of 16
 // consecutive cells with coalesced stores.  Also the per-cell sums used by the
 // periodic corrections: cellsum = (sum q, sum q u_x, sum q u_y, sum q u_z,
 // sum q |u|^2), accumulated in T per lane and stored in FP64.
 constexpr int P2M_LPC = 8;                  // lanes per cell
-constexpr int P2M_CPB = 256 / P2M_LPC;      // cells per block
+constexpr int P2M_THREADS = 128;            // (small blocks fit beside the near field of a split evaluation)
+constexpr int P2M_CPB = P2M_THREADS / P2M_LPC;  // cells per block
 
 template <int P, typename T>
-__global__ void __launch_bounds__(256) p2m_kernel(const T* __restrict__ part, const int* __restrict__ cs, int64_t K,
+__global__ void __launch_bounds__(P2M_THREADS) p2m_kernel(const T* __restrict__ part, const int* __restrict__ cs, int64_t K,
                                                   T* __restrict__ M, double* __restrict__ cellsum) {
   constexpr int C = (P + 1) * (P + 1);
   __shared__ T sh[C][P2M_CPB + 1];
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(256) p2m_kernel(const T* __restrict__ part, co
   }
   __syncthreads();
   const int64_t c0 = (int64_t)blockIdx.x * P2M_CPB;
-  for (int idx = threadIdx.x; idx < C * P2M_CPB; idx += 256) {
+  for (int idx = threadIdx.x; idx < C * P2M_CPB; idx += P2M_THREADS) {
     const int c = idx / P2M_CPB, l = idx - c * P2M_CPB;
     if (c0 + l < K) M[(int64_t)c * K + c0 + l] = sh[c][l];
   }
@@ -337,7 +338,7 @@ cudaError_t p2m_run(const void* part, const int* cs, int64_t K, void* M, double*
     }
   }
   const int blocks = (int)((K + P2M_CPB - 1) / P2M_CPB);
-  p2m_kernel<P, T><<<blocks, 256, 0, s>>>((const T*)part, cs, K, (T*)M, cq);
+  p2m_kernel<P, T><<<blocks, P2M_THREADS, 0, s>>>((const T*)part, cs, K, (T*)M, cq);
   return cudaGetLastError();
 }
 
