@@ -309,7 +309,8 @@ int64_t pp_items_max(int64_t K, int64_t n);
 int64_t pp_pairs_max(int64_t K, int64_t n);
 // Near-field work lists: item_start / pair_start (exclusive scans of the per-cell
 // item and source-pair counts, K + 1 entries; pair_start may be null) and the
-// reset of the work counter.
+// reset of the work counter; chunks: scratch of pp_lists_chunk_entries(K) entries.
+int64_t pp_lists_chunk_entries(int64_t K);
 cudaError_t launch_pp_lists(const int* cell_start, int64_t K, uint32_t* item_start, uint32_t* pair_start,
                             uint32_t* chunks, unsigned int* counter, cudaStream_t s, int* nlaunch);
 // Sorted records part[s] = rec[vals[s]] (position relative to the cell centre in

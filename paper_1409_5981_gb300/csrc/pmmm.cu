@@ -141,7 +141,7 @@ cudaError_t alloc_mesh(pmmm_plan* pl, int B) {
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(double) * 16 * (size_t)B); pl->corr = (double*)v; }
   if (e == cudaSuccess) { e = dalloc(pl, &v, sizeof(uint32_t) * (size_t)(Kb + 1)); pl->item_start = (uint32_t*)v; }
   if (e == cudaSuccess) {
-    e = dalloc(pl, &v, sizeof(uint32_t) * (size_t)scan_chunk_count(Kb + 1));
+    e = dalloc(pl, &v, sizeof(uint32_t) * (size_t)pp_lists_chunk_entries(Kb));
     pl->item_chunks = (uint32_t*)v;
   }
   if (e == cudaSuccess && !pl->fp64) {

@@ -59,16 +59,14 @@ __global__ void item_count_kernel(const int* __restrict__ cs, int64_t K, uint32_
 // {x_a, x_b, y_a, y_b}, {z_a, z_b, q_a, q_b}, so that one 128-bit load yields
 // the packed operands of two sources.
 
-// Work lists of cells small enough for one block (K + 1 <= LIST_SCAN_MAX): item and
-// source-pair counts from the cell offsets and their exclusive prefix sums in one
-// launch.  Warp w owns the contiguous chunk of cells [w CH, (w+1) CH) and walks it
-// 32 cells at a time (lane = cell, loads and stores coalesced, eight rows of loads
-// in flight): a first walk sums the chunk, a block scan of the 32 chunk totals
-// gives each chunk its offset, a second walk writes the prefix sums with warp
-// scans and a running carry.
-constexpr int LIST_SCAN_THREADS = 1024;
-constexpr int64_t LIST_SCAN_MAX = 65537;
-constexpr int LIST_UNROLL = 8;
+// Work lists: item and source-pair counts per cell from the cell offsets and
+// their exclusive prefix sums, in two launches of LIST_BLK cells per block
+// (lane = cell, loads and stores coalesced): list_local_kernel scans each block's
+// cells (warp scans, then a scan of the 32 warp totals) and writes the block
+// totals; list_fix_kernel adds to every cell the totals of the blocks before its
+// own (a warp sums at most LIST_MAX_BLOCKS of them).
+constexpr int LIST_BLK = 1024;
+constexpr int64_t LIST_MAX_BLOCKS = 1024;
 
 __device__ __forceinline__ void cell_counts(const int* __restrict__ cs, int64_t c, int64_t K, uint32_t& ni,
                                             uint32_t& np) {
@@ -80,41 +78,31 @@ __device__ __forceinline__ void cell_counts(const int* __restrict__ cs, int64_t 
   }
 }
 
-__global__ void __launch_bounds__(LIST_SCAN_THREADS) list_scan_kernel(const int* __restrict__ cs, int64_t K,
-                                                                     uint32_t* __restrict__ item_start,
-                                                                     uint32_t* __restrict__ pair_start,
-                                                                     unsigned int* __restrict__ counter) {
+__global__ void __launch_bounds__(LIST_BLK) list_local_kernel(const int* __restrict__ cs, int64_t K,
+                                                              uint32_t* __restrict__ item_start,
+                                                              uint32_t* __restrict__ pair_start,
+                                                              uint32_t* __restrict__ tot,
+                                                              unsigned int* __restrict__ counter) {
   __shared__ uint32_t wi[32], wp[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t nk = K + 1;
-  const int64_t CH = (nk + 31) / 32;
-  const int64_t c_beg = (int64_t)warp * CH, c_end = c_beg + CH < nk ? c_beg + CH : nk;
-  // first walk: the chunk's totals
-  uint32_t si = 0, sp = 0;
-  for (int64_t b = c_beg; b < c_end; b += 32 * LIST_UNROLL) {
-    uint32_t a[LIST_UNROLL], q[LIST_UNROLL];
+  const int64_t c = (int64_t)blockIdx.x * LIST_BLK + tid;
+  uint32_t a, q;
+  cell_counts(cs, c, K, a, q);
+  uint32_t ii = a, ip = q;
 #pragma unroll
-    for (int u = 0; u < LIST_UNROLL; ++u) {
-      const int64_t c = b + 32 * u + lane;
-      cell_counts(cs, c < c_end ? c : K, K, a[u], q[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < LIST_UNROLL; ++u) {
-      si += a[u];
-      sp += q[u];
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, ii, o), y = __shfl_up_sync(0xffffffffu, ip, o);
+    if (lane >= o) {
+      ii += x;
+      ip += y;
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    si += __shfl_xor_sync(0xffffffffu, si, o);
-    sp += __shfl_xor_sync(0xffffffffu, sp, o);
-  }
-  if (lane == 0) {
-    wi[warp] = si;
-    wp[warp] = sp;
+  if (lane == 31) {
+    wi[warp] = ii;
+    wp[warp] = ip;
   }
   __syncthreads();
-  // chunk offsets: exclusive scan of the 32 chunk totals (every warp computes it)
+  // exclusive offsets of the warps (every warp scans the 32 totals)
   uint32_t ti = wi[lane], tp = wp[lane];
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -124,37 +112,47 @@ __global__ void __launch_bounds__(LIST_SCAN_THREADS) list_scan_kernel(const int*
       tp += y;
     }
   }
-  uint32_t carry_i = __shfl_sync(0xffffffffu, ti - wi[lane], warp);
-  uint32_t carry_p = __shfl_sync(0xffffffffu, tp - wp[lane], warp);
-  // second walk: exclusive prefix sums, 32 cells per row
-  for (int64_t b = c_beg; b < c_end; b += 32 * LIST_UNROLL) {
-    uint32_t a[LIST_UNROLL], q[LIST_UNROLL];
-#pragma unroll
-    for (int u = 0; u < LIST_UNROLL; ++u) {
-      const int64_t c = b + 32 * u + lane;
-      cell_counts(cs, c < c_end ? c : K, K, a[u], q[u]);
+  const uint32_t oi = __shfl_sync(0xffffffffu, ti - wi[lane], warp);
+  const uint32_t op = __shfl_sync(0xffffffffu, tp - wp[lane], warp);
+  if (c <= K) {
+    item_start[c] = oi + ii - a;
+    if (pair_start) pair_start[c] = op + ip - q;
+  }
+  if (tid == LIST_BLK - 1) {
+    tot[2 * blockIdx.x] = __shfl_sync(0xffffffffu, ti, 31);
+    tot[2 * blockIdx.x + 1] = __shfl_sync(0xffffffffu, tp, 31);
+  }
+  if (c == 0) *counter = 0u;
+}
+
+__global__ void __launch_bounds__(LIST_BLK) list_fix_kernel(int64_t K, uint32_t* __restrict__ item_start,
+                                                            uint32_t* __restrict__ pair_start,
+                                                            const uint32_t* __restrict__ tot) {
+  __shared__ uint32_t pre[2];
+  const int b = blockIdx.x;
+  if (b == 0) return;  // the first block's sums are complete
+  if (threadIdx.x < 32) {
+    uint32_t si = 0u, sp = 0u;
+    for (int j = threadIdx.x; j < b; j += 32) {
+      si += tot[2 * j];
+      sp += tot[2 * j + 1];
     }
 #pragma unroll
-    for (int u = 0; u < LIST_UNROLL; ++u) {
-      const int64_t c = b + 32 * u + lane;
-      uint32_t ii = a[u], ip = q[u];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t x = __shfl_up_sync(0xffffffffu, ii, o), y = __shfl_up_sync(0xffffffffu, ip, o);
-        if (lane >= o) {
-          ii += x;
-          ip += y;
-        }
-      }
-      if (c < c_end) {
-        item_start[c] = carry_i + ii - a[u];
-        if (pair_start) pair_start[c] = carry_p + ip - q[u];
-      }
-      carry_i += __shfl_sync(0xffffffffu, ii, 31);
-      carry_p += __shfl_sync(0xffffffffu, ip, 31);
+    for (int o = 16; o > 0; o >>= 1) {
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+      sp += __shfl_xor_sync(0xffffffffu, sp, o);
+    }
+    if (threadIdx.x == 0) {
+      pre[0] = si;
+      pre[1] = sp;
     }
   }
-  if (tid == 0) *counter = 0u;
+  __syncthreads();
+  const int64_t c = (int64_t)b * LIST_BLK + threadIdx.x;
+  if (c <= K) {
+    item_start[c] += pre[0];
+    if (pair_start) pair_start[c] += pre[1];
+  }
 }
 
 // Sorted records part[s] = rec[vals[s]] (a pure permutation), and with them the
@@ -172,27 +170,48 @@ __global__ void gather_lists_kernel(const V* __restrict__ rec, const uint32_t* _
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (int64_t i = (zero_all ? 0 : (int64_t)item_start[K]) + s; i < max_items; i += (int64_t)gridDim.x * blockDim.x)
     epart[4 * i] = epart[4 * i + 1] = epart[4 * i + 2] = epart[4 * i + 3] = 0.0;
-  if (s >= n) return;
-  const V r = rec[vals[s]];
-  part[s] = r;
-  const uint32_t cell = keys[s];
-  const int c0 = cs[cell];
-  const int j = (int)(s - c0);
-  if (j % CHUNK == 0) item_cell[item_start[cell] + j / CHUNK] = cell;
+  if (s - (int64_t)(threadIdx.x & 31) >= n) return;  // the whole warp lies past the particles
+  const bool live = s < n;  // lanes past the particles stay for the shuffles below
+  V r;
+  r.x = r.y = r.z = r.w = 0;
+  uint32_t cell = 0;
+  int j = 0;
+  if (live) {
+    r = rec[vals[s]];
+    part[s] = r;
+    cell = keys[s];
+    j = (int)(s - cs[cell]);
+    if (j % CHUNK == 0) item_cell[item_start[cell] + j / CHUNK] = cell;
+  }
   if constexpr (PACK) {
-    const int64_t pj = (int64_t)pair_start[cell] + j / 2;
+    // pair record of (a, b) = sorted particles (s, s + 1), j even: a writes
+    // {x_a, x_b, y_a, y_b}, b writes {z_a, z_b, q_a, q_b}, each one 16-byte store; the
+    // partner's values come from the neighbouring lane (a global load at the warp's edge)
     const int slot = j & 1;
-    float* o = src2 + 8 * pj;
-    o[0 + slot] = (float)r.x;
-    o[2 + slot] = (float)r.y;
-    o[4 + slot] = (float)r.z;
-    o[6 + slot] = (float)r.w;
-    if (slot == 0 && s + 1 == (int64_t)cs[cell + 1]) {  // odd count: dummy partner
-      o[1] = 1.0e4f;
-      o[3] = 1.0e4f;
-      o[5] = 1.0e4f;
-      o[7] = 0.0f;
+    const int lane = threadIdx.x & 31;
+    const int src_lane = (slot == 0 ? lane + 1 : lane - 1) & 31;
+    float px = __shfl_sync(0xffffffffu, (float)r.x, src_lane), py = __shfl_sync(0xffffffffu, (float)r.y, src_lane);
+    float pz = __shfl_sync(0xffffffffu, (float)r.z, src_lane), pw = __shfl_sync(0xffffffffu, (float)r.w, src_lane);
+    if (!live) return;
+    const int64_t pj = (int64_t)pair_start[cell] + j / 2;
+    const bool alone = slot == 0 && s + 1 == (int64_t)cs[cell + 1];  // odd count: dummy partner
+    const bool edge = slot == 0 ? lane == 31 : lane == 0;  // partner in the neighbouring warp
+    if (alone) {
+      px = py = pz = 1.0e4f;
+      pw = 0.0f;
+    } else if (edge) {
+      const V pr = rec[vals[slot == 0 ? s + 1 : s - 1]];
+      px = (float)pr.x;
+      py = (float)pr.y;
+      pz = (float)pr.z;
+      pw = (float)pr.w;
     }
+    float4* o = reinterpret_cast<float4*>(src2 + 8 * pj);
+    if (slot == 0)
+      o[0] = make_float4((float)r.x, px, (float)r.y, py);
+    else
+      o[1] = make_float4(pz, (float)r.z, pw, (float)r.w);
+    if (alone) o[1] = make_float4((float)r.z, pz, (float)r.w, pw);
   }
 }
 
@@ -978,11 +997,21 @@ int64_t pp_items_max(int64_t K, int64_t n) { return K + (n + CHUNK - 1) / CHUNK 
 
 int64_t pp_pairs_max(int64_t K, int64_t n) { return (n + K) / 2 + 1; }
 
+int64_t pp_lists_chunk_entries(int64_t K) {
+  const int64_t a = scan_chunk_count(K + 1), b = 2 * ((K + 1 + LIST_BLK - 1) / LIST_BLK);
+  return a > b ? a : b;
+}
+
 cudaError_t launch_pp_lists(const int* cell_start, int64_t K, uint32_t* item_start, uint32_t* pair_start,
                             uint32_t* chunks, unsigned int* counter, cudaStream_t s, int* nl) {
-  if (K + 1 <= LIST_SCAN_MAX) {
-    list_scan_kernel<<<1, LIST_SCAN_THREADS, 0, s>>>(cell_start, K, item_start, pair_start, counter);
+  const int64_t nb = (K + 1 + LIST_BLK - 1) / LIST_BLK;
+  if (nb <= LIST_MAX_BLOCKS) {
+    list_local_kernel<<<(unsigned)nb, LIST_BLK, 0, s>>>(cell_start, K, item_start, pair_start, chunks, counter);
     ++*nl;
+    if (nb > 1) {
+      list_fix_kernel<<<(unsigned)nb, LIST_BLK, 0, s>>>(K, item_start, pair_start, chunks);
+      ++*nl;
+    }
     return cudaGetLastError();
   }
   item_count_kernel<<<(unsigned)((K + 1 + 255) / 256), 256, 0, s>>>(cell_start, K, item_start, pair_start, counter);
@@ -1022,9 +1051,8 @@ cudaError_t launch_pp_combine(const void* part, const uint32_t* vals, const int*
                               const void* far, const void* nearv, PPParams pp, void* phi, void* force, double* epart,
                               int num_sms, cudaStream_t s, int* nl) {
   if (max_items <= 0) return cudaSuccess;
-  int64_t blocks = (max_items + 7) / 8;  // 8 warps (items) per block
-  const int64_t cap = 8 * (int64_t)(num_sms > 0 ? num_sms : 1);
-  if (blocks > cap) blocks = cap;
+  (void)num_sms;
+  const int64_t blocks = (max_items + 7) / 8;  // 8 warps (items) per block, one item per warp
   pp_combine_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float4*)part, vals, cell_start, K, item_start, item_cell,
                                                      (const float4*)far, (const float4*)nearv, pp, (float*)phi,
                                                      (float*)force, epart);
