@@ -57,8 +57,15 @@ typedef enum { PMMM_FP64 = 0, PMMM_FP32 = 1, PMMM_FP32_SPLITBF16_M2L = 2 } pmmm_
  *   PMMM_NEAR_PER_TARGET  one thread per particle (FP32 precisions, c = 1 only):
  *                         for sparsely filled cells
  *   PMMM_NEAR_AUTO        per target when N < PMMM_NEAR_AUTO_OCCUPANCY x cells
- *                         (and it applies), else cell items */
-typedef enum { PMMM_NEAR_AUTO = 0, PMMM_NEAR_CELL_ITEMS = 1, PMMM_NEAR_PER_TARGET = 2 } pmmm_near_field;
+ *                         (and it applies), else cell items
+ *   PMMM_NEAR_CELL_ITEMS_SPLIT  cell items, with the far field on a second stream
+ *                         beside them (FP32 precisions; see PMMM_INFO_SPLIT) */
+typedef enum {
+  PMMM_NEAR_AUTO = 0,
+  PMMM_NEAR_CELL_ITEMS = 1,
+  PMMM_NEAR_PER_TARGET = 2,
+  PMMM_NEAR_CELL_ITEMS_SPLIT = 3
+} pmmm_near_field;
 #define PMMM_NEAR_AUTO_OCCUPANCY 8
 
 enum {
@@ -254,13 +261,14 @@ enum {
   PMMM_INFO_M2L_ARITH = 12, /* arithmetic of the last compute's M2L: PMMM_M2L_ARITH_* (-1 before any) */
   PMMM_INFO_SPLIT = 13      /* 1 if the last compute ran the far field beside the near field (below) */
 };
-/* Split evaluation (FP32 plans whose near field runs on cell items, i.e. not the
- * per-target kernel of sparse cells): after the sort, the far field (P2M, mesh
- * stage, periodic corrections, L2P) runs on a second stream of the plan, created
- * with the highest priority, beside the near field, whose sums go to a workspace
- * buffer; one more launch adds the two.  The results equal those of the plain
- * sequence bit for bit.  Off while stage timing is on and for surrogate
- * evaluations. */
+/* Split evaluation (near_field = PMMM_NEAR_CELL_ITEMS_SPLIT, set in the config or
+ * chosen by pmmm_plan_autotune; FP32 plans): after the sort, the far field (P2M,
+ * mesh stage, periodic corrections, L2P) runs on a second stream of the plan,
+ * created with the highest priority, beside the cell-item near field, whose sums
+ * go to a workspace buffer (16 bytes per particle, allocated on the first plain
+ * call that needs it); one more launch adds the two.  The results equal those of
+ * the one-stream sequence bit for bit.  One stream while stage timing is on, for
+ * surrogate evaluations and inside a capture that would need the buffer first. */
 /* The M2L arithmetic that actually ran.  PMMM_FP32_SPLITBF16_M2L asks for the
  * tensor cores, but they serve only where the per-wavevector M2L is a true matrix
  * product: batched evaluations of more than one system, and the fine-level block

@@ -21,7 +21,7 @@ ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OUT_OF_BOX, ERR_NONFINITE_INPUT = -1, -2, 
 ERR_CUDA, ERR_TIMEOUT, ERR_OOM = -5, -6, -7
 OPEN, PERIODIC = 0, 1
 FP64, FP32, FP32_SPLITBF16_M2L = 0, 1, 2
-NEAR_AUTO, NEAR_CELL_ITEMS, NEAR_PER_TARGET = 0, 1, 2
+NEAR_AUTO, NEAR_CELL_ITEMS, NEAR_PER_TARGET, NEAR_CELL_ITEMS_SPLIT = 0, 1, 2, 3
 NEAR_AUTO_OCCUPANCY = 8
 EXPORT_PERM, EXPORT_SORTED_CELL, EXPORT_CELL_START = 1, 2, 3
 EXPORT_MULTIPOLE, EXPORT_LOCAL, EXPORT_CORR, EXPORT_FAR = 4, 5, 6, 7

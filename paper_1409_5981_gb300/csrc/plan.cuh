@@ -109,13 +109,13 @@ struct pmmm_plan {
   size_t ws_bytes = 0;
   bool timing = false, timed = false;
   cudaEvent_t ev[ST_COUNT + 1] = {};
-  // split evaluation (FP32 cell-item near field): the far field (P2M .. L2P) runs
-  // on `aux` beside the near field, which leaves its sums in `nearv` (float4 per
-  // sorted particle); fork / join order the two streams
+  // split evaluation (PMMM_NEAR_CELL_ITEMS_SPLIT, FP32): the far field (P2M .. L2P)
+  // runs on `aux` beside the near field, which leaves its sums in `nearv` (float4
+  // per sorted particle); fork / join order the two streams
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   void* nearv = nullptr;
-  bool split = true, split_last = false;
+  bool split_last = false;
 };
 
 

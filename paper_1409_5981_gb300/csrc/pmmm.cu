@@ -159,6 +159,11 @@ cudaError_t alloc_mesh(pmmm_plan* pl, int B) {
 int ensure_particles(pmmm_plan* pl, int64_t n);
 int ensure_m2l_tables(pmmm_plan* pl);
 void set_streams(pmmm_plan* pl, cudaStream_t s);
+// the near sums' buffer of the split evaluation is kept once a choice asks for it
+bool wants_split(const pmmm_plan* pl) {
+  return !pl->fp64 && (pl->cfg.near_field == PMMM_NEAR_CELL_ITEMS_SPLIT || pl->tuned_near == PMMM_NEAR_CELL_ITEMS_SPLIT ||
+                       pl->nearv != nullptr);
+}
 
 // Grows the mesh workspace to B systems (the particle workspace, sized by the
 // cell count, is rebuilt with it).
@@ -187,7 +192,7 @@ int validate(const pmmm_config* c) {
   if (c->p < 0 || c->cutoff < 1) return PMMM_ERR_INVALID_ARG;
   if (!(c->sign == 1.0 || c->sign == -1.0)) return PMMM_ERR_INVALID_ARG;
   if (c->ewald_alpha < 0.0 || !isfinite(c->ewald_alpha) || c->ewald_nmax < 0) return PMMM_ERR_INVALID_ARG;
-  if (c->near_field < PMMM_NEAR_AUTO || c->near_field > PMMM_NEAR_PER_TARGET) return PMMM_ERR_INVALID_ARG;
+  if (c->near_field < PMMM_NEAR_AUTO || c->near_field > PMMM_NEAR_CELL_ITEMS_SPLIT) return PMMM_ERR_INVALID_ARG;
   if (c->p > PMMM_PMAX || c->cutoff > 2) return PMMM_ERR_UNSUPPORTED;
   for (int a = 0; a < 3; ++a) {
     if (!pow2(c->mesh[a])) return PMMM_ERR_UNSUPPORTED;
@@ -240,7 +245,7 @@ int ensure_particles(pmmm_plan* pl, int64_t n) {
   if (e == cudaSuccess) e = dalloc(pl, &v, sizeof(double) * 4 * (size_t)mi);
   if (e == cudaSuccess) pl->epart = (double*)v;
   if (e == cudaSuccess && !pl->fp64) e = dalloc(pl, &pl->src2, 32 * (size_t)pp_pairs_max(Kb, cap));
-  if (e == cudaSuccess && !pl->fp64 && pl->split) e = dalloc(pl, &pl->nearv, 16 * (size_t)cap);
+  if (e == cudaSuccess && wants_split(pl)) e = dalloc(pl, &pl->nearv, 16 * (size_t)cap);
   // items of one system: at most its cells + cap / 32 + 1
   const int bch = reduce_batched_chunks(pl->d.K, pp_items_max(pl->d.K, cap));
   if (e == cudaSuccess) e = dalloc(pl, &v, sizeof(double) * 5 * (size_t)pl->bcap * bch);
@@ -497,8 +502,15 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
   // and runs beside the near field, which then leaves its sums in nearv; a
   // combination launch follows both.  Not with stage timing (stages queued one
   // by one) nor with a far-field hook (the surrogate's own plans).
-  split = pl->split && pl->aux && pl->nearv && !pl->timing && !pl->hook && pl->src2 &&
+  split = near == PMMM_NEAR_CELL_ITEMS_SPLIT && pl->aux && !pl->timing && !pl->hook && pl->src2 &&
           pp_tma_applies(fp64, pl->g.c, per_target);
+  if (split && !pl->nearv) {
+    // the near sums' buffer, allocated outside a capture (inside one: one stream)
+    if (pl->capturing || pl->cap <= 0)
+      split = false;
+    else
+      CK(dalloc(pl, &pl->nearv, 16 * (size_t)pl->cap));
+  }
   fs = s;
   if (split) {
     CK(cudaEventRecord(pl->ev_fork, s));
@@ -867,7 +879,6 @@ int pmmm_plan_create(const pmmm_config* cfg, void* stream, pmmm_plan** out) {
   pl->C = (cfg->p + 1) * (cfg->p + 1);
   pl->CG = (2 * cfg->p + 1) * (2 * cfg->p + 1);
   pl->fp64 = cfg->precision == PMMM_FP64;
-  pl->split = !pl->fp64;
   pl->m2l_tc = cfg->precision == PMMM_FP32_SPLITBF16_M2L && m2l_tc_supported(cfg->p);
   pl->tsize = pl->fp64 ? sizeof(double) : sizeof(float);
   const bool per = cfg->boundary == PMMM_PERIODIC;
@@ -912,7 +923,7 @@ int pmmm_plan_create(const pmmm_config* cfg, void* stream, pmmm_plan** out) {
   if (e == cudaSuccess) e = launch_twiddles(pl->fp64, d.Ly, pl->twy, pl->stream);
   if (e == cudaSuccess) e = launch_twiddles(pl->fp64, d.Lz, pl->twz, pl->stream);
   for (int i = 0; i <= ST_COUNT && e == cudaSuccess; ++i) e = cudaEventCreate(&pl->ev[i]);
-  if (e == cudaSuccess && pl->split) {
+  if (e == cudaSuccess && !pl->fp64) {
     // the far field's stream takes the highest priority, so that its blocks are
     // placed ahead of queued near-field blocks
     int lo = 0, hi = 0;
@@ -1040,7 +1051,8 @@ int pmmm_plan_autotune(pmmm_plan* pl, int32_t nsys, const int64_t* offsets, cons
   if (rc != PMMM_OK) return rc;
   if (n > 0 && (!pos || !q)) return PMMM_ERR_INVALID_ARG;
   std::vector<int> nears = {pl->tuned_near};
-  if (pp_per_target_applies(pl->fp64, pl->g.c)) nears = {PMMM_NEAR_CELL_ITEMS, PMMM_NEAR_PER_TARGET};
+  if (pp_per_target_applies(pl->fp64, pl->g.c))
+    nears = {PMMM_NEAR_CELL_ITEMS, PMMM_NEAR_PER_TARGET, PMMM_NEAR_CELL_ITEMS_SPLIT};
   std::vector<int> tiles = {pl->m2l_tile};
   if (pl->m2l_tc && nsys > 1) tiles = {64, 32};
   cudaEvent_t e0, e1;

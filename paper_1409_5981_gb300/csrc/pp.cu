@@ -20,7 +20,7 @@ namespace pmmm {
 namespace {
 
 constexpr int PP_WARPS = 4;
-constexpr int PP_BATCH = 4;  // work items taken per atomic by the FP32 near-field warps
+constexpr int PP_BATCH = 1;  // work items taken per atomic by the FP32 near-field warps (one: the shortest tail)
 constexpr int PP_BLOCKS_PER_SM = 6;  // resident blocks per SM (up to 80 registers per thread)
 constexpr int CHUNK = 32;
 

@@ -392,7 +392,8 @@ def test_batched_splitbf16_tensor_core_m2l(pk, p, boundary):
 
 
 def test_autotune_choices_are_equivalent(pk):
-    """pmmm_plan_autotune picks a near-field kernel and a tensor-core M2L tile by timing;
+    """pmmm_plan_autotune picks a near-field kernel (cell items with or without the far
+    field beside them, or one thread per target) and a tensor-core M2L tile by timing;
     whatever it picks, the results agree with the untuned plan to rounding, and the
     chosen configuration reproduces itself bit for bit."""
     import torch
@@ -404,7 +405,7 @@ def test_autotune_choices_are_equivalent(pk):
     phi0, f0, e0 = base.compute_batched(counts, tp, tq, energies=True)
     plan = pk.Plan(cfg)
     near, tile = plan.autotune(counts, tp, tq, reps=2)
-    assert near in (pk.NEAR_CELL_ITEMS, pk.NEAR_PER_TARGET) and tile in (32, 64)
+    assert near in (pk.NEAR_CELL_ITEMS, pk.NEAR_PER_TARGET, pk.NEAR_CELL_ITEMS_SPLIT) and tile in (32, 64)
     phi1, f1, e1 = plan.compute_batched(counts, tp, tq, energies=True)
     phi2, f2, e2 = plan.compute_batched(counts, tp, tq, energies=True)
     assert torch.equal(phi1, phi2) and torch.equal(f1, f2) and np.array_equal(e1, e2)

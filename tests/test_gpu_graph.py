@@ -103,13 +103,14 @@ def test_batched_graph_default_stream(pk):
 
 @pytest.mark.parametrize("boundary,cutoff", [("periodic", 1), ("periodic", 2), ("open", 1)])
 def test_split_evaluation_matches_plain_sequence(pk, boundary, cutoff):
-    """FP32 cell-item near field: the far field runs on the plan's second stream
+    """near_field = NEAR_CELL_ITEMS_SPLIT: the far field runs on the plan's second stream
     beside the near field (PMMM_INFO_SPLIT = 1), plain and graph-launched, and
     gives the results of the one-stream sequence (stage timing on) bit for bit,
     energies included; the batched form too."""
     import torch
     bc = pk.PERIODIC if boundary == "periodic" else pk.OPEN
-    cfg = pk.Config(mesh=(8, 8, 8), p=4, boundary=bc, precision=pk.FP32, cutoff=cutoff)
+    cfg = pk.Config(mesh=(8, 8, 8), p=4, boundary=bc, precision=pk.FP32, cutoff=cutoff,
+                    near_field=pk.NEAR_CELL_ITEMS_SPLIT)
     n = 32 * 8 ** 3  # 32 per cell: cell items, not the per-target kernel
     pos, q = synth.uniform_pm1(n, synth.seed(7, 10 + cutoff))
     tp = torch.tensor(pos.astype(np.float32), device="cuda")
