@@ -352,8 +352,8 @@ def _mesh_roofline_64(pk, torch, dev, hbm, flush, steps=6):
             "achieved": own / (ms * 1e-3) / 1e9, "frac": own / (ms * 1e-3) / 1e9 / hbm,
             "bytes": own, "bytes_model": "4B*(2CK + 8CKh + C_G Kh): M read, spectra written and read, parity-reduced "
                                           "G~ read (one real number per value), L written",
-            "frac_survey_model": full / (ms * 1e-3) / 1e9 / hbm,
-            "survey_model": "16CK + 32CKh + 8C_G Kh (adds the P2M write of M and the L2P read of L, whose "
+            "frac_full_pass_model": full / (ms * 1e-3) / 1e9 / hbm,
+            "full_pass_model": "16CK + 32CKh + 8C_G Kh (adds the P2M write of M and the L2P read of L, whose "
                             "time is not in the stages timed)"}
 
 
