@@ -285,8 +285,9 @@ int pmmm_plan_info(pmmm_plan* plan, int what, int64_t* value);
 /* Autotuner: evaluates the given input (nsys systems; offsets as in
  * pmmm_compute_batched, or {0, n} for one system) once per candidate of each
  * tunable choice, timed over `reps` evaluations with CUDA events after one
- * warm-up, and keeps the fastest: the near-field kernel (cell items or per
- * target, where both apply) and, for batched PMMM_FP32_SPLITBF16_M2L plans, the
+ * warm-up, and keeps the fastest: the near-field schedule (cell items, cell items
+ * with the far field beside them, or per target, where these apply) and, for
+ * batched PMMM_FP32_SPLITBF16_M2L plans, the
  * systems per CTA of the tensor-core M2L (64 or 32).  The choice overrides the
  * config's near_field; results differ between choices only by the order of
  * floating-point sums.  Synchronous; reads back with PMMM_INFO_TUNED_NEAR and
