@@ -505,8 +505,12 @@ int run(pmmm_plan* pl, int B, int64_t n, const void* pos, const void* q, void* p
   split = near == PMMM_NEAR_CELL_ITEMS_SPLIT && pl->aux && !pl->timing && !pl->hook && pl->src2 &&
           pp_tma_applies(fp64, pl->g.c, per_target);
   if (split && !pl->nearv) {
-    // the near sums' buffer, allocated outside a capture (inside one: one stream)
-    if (pl->capturing || pl->cap <= 0)
+    // the near sums' buffer, allocated outside a capture (the plan's or the
+    // caller's; inside one the evaluation keeps one stream)
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    const cudaError_t qe = pl->capturing ? cudaSuccess : cudaStreamIsCapturing(s, &cst);
+    if (qe != cudaSuccess) cudaGetLastError();  // only the answer matters here
+    if (pl->capturing || pl->cap <= 0 || qe != cudaSuccess || cst != cudaStreamCaptureStatusNone)
       split = false;
     else
       CK(dalloc(pl, &pl->nearv, 16 * (size_t)pl->cap));
