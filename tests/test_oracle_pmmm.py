@@ -169,3 +169,34 @@ def test_binning_faces_wrap_and_errors():
     assert st == 0
     assert np.allclose(w, [[0.25, 0.5, 3.0], [0.75, -1.0, 5.0]])
     assert list(cell) == [1 + 4 * (6 + 8 * 0), 3 + 4 * (0 + 8 * 1)]
+
+
+def test_fixed_error_order_per_cutoff():
+    """The error axis of the headline metric: relative RMS force error against Ewald
+    (Eq. refewald) of the bench's distribution (uniform, 32 particles per cell, +-1
+    charges, periodic) for p = 2..8 (c = 1) and 2..6 (c = 2), on all particles of 32
+    seeded cells of an 8^3 mesh.  It falls by a constant ratio per order, faster than Eq. errest's
+    worst-case ratio, c = 2 below c = 1; the lowest order at a relative RMS force error
+    <= 1e-4 is p = 7 for c = 1 (the bench's order) and p = 4 for c = 2."""
+    n, m = 16384, 8
+    pos, q = synth.uniform_pm1(n, synth.seed(2, 77))
+    cells = synth.rng(synth.seed(2, 78)).choice(m ** 3, size=32, replace=False)
+    _, cell, *_ = oracle.bin_particles(pos, *UNIT, (m,) * 3, True)
+    tg = np.nonzero(np.isin(cell, cells))[0]
+    _, g_e = oracle.ewald(pos, q, (1, 1, 1), targets=tg)
+    lowest = {}
+    for c, orders in ((1, range(2, 9)), (2, range(2, 7))):
+        e = []
+        for p in orders:
+            r = oracle.pmmm(pos, q, *UNIT, (m,) * 3, p, c, True, target_cells=cells)
+            g = r["grad"][tg]
+            e.append(float(np.sqrt((q[tg, None] ** 2 * (g - g_e) ** 2).sum() / (q[tg, None] ** 2 * g_e ** 2).sum())))
+        print(f"c = {c}: force error vs Ewald " + ", ".join(f"p={p} {x:.2e}" for p, x in zip(orders, e)))
+        assert all(b < a for a, b in zip(e, e[1:])), e
+        rate = (e[-1] / e[0]) ** (1.0 / (len(e) - 1))
+        assert rate < oracle.error_estimate(c, 1) / oracle.error_estimate(c, 0), (c, rate)
+        lowest[c] = next(p for p, x in zip(orders, e) if x <= 1e-4)
+        if c == 2:  # same orders: c = 2 below c = 1
+            assert all(x2 < x1 for x2, x1 in zip(e, e1)), (e, e1)
+        e1 = e
+    assert lowest == {1: 7, 2: 4}, lowest
